@@ -1,0 +1,187 @@
+/*
+ * stmg.h -- C ABI of the GB300 space-time multigrid (STMG) library, libstmg.so.
+ *
+ * The library solves the slab systems of tensor-product space-time finite
+ * elements (continuous Q_p in space on a structured, Q1-mapped grid; dG(k) or
+ * cGP(k) in time) for the heat equation and the acoustic wave equation:
+ *
+ *     S u = rhs,   S = T_A (x) A_h + T_M (x) M_h            (Section 2)
+ *
+ * heat dG  (eq. heat-cg-dg):  T_A = M_tau, T_M = A_tau
+ * heat cGP (eq. heat-cg-cg):  T_A = M_tau, T_M = A_tau
+ * wave dG/cGP (eqs. wave-cg-dg, wave-cg-cg, condensed to u):
+ *                             T_A = M_tau, T_M = A_tau M_tau^-1 A_tau
+ * with M_h, A_h the Q_p mass and rho-weighted stiffness matrices
+ * (eq. space-matrices), by FGMRES preconditioned with one space-time multigrid
+ * V-cycle (Algorithm stmg) whose smoother is the space-time cell-wise additive
+ * Schwarz method (eqs. vanka0, vanka) and whose levels coarsen first in space
+ * (p, then h) and then in time (k) (Algorithm mg-sequence, Section 3.2).
+ *
+ * Conventions for every vector argument:
+ *   - caller-owned DEVICE memory (unless the function name ends in _host);
+ *   - layout [N_t][n_nodes]: N_t time-major blocks of all spatial nodes;
+ *   - nodes lexicographic, x fastest: node (gx, gy, gz) ->
+ *       gx + (p*N+1) * (gy + (p*N+1) * gz);
+ *   - nodes on the boundary of the domain carry homogeneous Dirichlet
+ *     conditions: operators act as the identity on those rows and ignore
+ *     those columns; right-hand sides and corrections are zero there;
+ *   - element type double for precision STMG_FP64 and float for STMG_FP32.
+ * Calls are asynchronous on the stream passed to stmg_create unless stated.
+ * No call throws; every call returns a status and, on error, stores a message
+ * readable with stmg_last_error.  After STMG_ERR_CUDA the context must be
+ * destroyed.  A context is not thread safe.
+ */
+#ifndef STMG_H
+#define STMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stmg_ctx stmg_ctx;
+
+typedef enum {
+  STMG_OK = 0,
+  STMG_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range */
+  STMG_ERR_CUDA = 2,          /* a CUDA runtime call failed; destroy the context */
+  STMG_ERR_OOM = 3,           /* device allocation failed */
+  STMG_ERR_NOT_CONVERGED = 4, /* FGMRES hit max_it before rtol */
+  STMG_ERR_BREAKDOWN = 5,     /* Krylov breakdown before convergence */
+  STMG_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  STMG_ERR_NONFINITE = 7,     /* NaN/Inf met in a residual or preconditioner output */
+  STMG_ERR_INTERNAL = 8,
+  STMG_ERR_UNSUPPORTED = 9    /* valid request outside the compiled kernel set */
+} stmg_status;
+
+enum { STMG_HEAT = 0, STMG_WAVE = 1 };                 /* PDE, eqs. heat, wave */
+enum { STMG_DG = 0, STMG_CGP = 1 };                    /* time discretisation, Sections 2.1 / 2.2 */
+enum { STMG_COEFF_PER_CELL = 0, STMG_COEFF_PER_QPOINT = 1 };
+enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3 };   /* 0 in an option = default */
+enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2 };
+
+/* Structured grid of n_cells^dim cells.  vertices: HOST array of
+ * (n_cells+1)^dim x dim coordinates (lexicographic, x fastest), copied at
+ * create; NULL means the Cartesian grid of [0,1]^dim.  Boundary vertices must
+ * lie on the boundary of the unit box (homogeneous Dirichlet on all of it). */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int n_cells;             /* cells per direction, >= 2 */
+  const double* vertices;  /* host, may be NULL */
+} stmg_mesh;
+
+/* The slab problem (Section 2).  p: spatial degree 1..4; k: time degree
+ * (dG: 0..3, N_t = k+1; cGP: 1..4, N_t = k); tau: slab length.
+ * coeff (HOST, copied at create): rho of eq. space-matrices, either one value
+ * per finest cell (PER_CELL) or one per finest-level Gauss point
+ * ([cell][(p+1)^dim points, x fastest], PER_QPOINT); NULL means rho = 1.
+ * Coarse levels sample the finest cell means at their Gauss points by logical
+ * (reference-grid) position. */
+typedef struct {
+  int pde;
+  int time_scheme;
+  int p;
+  int k;
+  double tau;
+  int coeff_mode;
+  const double* coeff;
+} stmg_problem;
+
+/* Solver options.  Zero-initialised fields take the defaults in brackets.
+ * omega: HOST array with one relaxation weight per smoothed level (all levels
+ * but the coarsest), copied at create; NULL estimates each by eq. relaxation
+ * (20-step Arnoldi on S_l B_l, omega = 2/(Re lambda_max + Re lambda_min)). */
+typedef struct {
+  int nu_pre;              /* pre-smoothing sweeps nu_1 of Algorithm stmg [1] */
+  int nu_post;             /* post-smoothing sweeps nu_2 [1] */
+  int vcycle_precision;    /* STMG_FP32 (mixed) or STMG_FP64 (plain) [FP32] */
+  int inverse_precision;   /* storage of dense local inverses: FP64/FP32/BF16 [same as V-cycle] */
+  int smoother_kind;       /* AUTO, DENSE or FD [AUTO: FD on Cartesian grids with constant rho, else DENSE] */
+  const double* omega;     /* host, may be NULL */
+  int fgmres_restart;      /* [30] */
+  double rtol;             /* relative residual target of stmg_solve [1e-8] */
+  int max_it;              /* [200] */
+} stmg_options;
+
+typedef struct {
+  int iterations;          /* FGMRES iterations (= V-cycles) */
+  int restarts;
+  double rel_residual;     /* ||rhs - S u||_2 / ||rhs||_2 computed in FP64 at exit */
+  double initial_rel_residual;
+} stmg_solve_stats;
+
+/* Builds all levels, geometry, smoother inverses, transfers and the coarse
+ * solver on the device; *out receives the context.  stream: a cudaStream_t
+ * (NULL = legacy default stream).  Synchronous. */
+stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_problem* problem,
+                        const stmg_options* options, void* stream);
+stmg_status stmg_destroy(stmg_ctx* ctx);
+const char* stmg_last_error(const stmg_ctx* ctx);
+
+/* Sizes of the finest level and number of levels (level 0 = finest). */
+stmg_status stmg_sizes(const stmg_ctx* ctx, int64_t* n_nodes, int* n_t, int* n_levels);
+/* Per-level data: degree p, cells per direction, time degree k, nodes, N_t, omega. */
+stmg_status stmg_level_info(const stmg_ctx* ctx, int level, int* p, int* n_cells, int* k,
+                            int64_t* n_nodes, int* n_t, double* omega);
+/* Physical node coordinates of a level (HOST output, n_nodes x dim).  Synchronous. */
+stmg_status stmg_node_coords(const stmg_ctx* ctx, int level, double* xyz);
+/* Physical Gauss-point coordinates of a level (HOST output, cells x (p+1)^dim x dim). */
+stmg_status stmg_qpoint_coords(const stmg_ctx* ctx, int level, double* xyz);
+
+/* y = S_l x on level l (matrix-free, sum factorisation, Section 3.1). */
+stmg_status stmg_apply(stmg_ctx* ctx, int level, int precision, const void* x, void* y);
+/* r = f - S_l u. */
+stmg_status stmg_residual(stmg_ctx* ctx, int level, int precision, const void* f, const void* u, void* r);
+/* sweeps of u <- u + omega_l sum_T R_T^T [R_T S_l R_T^T]^-1 R_T (f - S_l u)  (eqs. vanka0, vanka). */
+stmg_status stmg_smooth(stmg_ctx* ctx, int level, int precision, int sweeps, const void* f, void* u);
+/* r_{l+1} = P_l^T r_l (restriction from level l to level l+1, Section 3.2). */
+stmg_status stmg_restrict(stmg_ctx* ctx, int level, int precision, const void* r_fine, void* r_coarse);
+/* u_l += P_l e_{l+1} (prolongation and correction, Section 3.2). */
+stmg_status stmg_prolongate_add(stmg_ctx* ctx, int level, int precision, const void* e_coarse, void* u_fine);
+/* e = V-cycle(r) with zero initial guess on the finest level (Algorithm stmg). */
+stmg_status stmg_vcycle(stmg_ctx* ctx, int precision, const void* r, void* e);
+
+/* Right-hand side of the slab (FP64): rhs = M_tau(x)M_h f + [known-data terms of
+ * eqs. heat-cg-dg / heat-cg-cg / wave-cg-dg / wave-cg-cg]; f: nodal source
+ * values [N_t][n_nodes] at the free time nodes of the slab; f0: source at the
+ * slab start (cGP only, else ignored, may be NULL); u0, v0: end values of the
+ * previous slab (v0 wave only).  Rows of boundary nodes are set to 0. */
+stmg_status stmg_rhs(stmg_ctx* ctx, const double* f, const double* f0, const double* u0,
+                     const double* v0, double* rhs);
+/* FGMRES (right preconditioned, one V-cycle per iteration) on the finest level
+ * in FP64 until ||rhs - S u|| <= rtol ||rhs||; u holds the initial guess on entry.
+ * Synchronous (reads the Krylov scalars each iteration).  stats may be NULL. */
+stmg_status stmg_solve(stmg_ctx* ctx, const double* rhs, double* u, stmg_solve_stats* stats);
+/* Wave only: velocity of the slab from the condensed solution,
+ * v = M_tau^-1 (A_tau u + alpha u0 - beta v0) (cGP) / M_tau^-1 (A_tau u - alpha u0) (dG). */
+stmg_status stmg_wave_velocity(stmg_ctx* ctx, const double* u, const double* u0, const double* v0,
+                               double* v);
+/* Broadcast of the previous slab's end value to all time DoFs (the plain initial guess). */
+stmg_status stmg_guess_previous(stmg_ctx* ctx, const double* u0, double* u);
+
+/* End-to-end slab step from HOST buffers: uploads f [N_t][n], f0, u0, v0 (may be
+ * NULL as above), builds the right-hand side, solves from the previous-slab
+ * guess and downloads u [N_t][n] (and v for the wave equation, may be NULL).
+ * Synchronous. */
+stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f0, const double* u0,
+                                 const double* v0, double* u, double* v, stmg_solve_stats* stats);
+
+/* Number of kernels this context has launched so far (a captured V-cycle graph
+ * counts its kernel nodes at every replay).  Host-side counter, no device work. */
+stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count);
+
+/* Measurement hook: runs `reps` back-to-back launches of one kernel on the
+ * context's own stream over the level's work vectors (contents are
+ * overwritten) and returns the mean duration from CUDA events recorded on that
+ * stream.  kernel: STMG_KERNEL_APPLY (the operator kernel alone, no row
+ * initialisation), STMG_KERNEL_ASM (one additive Schwarz application) or
+ * STMG_KERNEL_VCYCLE (one whole V-cycle from level 0; level must be 0).  Synchronous. */
+enum { STMG_KERNEL_APPLY = 1, STMG_KERNEL_ASM = 2, STMG_KERNEL_VCYCLE = 3 };
+stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision, int reps, double* avg_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STMG_H */

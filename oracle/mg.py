@@ -21,8 +21,9 @@ Paper sections and the readings taken where it is silent:
     matrix = R_T S R_T^T of the global S (neighbour contributions included),
     solved exactly; u <- u + omega * sum_T R_T^T L_T^-1 R_T (f - S u).
   * relaxation (eq. relaxation): omega = 2 / (lambda_max + lambda_min), with the
-    extreme real parts of the Ritz values of a 20-step Arnoldi on S_l B_l from
-    the counter-based start vector synth.splitmix_uniform(n, key=level).
+    extreme real parts of the Ritz values of an Arnoldi process on S_l B_l with
+    min(20, number of unconstrained DoFs) steps from the counter-based start
+    vector synth.splitmix_uniform(n, key=level).
   * coarsest level: exact solve; no smoothing there (Algorithm stmg).
 """
 from __future__ import annotations
@@ -169,6 +170,8 @@ def arnoldi_ritz(matvec, v0: np.ndarray, m: int) -> np.ndarray:
 def estimate_omega(prob: SlabProblem, B: sp.csr_matrix, key: int, steps: int = 20) -> float:
     v0 = synth.splitmix_uniform(prob.n, key=key)
     v0[prob.bmask_full] = 0.0
+    # the Krylov space lives on the unconstrained DoFs: at most that many steps
+    steps = min(steps, int((~prob.bmask_full).sum()))
     ritz = arnoldi_ritz(lambda v: prob.S @ (B @ v), v0, steps)
     re = np.real(ritz)
     re = re[np.abs(ritz) > 1e-12]

@@ -1,0 +1,341 @@
+// Space-time cell-wise additive Schwarz smoother (eqs. vanka0, vanka).
+//
+// The block of space-time cell T = K x I_n holds all unconstrained nodes of the
+// spatial cell K for all N_t time DoFs of the slab.  Its matrix is the global
+// S = TA (x) A_h + TM (x) M_h restricted to those DoFs,
+//     L_T = TA (x) A_K + TM (x) M_K ,
+// A_K, M_K = global A_h, M_h restricted to the nodes of K (neighbour cells
+// contribute on shared faces, edges and vertices).  With TA^-1 TM = V diag(lambda) V^-1
+//     L_T^-1 = (V (x) I) diag_m (A_K + lambda_m M_K)^-1 (V^-1 TA^-1 (x) I),
+// so each cell stores N_t real planes of (p+1)^dim x (p+1)^dim numbers: one
+// plane per real lambda, two (re, im) per conjugate pair.  This is exact (up to
+// rounding) and takes N_t times less memory than the dense (N_t (p+1)^dim)^2 block.
+// Constrained (Dirichlet) nodes get identity rows/columns and zero residual.
+//
+// asm_apply: u += omega * sum_T R_T^T L_T^-1 R_T r, one warp-multiple per cell,
+// reading the planes column by column (coalesced); the additive sum over
+// overlapping cells uses atomic adds.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace stmg {
+
+namespace {
+
+template <int DIM, int N>
+struct Shape {
+  static constexpr int NB = DIM == 3 ? N * N * N : N * N;
+};
+
+__device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline double2 cinv(double2 a) {
+  const double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(256)
+asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const double* __restrict__ lam_re,
+                 const double* __restrict__ lam_im, int nreal, int ncplx, void* __restrict__ inv_out, int inv_prec) {
+  constexpr int NB = Shape<DIM, N>::NB;
+  constexpr int NQ = NB;
+  constexpr int NG = DIM == 3 ? 7 : 4;
+  const int nt = nreal + 2 * ncplx;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Aloc = reinterpret_cast<double*>(smem_raw);
+  double* Mloc = Aloc + NB * NB;
+  double2* C = reinterpret_cast<double2*>(Mloc + NB * NB);
+  double2* fcol = C + NB * NB;
+  int* ipiv = reinterpret_cast<int*>(fcol + NB);
+  __shared__ int s_piv;
+  const int64_t cell = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int p = g.p;
+  const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
+  const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+
+  for (int pr = tid; pr < NB * NB; pr += blockDim.x) { Aloc[pr] = 0.0; Mloc[pr] = 0.0; }
+  __syncthreads();
+  // global matrices restricted to this cell's nodes: sum over the cells of the 3^dim patch
+  const int noff = DIM == 3 ? 27 : 9;
+  for (int o = 0; o < noff; ++o) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
+    const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
+    if (nx < 0 || nx >= g.N || ny < 0 || ny >= g.N || nz < 0 || nz >= (DIM == 3 ? g.N : 1)) continue;
+    const int64_t nc = nx + (int64_t)g.N * (ny + (int64_t)g.N * nz);
+    const double* gc = geo + nc * NG * NQ;
+    for (int pr = tid; pr < NB * NB; pr += blockDim.x) {
+      const int a = pr / NB, b = pr % NB;
+      const int ax = a % N - ox * p, ay = (a / N) % N - oy * p, az = DIM == 3 ? a / (N * N) - oz * p : 0;
+      const int bx = b % N - ox * p, by = (b / N) % N - oy * p, bz = DIM == 3 ? b / (N * N) - oz * p : 0;
+      if (ax < 0 || ax > p || ay < 0 || ay > p || az < 0 || az > p) continue;
+      if (bx < 0 || bx > p || by < 0 || by > p || bz < 0 || bz > p) continue;
+      double sa = 0.0, sm = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        const int qx = q % N, qy = (q / N) % N, qz = DIM == 3 ? q / (N * N) : 0;
+        if (DIM == 3) {
+          const double va = lt.B[qx][ax] * lt.B[qy][ay] * lt.B[qz][az];
+          const double vb = lt.B[qx][bx] * lt.B[qy][by] * lt.B[qz][bz];
+          const double da0 = lt.Dn[qx][ax] * lt.B[qy][ay] * lt.B[qz][az];
+          const double da1 = lt.B[qx][ax] * lt.Dn[qy][ay] * lt.B[qz][az];
+          const double da2 = lt.B[qx][ax] * lt.B[qy][ay] * lt.Dn[qz][az];
+          const double db0 = lt.Dn[qx][bx] * lt.B[qy][by] * lt.B[qz][bz];
+          const double db1 = lt.B[qx][bx] * lt.Dn[qy][by] * lt.B[qz][bz];
+          const double db2 = lt.B[qx][bx] * lt.B[qy][by] * lt.Dn[qz][bz];
+          const double G00 = gc[0 * NQ + q], G01 = gc[1 * NQ + q], G02 = gc[2 * NQ + q];
+          const double G11 = gc[3 * NQ + q], G12 = gc[4 * NQ + q], G22 = gc[5 * NQ + q];
+          sa += da0 * (G00 * db0 + G01 * db1 + G02 * db2) + da1 * (G01 * db0 + G11 * db1 + G12 * db2) +
+                da2 * (G02 * db0 + G12 * db1 + G22 * db2);
+          sm += gc[6 * NQ + q] * va * vb;
+        } else {
+          const double va = lt.B[qx][ax] * lt.B[qy][ay];
+          const double vb = lt.B[qx][bx] * lt.B[qy][by];
+          const double da0 = lt.Dn[qx][ax] * lt.B[qy][ay], da1 = lt.B[qx][ax] * lt.Dn[qy][ay];
+          const double db0 = lt.Dn[qx][bx] * lt.B[qy][by], db1 = lt.B[qx][bx] * lt.Dn[qy][by];
+          const double G00 = gc[0 * NQ + q], G01 = gc[1 * NQ + q], G11 = gc[2 * NQ + q];
+          sa += da0 * (G00 * db0 + G01 * db1) + da1 * (G01 * db0 + G11 * db1);
+          sm += gc[3 * NQ + q] * va * vb;
+        }
+      }
+      Aloc[pr] += sa;
+      Mloc[pr] += sm;
+    }
+    __syncthreads();
+  }
+  // constrained local nodes
+  auto constrained = [&](int a) {
+    const int gx = cx * p + a % N, gy = cy * p + (a / N) % N;
+    bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+    if (DIM == 3) bnd = bnd || on_boundary(cz * p + a / (N * N), g.nn1);
+    return bnd;
+  };
+  int plane = 0;
+  for (int m = 0; m < nreal + ncplx; ++m) {
+    const double lr = lam_re[m], li = m < nreal ? 0.0 : lam_im[m];
+    for (int pr = tid; pr < NB * NB; pr += blockDim.x) {
+      const int a = pr / NB, b = pr % NB;
+      double2 v = make_double2(Aloc[pr] + lr * Mloc[pr], li * Mloc[pr]);
+      if (constrained(a) || constrained(b)) v = make_double2(a == b ? 1.0 : 0.0, 0.0);
+      C[pr] = v;
+    }
+    __syncthreads();
+    // Gauss-Jordan inversion in place with partial pivoting
+    for (int k = 0; k < NB; ++k) {
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + tid; r < NB; r += 32) {
+          const double2 c = C[r * NB + k];
+          const double mag = c.x * c.x + c.y * c.y;
+          if (mag > best) { best = mag; bi = r; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) { s_piv = bi; ipiv[k] = bi; }
+      }
+      __syncthreads();
+      const int pv = s_piv;
+      if (pv != k)
+        for (int jj = tid; jj < NB; jj += blockDim.x) {
+          const double2 t = C[k * NB + jj];
+          C[k * NB + jj] = C[pv * NB + jj];
+          C[pv * NB + jj] = t;
+        }
+      __syncthreads();
+      const double2 d = cinv(C[k * NB + k]);
+      for (int ii = tid; ii < NB; ii += blockDim.x) fcol[ii] = ii == k ? make_double2(0.0, 0.0) : C[ii * NB + k];
+      __syncthreads();
+      for (int jj = tid; jj < NB; jj += blockDim.x) C[k * NB + jj] = jj == k ? d : cmul(C[k * NB + jj], d);
+      __syncthreads();
+      for (int pr = tid; pr < NB * NB; pr += blockDim.x) {
+        const int ii = pr / NB, jj = pr % NB;
+        if (ii == k) continue;
+        const double2 base = jj == k ? make_double2(0.0, 0.0) : C[pr];
+        const double2 f = cmul(fcol[ii], C[k * NB + jj]);
+        C[pr] = make_double2(base.x - f.x, base.y - f.y);
+      }
+      __syncthreads();
+    }
+    for (int k = NB - 1; k >= 0; --k) {
+      const int pv = ipiv[k];
+      if (pv != k)
+        for (int ii = tid; ii < NB; ii += blockDim.x) {
+          const double2 t = C[ii * NB + k];
+          C[ii * NB + k] = C[ii * NB + pv];
+          C[ii * NB + pv] = t;
+        }
+      __syncthreads();
+    }
+    // store column-major planes: element (a, b) at b * NB + a
+    const int nplanes = m < nreal ? 1 : 2;
+    for (int pl = 0; pl < nplanes; ++pl) {
+      const int64_t base = ((int64_t)cell * nt + plane + pl) * NB * NB;
+      for (int pr = tid; pr < NB * NB; pr += blockDim.x) {
+        const int b = pr / NB, a = pr % NB;
+        const double2 v = C[a * NB + b];
+        const double x = pl == 0 ? v.x : v.y;
+        if (inv_prec == 0) reinterpret_cast<double*>(inv_out)[base + pr] = x;
+        else if (inv_prec == 1) reinterpret_cast<float*>(inv_out)[base + pr] = (float)x;
+        else reinterpret_cast<__nv_bfloat16*>(inv_out)[base + pr] = __float2bfloat16((float)x);
+      }
+    }
+    plane += nplanes;
+    __syncthreads();
+  }
+}
+
+template <int DIM, int N, int NT, typename T, typename TI>
+__global__ void __launch_bounds__(128)
+asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g, ModeTab<T> mt) {
+  constexpr int NB = Shape<DIM, N>::NB;
+  constexpr int TPC = (NB + 31) / 32 * 32;
+  constexpr int CPB = TPC >= 128 ? 1 : 128 / TPC;
+  __shared__ T sr[CPB][NT][NB];
+  const int slot = threadIdx.x / TPC;
+  const int a = threadIdx.x - slot * TPC;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + slot;
+  const bool active = cell < g.n_cells && a < NB;
+  const int64_t cc = cell < g.n_cells ? cell : 0;
+  const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N);
+  const int cz = DIM == 3 ? (int)(cc / ((int64_t)g.N * g.N)) : 0;
+  const int aa = a < NB ? a : 0;
+  const int gx = cx * g.p + aa % N, gy = cy * g.p + (aa / N) % N;
+  const int gz = DIM == 3 ? cz * g.p + aa / (N * N) : 0;
+  bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+  if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
+  const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+  const bool live = active && !bnd;
+  T rr[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
+  if (a < NB) {
+#pragma unroll
+    for (int m = 0; m < NT; ++m) {
+      // plane m: real mode m (m < nreal) or re/im of complex mode (m - nreal) / 2
+      const bool is_real = m < mt.nreal;
+      const int mode = is_real ? m : mt.nreal + (m - mt.nreal) / 2;
+      const bool im_part = !is_real && ((m - mt.nreal) & 1);
+      T v = 0;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[t];
+      sr[slot][m][a] = v;
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  const TI* ic = inv + (size_t)cell * NT * NB * NB;
+  T z[NT];
+#pragma unroll
+  for (int m = 0; m < NT; ++m) z[m] = 0;
+#pragma unroll
+  for (int m = 0; m < NT; ++m) {
+    if (m < mt.nreal) {
+      const TI* pl = ic + (size_t)m * NB * NB;
+      T acc = 0;
+#pragma unroll 9
+      for (int b = 0; b < NB; ++b) acc += (T)load_f(pl + b * NB + a) * sr[slot][m][b];
+      z[m] = acc;
+    } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+      const TI* pr_ = ic + (size_t)m * NB * NB;
+      const TI* pi_ = pr_ + NB * NB;
+      T zr = 0, zi = 0;
+#pragma unroll 9
+      for (int b = 0; b < NB; ++b) {
+        const T ir = (T)load_f(pr_ + b * NB + a), ii = (T)load_f(pi_ + b * NB + a);
+        const T sre = sr[slot][m][b], sim = sr[slot][m + 1][b];
+        zr += ir * sre - ii * sim;
+        zi += ir * sim + ii * sre;
+      }
+      z[m] = zr;
+      z[m + 1] = zi;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    T o = 0;
+#pragma unroll
+    for (int m = 0; m < NT; ++m) {
+      if (m < mt.nreal) {
+        o += mt.Vr[t][m] * z[m];
+      } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+        const int mode = mt.nreal + (m - mt.nreal) / 2;
+        o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
+      }
+    }
+    atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
+  }
+}
+
+template <int DIM, int N>
+cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, const double* lr, const double* li,
+                    int nreal, int ncplx, void* inv, int inv_prec, cudaStream_t s) {
+  constexpr int NB = Shape<DIM, N>::NB;
+  const size_t smem = (size_t)2 * NB * NB * sizeof(double) + (size_t)NB * NB * sizeof(double2) +
+                      NB * sizeof(double2) + NB * sizeof(int);
+  auto k = asm_setup_kernel<DIM, N>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)g.n_cells, 256, smem, s>>>(g, geo64, lt, lr, li, nreal, ncplx, inv, inv_prec);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NT, typename T, typename TI>
+cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s) {
+  constexpr int NB = Shape<DIM, N>::NB;
+  constexpr int TPC = (NB + 31) / 32 * 32;
+  constexpr int CPB = TPC >= 128 ? 1 : 128 / TPC;
+  const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
+  asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, CPB * TPC, 0, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
+                             const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
+                             int inv_prec, cudaStream_t s) {
+  (void)nt;
+  if (dim == 3) {
+    if (n == 2) return setup_t<3, 2>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 3) return setup_t<3, 3>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 4) return setup_t<3, 4>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+  } else {
+    if (n == 2) return setup_t<2, 2>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 3) return setup_t<2, 3>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 4) return setup_t<2, 4>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 5) return setup_t<2, 5>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+#define STMG_ASM_CASE(DIM, N, NT)                                                                  \
+  if (dim == DIM && n == N && nt == NT) {                                                          \
+    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, s);                 \
+    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, s);                  \
+    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, s);                             \
+  }
+
+template <typename T>
+cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
+                             const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s) {
+  STMG_ASM_CASE(3, 2, 1) STMG_ASM_CASE(3, 2, 2) STMG_ASM_CASE(3, 2, 3) STMG_ASM_CASE(3, 2, 4)
+  STMG_ASM_CASE(3, 3, 1) STMG_ASM_CASE(3, 3, 2) STMG_ASM_CASE(3, 3, 3) STMG_ASM_CASE(3, 3, 4)
+  STMG_ASM_CASE(3, 4, 1) STMG_ASM_CASE(3, 4, 2) STMG_ASM_CASE(3, 4, 3) STMG_ASM_CASE(3, 4, 4)
+  STMG_ASM_CASE(2, 2, 1) STMG_ASM_CASE(2, 2, 2) STMG_ASM_CASE(2, 2, 3) STMG_ASM_CASE(2, 2, 4)
+  STMG_ASM_CASE(2, 3, 1) STMG_ASM_CASE(2, 3, 2) STMG_ASM_CASE(2, 3, 3) STMG_ASM_CASE(2, 3, 4)
+  STMG_ASM_CASE(2, 4, 1) STMG_ASM_CASE(2, 4, 2) STMG_ASM_CASE(2, 4, 3) STMG_ASM_CASE(2, 4, 4)
+  STMG_ASM_CASE(2, 5, 1) STMG_ASM_CASE(2, 5, 2) STMG_ASM_CASE(2, 5, 3) STMG_ASM_CASE(2, 5, 4)
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_asm_apply<float>(int, int, int, const float*, float*, const void*, int, const GridDesc&,
+                                             const ModeTab<float>&, cudaStream_t);
+template cudaError_t launch_asm_apply<double>(int, int, int, const double*, double*, const void*, int,
+                                              const GridDesc&, const ModeTab<double>&, cudaStream_t);
+
+}  // namespace stmg

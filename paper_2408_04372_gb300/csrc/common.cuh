@@ -1,0 +1,59 @@
+// Shared device-side definitions of the STMG library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace stmg {
+
+constexpr int kMaxN = 5;    // p <= 4
+constexpr int kMaxNT = 4;   // time DoFs per slab
+
+// Tables of one operator evaluation, passed by value (constant bank).
+//   B[q][i]  : 1D nodal (Gauss-Lobatto) basis i at Gauss point q
+//   D[q][r]  : derivative at Gauss point q of the Lagrange basis through the Gauss points (collocation)
+//   TA, TM   : time matrices of S = TA (x) A_h + TM (x) M_h
+template <typename T>
+struct OpTab {
+  T B[kMaxN][kMaxN];
+  T D[kMaxN][kMaxN];
+  T TA[kMaxNT][kMaxNT];
+  T TM[kMaxNT][kMaxNT];
+  T sign;
+};
+
+// Structured-grid description of one level.
+struct GridDesc {
+  int dim;
+  int N;          // cells per direction
+  int p;
+  int nn1;        // nodes per direction = p*N + 1
+  int64_t n_nodes;
+  int64_t n_cells;
+};
+
+__host__ __device__ inline bool on_boundary(int g, int nn1) { return g == 0 || g == nn1 - 1; }
+
+// Time diagonalisation of the local space-time matrices for the additive
+// Schwarz smoother: modes m = 0..nreal-1 are real, then ncplx complex modes
+// (one representative per conjugate pair).  W = V^-1 TA^-1 (rows = modes),
+// V[t][m] (columns = eigenvectors).
+template <typename T>
+struct ModeTab {
+  int nreal, ncplx;
+  T Wr[kMaxNT][kMaxNT], Wi[kMaxNT][kMaxNT];
+  T Vr[kMaxNT][kMaxNT], Vi[kMaxNT][kMaxNT];
+  T omega;
+};
+
+template <typename T> __device__ inline T to_t(float v);
+template <> __device__ inline float to_t<float>(float v) { return v; }
+template <> __device__ inline double to_t<double>(float v) { return (double)v; }
+
+template <typename T> __device__ inline T load_as(const T* p) { return *p; }
+__device__ inline float load_f(const float* p) { return __ldg(p); }
+__device__ inline double load_f(const double* p) { return __ldg(p); }
+__device__ inline float load_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+}  // namespace stmg

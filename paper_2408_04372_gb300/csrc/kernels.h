@@ -1,0 +1,81 @@
+// Host-callable launchers of the STMG device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace stmg {
+
+// ---- operator (apply.cu) ----
+template <typename T>
+cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo, const GridDesc& g,
+                         const OpTab<T>& tab, int mask_input, cudaStream_t s);
+// mode 0: y = constrained ? x : 0 ; mode 1: y = constrained ? f - x : f ; mode 2: y = 0
+template <typename T>
+cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, int nt, int mode, cudaStream_t s);
+
+// ---- geometry (setup.cu) ----
+// geo64 [cell][7 or 4][nq^dim]: rho w |J| J^-1 J^-T (upper triangle) and w |J|
+cudaError_t launch_geometry(const GridDesc& g, const double* vertices, const double* rho_qp, const double* xq,
+                            const double* wq, double* geo64, float* geo32, cudaStream_t s);
+
+// ---- additive Schwarz (asm.cu) ----
+struct LocalTab {        // 1D tables of the nodal basis at Gauss points (setup in FP64)
+  double B[kMaxN][kMaxN];   // value of node basis i at Gauss point q: B[q][i]
+  double Dn[kMaxN][kMaxN];  // derivative of node basis i at Gauss point q
+};
+// Builds, per cell and time mode, the inverse of (A_K + lambda_m M_K) with A_K, M_K the
+// global matrices restricted to the cell's nodes; writes planes of the storage type.
+cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
+                             const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
+                             int inv_prec, cudaStream_t s);
+template <typename T>
+cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
+                             const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s);
+
+// ---- transfers (transfer.cu) ----
+struct Transfer1D {
+  int width_p;           // coarse window width (pc + 1)
+  int width_r;           // max fine entries per coarse node
+  const int* p_start;    // [nn1_f]
+  const double* p_w;     // [nn1_f][width_p]
+  const int* r_idx;      // [nn1_c][width_r]  (fine index, -1 padding)
+  const double* r_w;     // [nn1_c][width_r]
+};
+template <typename T>
+cudaError_t launch_prolong_space_add(T* uf, const T* ec, const GridDesc& gf, const GridDesc& gc, int nt,
+                                     const Transfer1D& t, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict_space(T* rc, const T* rf, const GridDesc& gf, const GridDesc& gc, int nt,
+                                  const Transfer1D& t, cudaStream_t s);
+struct TimeTransfer { int ntf, ntc; double P[kMaxNT][kMaxNT]; };
+template <typename T>
+cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const TimeTransfer& t, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const TimeTransfer& t, cudaStream_t s);
+
+// ---- vectors, reductions, coarse solve (vec.cu) ----
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s);
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
+cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64_t n, cudaStream_t s);
+// partial[b][j] = sum over the block's range of V[j] . w (j < nv), plus partial[b][nv] = w.w if with_norm
+cudaError_t launch_multidot(const double* const* V, int nv, const double* w, int64_t n, int with_norm,
+                            double* partial, int nblocks, double* out, cudaStream_t s);
+// w -= sum_j h[j] V[j]  (h on the device)
+cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int nv, double sign,
+                              int64_t n, cudaStream_t s);
+cudaError_t launch_broadcast_time(const double* u0, double* u, int nt, int64_t n_nodes, cudaStream_t s);
+// y[i][node] = sum_j C[i][j] x_j[node] over nin vectors (time-only mixing)
+cudaError_t launch_time_mix(const double* const* xs, int nin, const double* C, int nout, double* y,
+                            int64_t n_nodes, int accumulate, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(const T* f, T* u, const T* inv, const int64_t* map, int n, int64_t total,
+                                cudaStream_t s);
+cudaError_t launch_zero_constrained(double* y, const GridDesc& g, int nt, cudaStream_t s);
+int multidot_blocks();
+
+}  // namespace stmg

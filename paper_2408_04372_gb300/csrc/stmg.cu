@@ -1,0 +1,1218 @@
+// Host side of libstmg: context, multigrid hierarchy, V-cycle, FGMRES and the C ABI (include/stmg.h).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/stmg.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "tables.h"
+
+using namespace stmg;
+
+namespace {
+
+struct Level {
+  int dim = 3, p = 1, n = 2, N = 2, k = 0, nt = 1;
+  GridDesc g{};
+  std::vector<double> vertices;   // host (N+1)^dim x dim
+  std::vector<double> rho_qp;     // host cells x (p+1)^dim
+  double* geo64 = nullptr;
+  float* geo32 = nullptr;
+  SlabCoeffs sc;
+  OpTab<double> tab64{};
+  OpTab<float> tab32{};
+  LocalTab lt{};
+  // smoother
+  int nreal = 0, ncplx = 0;
+  ModeTab<double> mt64{};
+  ModeTab<float> mt32{};
+  void* inv = nullptr;
+  int inv_prec = 1;
+  double omega = 1.0;
+  // work vectors
+  double *f64 = nullptr, *u64 = nullptr, *r64 = nullptr;
+  float *f32 = nullptr, *u32 = nullptr, *r32 = nullptr;
+  // transfer into this level from levels[l+1] (tkind 1 space, 2 time, 0 none)
+  int tkind = 0;
+  Transfer1D tr{};
+  TimeTransfer tt{};
+  // coarsest level dense solve
+  int n_coarse = 0;
+  int64_t* cmap = nullptr;
+  double* cinv64 = nullptr;
+  float* cinv32 = nullptr;
+  int64_t size() const { return (int64_t)nt * g.n_nodes; }
+};
+
+}  // namespace
+
+struct stmg_ctx {
+  cudaStream_t stream = nullptr;       // private stream (graph capture needs a non-legacy stream)
+  cudaStream_t user_stream = nullptr;  // caller's stream; every call is ordered after and before it
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int dim = 3, pde = 0, scheme = 0;
+  double tau = 1.0;
+  stmg_options opt{};
+  std::vector<Level> levels;
+  std::string err;
+  std::vector<void*> allocations;
+  // FGMRES workspace
+  int m = 30;
+  int nvec = 0;
+  double* V = nullptr;   // (nvec) vectors
+  double* Z = nullptr;   // (m) vectors
+  double* partial = nullptr;
+  double* dsm = nullptr;  // device scalars [0..nvec+8) h1, [128..) h2, [256..) outputs
+  double* hsm = nullptr;  // pinned host mirror
+  double* tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* rhs_buf = nullptr;
+  double* u_buf = nullptr;
+  cudaGraphExec_t graph32 = nullptr, graph64 = nullptr;
+  int64_t graph32_kernels = 0, graph64_kernels = 0;
+  bool warmed32 = false, warmed64 = false;
+  int64_t launches = 0;  // kernels issued by this context (graph replays count their kernel nodes)
+};
+
+namespace {
+
+#define CK(...)                                                                   \
+  do {                                                                            \
+    cudaError_t e_ = (__VA_ARGS__);                                               \
+    if (e_ != cudaSuccess) {                                                      \
+      ctx->err = std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_);       \
+      return STMG_ERR_CUDA;                                                       \
+    }                                                                             \
+  } while (0)
+
+#define CKS(...)                                                                  \
+  do {                                                                            \
+    stmg_status s_ = (__VA_ARGS__);                                               \
+    if (s_ != STMG_OK) return s_;                                                 \
+  } while (0)
+
+template <typename T>
+stmg_status dev_alloc(stmg_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STMG_ERR_OOM : STMG_ERR_CUDA;
+  }
+  ctx->allocations.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return STMG_OK;
+}
+
+stmg_status invalid(stmg_ctx* ctx, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return STMG_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- level setup
+
+struct Spec { int p, N, k; };
+
+std::vector<Spec> level_sequence(int p, int N, int k, int scheme) {
+  std::vector<Spec> s{{p, N, k}};
+  while (s.back().p > 1) s.push_back({s.back().p - 1, s.back().N, s.back().k});
+  while (s.back().N % 2 == 0 && s.back().N / 2 >= 2) s.push_back({s.back().p, s.back().N / 2, s.back().k});
+  const int kmin = scheme == STMG_DG ? 0 : 1;
+  while (s.back().k > kmin) s.push_back({s.back().p, s.back().N, s.back().k - 1});
+  return s;
+}
+
+void fill_tables(Level& L) {
+  std::vector<double> xn = space_nodes(L.p), xq, wq;
+  gauss_legendre(L.n, xq, wq);
+  OpTab<double> t{};
+  for (int q = 0; q < L.n; ++q)
+    for (int i = 0; i < L.n; ++i) {
+      t.B[q][i] = lagrange(xn, i, xq[q]);
+      t.D[q][i] = lagrange_deriv(xq, i, xq[q]);
+      L.lt.B[q][i] = t.B[q][i];
+      L.lt.Dn[q][i] = lagrange_deriv(xn, i, xq[q]);
+    }
+  for (int i = 0; i < L.nt; ++i)
+    for (int j = 0; j < L.nt; ++j) {
+      t.TA[i][j] = L.sc.TA[i * L.nt + j];
+      t.TM[i][j] = L.sc.TM[i * L.nt + j];
+    }
+  t.sign = 1.0;
+  L.tab64 = t;
+  OpTab<float> f{};
+  for (int a = 0; a < kMaxN; ++a)
+    for (int b = 0; b < kMaxN; ++b) { f.B[a][b] = (float)t.B[a][b]; f.D[a][b] = (float)t.D[a][b]; }
+  for (int a = 0; a < kMaxNT; ++a)
+    for (int b = 0; b < kMaxNT; ++b) { f.TA[a][b] = (float)t.TA[a][b]; f.TM[a][b] = (float)t.TM[a][b]; }
+  f.sign = 1.0f;
+  L.tab32 = f;
+}
+
+template <typename T> OpTab<T>& tab_of(Level& L);
+template <> OpTab<double>& tab_of<double>(Level& L) { return L.tab64; }
+template <> OpTab<float>& tab_of<float>(Level& L) { return L.tab32; }
+template <typename T> const T* geo_of(const Level& L);
+template <> const double* geo_of<double>(const Level& L) { return L.geo64; }
+template <> const float* geo_of<float>(const Level& L) { return L.geo32; }
+template <typename T> ModeTab<T>& mt_of(Level& L);
+template <> ModeTab<double>& mt_of<double>(Level& L) { return L.mt64; }
+template <> ModeTab<float>& mt_of<float>(Level& L) { return L.mt32; }
+template <typename T> T* fv(Level& L);
+template <> double* fv<double>(Level& L) { return L.f64; }
+template <> float* fv<float>(Level& L) { return L.f32; }
+template <typename T> T* uv(Level& L);
+template <> double* uv<double>(Level& L) { return L.u64; }
+template <> float* uv<float>(Level& L) { return L.u32; }
+template <typename T> T* rv(Level& L);
+template <> double* rv<double>(Level& L) { return L.r64; }
+template <> float* rv<float>(Level& L) { return L.r32; }
+template <typename T> const T* cinv_of(const Level& L);
+template <> const double* cinv_of<double>(const Level& L) { return L.cinv64; }
+template <> const float* cinv_of<float>(const Level& L) { return L.cinv32; }
+
+// y = S x (identity on constrained rows)
+template <typename T>
+stmg_status op_apply(stmg_ctx* ctx, Level& L, const T* x, T* y) {
+  CK(launch_init_rows<T>(y, nullptr, x, L.g, L.nt, 0, ctx->stream));
+  ctx->launches += 2;
+  OpTab<T> t = tab_of<T>(L);
+  t.sign = T(1);
+  CK(launch_apply<T>(L.dim, L.n, L.nt, x, y, geo_of<T>(L), L.g, t, 1, ctx->stream));
+  return STMG_OK;
+}
+
+// r = f - S u
+template <typename T>
+stmg_status op_residual(stmg_ctx* ctx, Level& L, const T* f, const T* u, T* r) {
+  CK(launch_init_rows<T>(r, f, u, L.g, L.nt, 1, ctx->stream));
+  ctx->launches += 2;
+  OpTab<T> t = tab_of<T>(L);
+  t.sign = T(-1);
+  CK(launch_apply<T>(L.dim, L.n, L.nt, u, r, geo_of<T>(L), L.g, t, 1, ctx->stream));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega) {
+  ModeTab<T> mt = mt_of<T>(L);
+  mt.omega = (T)omega;
+  ctx->launches += 1;
+  CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, ctx->stream));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status op_smooth(stmg_ctx* ctx, int l, int sweeps, const T* f, T* u, T* r) {
+  Level& L = ctx->levels[l];
+  for (int s = 0; s < sweeps; ++s) {
+    CKS(op_residual<T>(ctx, L, f, u, r));
+    CKS(op_asm<T>(ctx, L, r, u, L.omega));
+  }
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc) {
+  Level& F = ctx->levels[l];
+  Level& C = ctx->levels[l + 1];
+  ctx->launches += 1;
+  if (F.tkind == 1) CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, ctx->stream));
+  else CK(launch_restrict_time<T>(rc, rf, F.g, F.tt, ctx->stream));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf) {
+  Level& F = ctx->levels[l];
+  Level& C = ctx->levels[l + 1];
+  ctx->launches += 1;
+  if (F.tkind == 1) CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, ctx->stream));
+  else CK(launch_prolong_time_add<T>(uf, ec, F.g, F.tt, ctx->stream));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status coarse_solve(stmg_ctx* ctx, Level& L, const T* f, T* u) {
+  CK(cudaMemsetAsync(u, 0, sizeof(T) * L.size(), ctx->stream));
+  CK(launch_coarse_solve<T>(f, u, cinv_of<T>(L), L.cmap, L.n_coarse, L.size(), ctx->stream));
+  ctx->launches += 1;
+  return STMG_OK;
+}
+
+// Algorithm stmg: V-cycle with zero initial guess on level l, f_l -> u_l
+template <typename T>
+stmg_status vcycle_level(stmg_ctx* ctx, int l) {
+  Level& L = ctx->levels[l];
+  T* f = fv<T>(L);
+  T* u = uv<T>(L);
+  T* r = rv<T>(L);
+  if (l == (int)ctx->levels.size() - 1) return coarse_solve<T>(ctx, L, f, u);
+  CK(cudaMemsetAsync(u, 0, sizeof(T) * L.size(), ctx->stream));
+  for (int s = 0; s < ctx->opt.nu_pre; ++s) {
+    if (s == 0) {
+      CKS(op_asm<T>(ctx, L, f, u, L.omega));  // zero guess: residual = f
+    } else {
+      CKS(op_residual<T>(ctx, L, f, u, r));
+      CKS(op_asm<T>(ctx, L, r, u, L.omega));
+    }
+  }
+  const T* res = f;
+  if (ctx->opt.nu_pre > 0) {
+    CKS(op_residual<T>(ctx, L, f, u, r));
+    res = r;
+  }
+  Level& Cl = ctx->levels[l + 1];
+  CKS(op_restrict<T>(ctx, l, res, fv<T>(Cl)));
+  CKS(vcycle_level<T>(ctx, l + 1));
+  CKS(op_prolongate_add<T>(ctx, l, uv<T>(Cl), u));
+  CKS(op_smooth<T>(ctx, l, ctx->opt.nu_post, f, u, r));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status run_vcycle(stmg_ctx* ctx) {
+  bool& warmed = sizeof(T) == 4 ? ctx->warmed32 : ctx->warmed64;
+  cudaGraphExec_t& ge = sizeof(T) == 4 ? ctx->graph32 : ctx->graph64;
+  if (!warmed) {  // first call runs eagerly (sets kernel attributes), later calls replay a graph
+    warmed = true;
+    return vcycle_level<T>(ctx, 0);
+  }
+  if (!ge) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t saved = ctx->launches;
+    stmg_status st = vcycle_level<T>(ctx, 0);
+    ctx->launches = saved;
+    const int64_t before = ctx->launches;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != STMG_OK) return st;
+    if (e != cudaSuccess) { ctx->err = std::string("capture: ") + cudaGetErrorString(e); return STMG_ERR_CUDA; }
+    (void)before;
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int64_t nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      if (ty == cudaGraphNodeTypeKernel) ++nk;
+    }
+    (sizeof(T) == 4 ? ctx->graph32_kernels : ctx->graph64_kernels) = nk;
+    e = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { ctx->err = std::string("instantiate: ") + cudaGetErrorString(e); ge = nullptr; return STMG_ERR_CUDA; }
+  }
+  CK(cudaGraphLaunch(ge, ctx->stream));
+  ctx->launches += sizeof(T) == 4 ? ctx->graph32_kernels : ctx->graph64_kernels;
+  return STMG_OK;
+}
+
+// splitmix64 counter-based generator (Steele, Lea, Flood 2014)
+uint64_t splitmix64(uint64_t i) {
+  uint64_t z = i + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+bool node_constrained(const Level& L, int64_t node) {
+  const int nn1 = L.g.nn1;
+  const int gx = (int)(node % nn1);
+  const int64_t rest = node / nn1;
+  if (gx == 0 || gx == nn1 - 1) return true;
+  if (L.dim == 3) {
+    const int gy = (int)(rest % nn1), gz = (int)(rest / nn1);
+    return gy == 0 || gy == nn1 - 1 || gz == 0 || gz == nn1 - 1;
+  }
+  return rest == 0 || rest == nn1 - 1;
+}
+
+// device multi-dot helper: out[0..nv) = V_j . w (+ w.w at nv)
+stmg_status dots(stmg_ctx* ctx, const double* const* V, int nv, const double* w, int64_t n, int with_norm, double* out) {
+  CK(launch_multidot(V, nv, w, n, with_norm, ctx->partial, multidot_blocks(), out, ctx->stream));
+  return STMG_OK;
+}
+
+__global__ void finalize_arnoldi_kernel(const double* h1, const double* h2, int nv, const double* nrm2, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int j = 0; j < nv; ++j) out[j] = h1[j] + h2[j];
+    const double hn = sqrt(fmax(nrm2[0], 0.0));
+    out[nv] = hn;
+    out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+  }
+}
+
+// One Arnoldi/FGMRES orthogonalisation step (classical Gram-Schmidt, twice):
+// w <- w - V h, h = [V^T w]_1 + [V^T w]_2 ; hn = ||w|| ; w <- w / hn.  Host gets h (nv) and hn.
+stmg_status orthogonalise(stmg_ctx* ctx, const double* const* Vp, int nv, double* w, int64_t n, std::vector<double>& h,
+                          double& hn) {
+  double* d_h1 = ctx->dsm;
+  double* d_h2 = ctx->dsm + 128;
+  double* d_n = ctx->dsm + 256;
+  double* d_out = ctx->dsm + 384;
+  CKS(dots(ctx, Vp, nv, w, n, 0, d_h1));
+  CK(launch_multi_axpy(w, Vp, d_h1, nv, -1.0, n, ctx->stream));
+  CKS(dots(ctx, Vp, nv, w, n, 0, d_h2));
+  CK(launch_multi_axpy(w, Vp, d_h2, nv, -1.0, n, ctx->stream));
+  CKS(dots(ctx, nullptr, 0, w, n, 1, d_n));
+  finalize_arnoldi_kernel<<<1, 1, 0, ctx->stream>>>(d_h1, d_h2, nv, d_n, d_out);
+  ctx->launches += 10;
+  CK(cudaGetLastError());
+  CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  h.assign(ctx->hsm, ctx->hsm + nv);
+  hn = ctx->hsm[nv];
+  return STMG_OK;
+}
+
+stmg_status estimate_omega(stmg_ctx* ctx, int l) {
+  Level& L = ctx->levels[l];
+  const int64_t n = L.size();
+  int64_t n_free = 0;
+  for (int64_t node = 0; node < L.g.n_nodes; ++node) n_free += node_constrained(L, node) ? 0 : 1;
+  n_free *= L.nt;
+  // the Krylov space lives on the unconstrained DoFs: at most that many steps
+  const int steps = (int)std::min<int64_t>(20, n_free);
+  std::vector<double> v0(n);
+  const uint64_t base = (uint64_t)l << 32;
+  double nr = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double x = 2.0 * ((double)(splitmix64(base + (uint64_t)i) >> 11) * 0x1.0p-53) - 1.0;
+    if (node_constrained(L, i % L.g.n_nodes)) x = 0.0;
+    v0[i] = x;
+    nr += x * x;
+  }
+  nr = std::sqrt(nr);
+  for (auto& x : v0) x /= nr;
+  std::vector<double*> V(steps + 1);
+  for (int j = 0; j <= steps; ++j) V[j] = ctx->V + (size_t)j * n;
+  CK(cudaMemcpyAsync(V[0], v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<double> H((steps + 1) * steps, 0.0);
+  int m = steps;
+  double* z = ctx->Z;
+  for (int j = 0; j < steps; ++j) {
+    CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
+    CKS(op_asm<double>(ctx, L, V[j], z, 1.0));
+    CKS(op_apply<double>(ctx, L, z, V[j + 1]));
+    std::vector<double> h;
+    double hn = 0.0;
+    std::vector<const double*> Vc(V.begin(), V.begin() + j + 1);
+    CKS(orthogonalise(ctx, Vc.data(), j + 1, V[j + 1], n, h, hn));
+    for (int i = 0; i <= j; ++i) H[i * steps + j] = h[i];
+    H[(j + 1) * steps + j] = hn;
+    if (hn <= 1e-14 * std::fabs(H[j * steps + j]) + 1e-300) { m = j + 1; break; }
+  }
+  std::vector<double> Hm(m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) Hm[i * m + j] = H[i * steps + j];
+  std::vector<cplx> ev = eigenvalues(m, Hm);
+  double lmax = -1e300, lmin = 1e300;
+  for (auto& e : ev) {
+    if (std::abs(e) <= 1e-12) continue;
+    lmax = std::max(lmax, e.real());
+    lmin = std::min(lmin, e.real());
+  }
+  if (!(lmax + lmin > 0.0) || !std::isfinite(lmax + lmin)) {
+    ctx->err = "relaxation estimate failed on level " + std::to_string(l);
+    return STMG_ERR_INTERNAL;
+  }
+  L.omega = 2.0 / (lmax + lmin);
+  return STMG_OK;
+}
+
+stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
+  const int nt = L.nt;
+  // T = TA^-1 TM, eigen-decomposition
+  std::vector<double> TAi = L.sc.TA;
+  if (!invert(nt, TAi)) { ctx->err = "singular time matrix"; return STMG_ERR_INTERNAL; }
+  std::vector<double> T(nt * nt, 0.0);
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j < nt; ++j)
+      for (int l = 0; l < nt; ++l) T[i * nt + j] += TAi[i * nt + l] * L.sc.TM[l * nt + j];
+  std::vector<cplx> lam, V;
+  if (!eigen_decompose(nt, T, lam, V)) { ctx->err = "time matrix not diagonalisable"; return STMG_ERR_INTERNAL; }
+  std::vector<cplx> Vinv = V;
+  invert_complex(nt, Vinv);
+  // representatives: real modes, then one of each conjugate pair (Im > 0)
+  std::vector<int> reps;
+  for (int m = 0; m < nt; ++m) if (lam[m].imag() == 0.0) reps.push_back(m);
+  L.nreal = (int)reps.size();
+  for (int m = 0; m < nt; ++m) if (lam[m].imag() > 0.0) reps.push_back(m);
+  L.ncplx = (int)reps.size() - L.nreal;
+  if (L.nreal + 2 * L.ncplx != nt) { ctx->err = "unpaired complex time eigenvalue"; return STMG_ERR_INTERNAL; }
+  ModeTab<double> mt{};
+  mt.nreal = L.nreal; mt.ncplx = L.ncplx;
+  std::vector<double> lr, li;
+  for (size_t r = 0; r < reps.size(); ++r) {
+    const int m = reps[r];
+    lr.push_back(lam[m].real());
+    li.push_back(lam[m].imag());
+    for (int t = 0; t < nt; ++t) {
+      cplx w = 0.0;  // W = V^-1 TA^-1
+      for (int l = 0; l < nt; ++l) w += Vinv[m * nt + l] * TAi[l * nt + t];
+      mt.Wr[r][t] = w.real(); mt.Wi[r][t] = w.imag();
+      mt.Vr[t][r] = V[t * nt + m].real(); mt.Vi[t][r] = V[t * nt + m].imag();
+    }
+  }
+  mt.omega = 1.0;
+  L.mt64 = mt;
+  ModeTab<float> mf{};
+  mf.nreal = mt.nreal; mf.ncplx = mt.ncplx;
+  for (int a = 0; a < kMaxNT; ++a)
+    for (int b = 0; b < kMaxNT; ++b) {
+      mf.Wr[a][b] = (float)mt.Wr[a][b]; mf.Wi[a][b] = (float)mt.Wi[a][b];
+      mf.Vr[a][b] = (float)mt.Vr[a][b]; mf.Vi[a][b] = (float)mt.Vi[a][b];
+    }
+  mf.omega = 1.0f;
+  L.mt32 = mf;
+  const int NB = L.dim == 3 ? L.n * L.n * L.n : L.n * L.n;
+  if (L.dim == 3 && L.n > 4) {
+    ctx->err = "dense additive Schwarz setup supports p <= 3 in 3D";
+    return STMG_ERR_UNSUPPORTED;
+  }
+  const size_t esz = L.inv_prec == 0 ? 8 : L.inv_prec == 1 ? 4 : 2;
+  const size_t count = (size_t)L.g.n_cells * nt * NB * NB;
+  void* inv = nullptr;
+  cudaError_t e = cudaMalloc(&inv, count * esz);
+  if (e != cudaSuccess) { ctx->err = std::string("cudaMalloc inverses: ") + cudaGetErrorString(e); return STMG_ERR_OOM; }
+  ctx->allocations.push_back(inv);
+  L.inv = inv;
+  double* dl = nullptr;
+  CKS(dev_alloc(ctx, &dl, 2 * kMaxNT));
+  std::vector<double> lam_host(2 * kMaxNT, 0.0);
+  for (size_t r = 0; r < lr.size(); ++r) { lam_host[r] = lr[r]; lam_host[kMaxNT + r] = li[r]; }
+  CK(cudaMemcpyAsync(dl, lam_host.data(), sizeof(double) * 2 * kMaxNT, cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_asm_setup(L.dim, L.n, nt, L.g, L.geo64, L.lt, dl, dl + kMaxNT, L.nreal, L.ncplx, L.inv, L.inv_prec,
+                      ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return STMG_OK;
+}
+
+stmg_status setup_transfer(stmg_ctx* ctx, Level& F, const Level& C) {
+  if (F.k != C.k) {
+    F.tkind = 2;
+    std::vector<double> P = time_prolongation(ctx->scheme, F.k, C.k);
+    F.tt.ntf = F.nt; F.tt.ntc = C.nt;
+    for (int i = 0; i < F.nt; ++i)
+      for (int j = 0; j < C.nt; ++j) F.tt.P[i][j] = P[i * C.nt + j];
+    return STMG_OK;
+  }
+  F.tkind = 1;
+  std::vector<int> start;
+  std::vector<double> w;
+  prolongation_1d(F.p, F.N, C.p, C.N, start, w);
+  const int W = C.p + 1;
+  const int nf = F.g.nn1, nc = C.g.nn1;
+  std::vector<std::vector<std::pair<int, double>>> lists(nc);
+  for (int gf = 0; gf < nf; ++gf)
+    for (int b = 0; b < W; ++b) {
+      const double v = w[(size_t)gf * W + b];
+      if (v != 0.0) lists[start[gf] + b].push_back({gf, v});
+    }
+  int R = 1;
+  for (auto& l : lists) R = std::max<int>(R, (int)l.size());
+  std::vector<int> ridx((size_t)nc * R, -1);
+  std::vector<double> rw((size_t)nc * R, 0.0);
+  for (int G = 0; G < nc; ++G)
+    for (size_t c = 0; c < lists[G].size(); ++c) { ridx[(size_t)G * R + c] = lists[G][c].first; rw[(size_t)G * R + c] = lists[G][c].second; }
+  int *d_start = nullptr, *d_ridx = nullptr;
+  double *d_w = nullptr, *d_rw = nullptr;
+  CKS(dev_alloc(ctx, &d_start, nf));
+  CKS(dev_alloc(ctx, &d_w, (size_t)nf * W));
+  CKS(dev_alloc(ctx, &d_ridx, (size_t)nc * R));
+  CKS(dev_alloc(ctx, &d_rw, (size_t)nc * R));
+  CK(cudaMemcpy(d_start, start.data(), sizeof(int) * nf, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_w, w.data(), sizeof(double) * nf * W, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_ridx, ridx.data(), sizeof(int) * nc * R, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_rw, rw.data(), sizeof(double) * nc * R, cudaMemcpyHostToDevice));
+  F.tr.width_p = W;
+  F.tr.width_r = R;
+  F.tr.p_start = d_start;
+  F.tr.p_w = d_w;
+  F.tr.r_idx = d_ridx;
+  F.tr.r_w = d_rw;
+  return STMG_OK;
+}
+
+stmg_status setup_coarse(stmg_ctx* ctx, Level& L) {
+  std::vector<int64_t> map;
+  for (int t = 0; t < L.nt; ++t)
+    for (int64_t node = 0; node < L.g.n_nodes; ++node)
+      if (!node_constrained(L, node)) map.push_back((int64_t)t * L.g.n_nodes + node);
+  const int n = (int)map.size();
+  if (n > 4096) { ctx->err = "coarsest level too large for the dense solver"; return STMG_ERR_UNSUPPORTED; }
+  L.n_coarse = n;
+  const int64_t tot = L.size();
+  double *x = nullptr, *y = nullptr;
+  CKS(dev_alloc(ctx, &x, tot));
+  CKS(dev_alloc(ctx, &y, tot));
+  std::vector<double> S((size_t)n * n), col(tot);
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * tot, ctx->stream));
+  const double one = 1.0, zero = 0.0;
+  for (int j = 0; j < n; ++j) {
+    CK(cudaMemcpyAsync(x + map[j], &one, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CKS(op_apply<double>(ctx, L, x, y));
+    CK(cudaMemcpyAsync(col.data(), y, sizeof(double) * tot, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(x + map[j], &zero, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n; ++i) S[(size_t)i * n + j] = col[map[i]];
+  }
+  if (!invert(n, S)) { ctx->err = "coarsest operator singular"; return STMG_ERR_INTERNAL; }
+  std::vector<double> cm((size_t)n * n);
+  std::vector<float> cmf((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) { cm[(size_t)j * n + i] = S[(size_t)i * n + j]; cmf[(size_t)j * n + i] = (float)S[(size_t)i * n + j]; }
+  CKS(dev_alloc(ctx, &L.cmap, n));
+  CKS(dev_alloc(ctx, &L.cinv64, (size_t)n * n));
+  CKS(dev_alloc(ctx, &L.cinv32, (size_t)n * n));
+  CK(cudaMemcpy(L.cmap, map.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cinv64, cm.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cinv32, cmf.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice));
+  return STMG_OK;
+}
+
+stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem* pr, const stmg_options* op) {
+  if (!mesh || !pr) return invalid(ctx, "mesh and problem are required");
+  const int dim = mesh->dim, N = mesh->n_cells;
+  if (dim != 2 && dim != 3) return invalid(ctx, "dim must be 2 or 3");
+  if (N < 2) return invalid(ctx, "n_cells must be >= 2");
+  if (pr->p < 1 || pr->p > 4) return invalid(ctx, "p must be in 1..4");
+  if (pr->time_scheme != STMG_DG && pr->time_scheme != STMG_CGP) return invalid(ctx, "unknown time scheme");
+  if (pr->pde != STMG_HEAT && pr->pde != STMG_WAVE) return invalid(ctx, "unknown pde");
+  const int nt = pr->time_scheme == STMG_DG ? pr->k + 1 : pr->k;
+  if (nt < 1 || nt > kMaxNT || (pr->time_scheme == STMG_CGP && pr->k < 1)) return invalid(ctx, "time degree out of range");
+  if (!(pr->tau > 0.0)) return invalid(ctx, "tau must be positive");
+  ctx->dim = dim; ctx->pde = pr->pde; ctx->scheme = pr->time_scheme; ctx->tau = pr->tau;
+  stmg_options o{};
+  if (op) o = *op;
+  if (o.nu_pre < 0 || o.nu_post < 0) return invalid(ctx, "negative smoothing sweeps");
+  if (o.nu_pre == 0) o.nu_pre = 1;
+  if (o.nu_post == 0) o.nu_post = 1;
+  if (o.vcycle_precision != STMG_FP64) o.vcycle_precision = STMG_FP32;
+  if (o.fgmres_restart <= 0) o.fgmres_restart = 30;
+  if (o.fgmres_restart > 64) return invalid(ctx, "fgmres_restart must be <= 64");
+  if (!(o.rtol > 0.0)) o.rtol = 1e-8;
+  if (o.max_it <= 0) o.max_it = 200;
+  if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
+  if (o.inverse_precision < STMG_FP64 || o.inverse_precision > STMG_BF16) return invalid(ctx, "inverse_precision out of range");
+  const int inv_prec = o.inverse_precision == STMG_FP64 ? 0 : o.inverse_precision == STMG_FP32 ? 1 : 2;
+  ctx->opt = o;
+  const int64_t nv1 = N + 1;
+  const int64_t nverts = dim == 3 ? nv1 * nv1 * nv1 : nv1 * nv1;
+  std::vector<double> verts((size_t)nverts * dim);
+  if (mesh->vertices) {
+    std::memcpy(verts.data(), mesh->vertices, sizeof(double) * verts.size());
+  } else {
+    for (int64_t v = 0; v < nverts; ++v) {
+      int64_t r = v;
+      for (int d = 0; d < dim; ++d) { verts[v * dim + d] = (double)(r % nv1) / N; r /= nv1; }
+    }
+  }
+  // finest-level coefficient at Gauss points and per-cell means
+  const int64_t ncells_f = dim == 3 ? (int64_t)N * N * N : (int64_t)N * N;
+  const int nqd_f = dim == 3 ? (pr->p + 1) * (pr->p + 1) * (pr->p + 1) : (pr->p + 1) * (pr->p + 1);
+  std::vector<double> rho_f((size_t)ncells_f * nqd_f, 1.0), cell_mean(ncells_f, 1.0);
+  if (pr->coeff) {
+    if (pr->coeff_mode == STMG_COEFF_PER_CELL) {
+      for (int64_t c = 0; c < ncells_f; ++c) {
+        cell_mean[c] = pr->coeff[c];
+        for (int q = 0; q < nqd_f; ++q) rho_f[c * nqd_f + q] = pr->coeff[c];
+      }
+    } else if (pr->coeff_mode == STMG_COEFF_PER_QPOINT) {
+      for (int64_t c = 0; c < ncells_f; ++c) {
+        double s = 0.0;
+        for (int q = 0; q < nqd_f; ++q) { rho_f[c * nqd_f + q] = pr->coeff[c * nqd_f + q]; s += pr->coeff[c * nqd_f + q]; }
+        cell_mean[c] = s / nqd_f;
+      }
+    } else {
+      return invalid(ctx, "unknown coefficient mode");
+    }
+    for (double v : rho_f) if (!(v > 0.0) || !std::isfinite(v)) return invalid(ctx, "coefficient must be positive and finite");
+  }
+  std::vector<Spec> seq = level_sequence(pr->p, N, pr->k, pr->time_scheme);
+  ctx->levels.resize(seq.size());
+  for (size_t li = 0; li < seq.size(); ++li) {
+    Level& L = ctx->levels[li];
+    L.dim = dim; L.p = seq[li].p; L.n = L.p + 1; L.N = seq[li].N; L.k = seq[li].k;
+    L.nt = pr->time_scheme == STMG_DG ? L.k + 1 : L.k;
+    L.g.dim = dim; L.g.N = L.N; L.g.p = L.p; L.g.nn1 = L.p * L.N + 1;
+    L.g.n_nodes = dim == 3 ? (int64_t)L.g.nn1 * L.g.nn1 * L.g.nn1 : (int64_t)L.g.nn1 * L.g.nn1;
+    L.g.n_cells = dim == 3 ? (int64_t)L.N * L.N * L.N : (int64_t)L.N * L.N;
+    L.sc = slab_coeffs(pr->pde, pr->time_scheme, L.k, pr->tau);
+    fill_tables(L);
+    // vertices: every (N/N_l)-th fine vertex
+    const int r = N / L.N;
+    const int64_t lv1 = L.N + 1;
+    const int64_t lnv = dim == 3 ? lv1 * lv1 * lv1 : lv1 * lv1;
+    L.vertices.resize((size_t)lnv * dim);
+    for (int64_t v = 0; v < lnv; ++v) {
+      const int64_t ix = v % lv1, iy = (v / lv1) % lv1, iz = dim == 3 ? v / (lv1 * lv1) : 0;
+      const int64_t fv_ = ix * r + nv1 * (iy * r + nv1 * iz * r);
+      for (int d = 0; d < dim; ++d) L.vertices[v * dim + d] = verts[fv_ * dim + d];
+    }
+    const int nq = L.n;
+    const int nqd = dim == 3 ? nq * nq * nq : nq * nq;
+    if (li == 0) {
+      L.rho_qp = rho_f;
+    } else {
+      std::vector<double> xq, wq;
+      gauss_legendre(nq, xq, wq);
+      L.rho_qp.resize((size_t)L.g.n_cells * nqd);
+      for (int64_t c = 0; c < L.g.n_cells; ++c) {
+        const int64_t cx = c % L.N, cy = (c / L.N) % L.N, cz = dim == 3 ? c / ((int64_t)L.N * L.N) : 0;
+        const int64_t cc[3] = {cx, cy, cz};
+        for (int q = 0; q < nqd; ++q) {
+          const int qi[3] = {q % nq, (q / nq) % nq, q / (nq * nq)};
+          int64_t fid = 0;
+          for (int d = dim - 1; d >= 0; --d) {
+            const double s = (cc[d] + xq[qi[d]]) / L.N;
+            int64_t fc = (int64_t)std::floor(s * N);
+            if (fc > N - 1) fc = N - 1;
+            fid = fid * N + fc;
+          }
+          L.rho_qp[c * nqd + q] = cell_mean[fid];
+        }
+      }
+    }
+    // device geometry
+    double *dvert = nullptr, *drho = nullptr, *dxq = nullptr, *dwq = nullptr;
+    CKS(dev_alloc(ctx, &dvert, L.vertices.size()));
+    CKS(dev_alloc(ctx, &drho, L.rho_qp.size()));
+    CKS(dev_alloc(ctx, &dxq, nq));
+    CKS(dev_alloc(ctx, &dwq, nq));
+    std::vector<double> xq, wq;
+    gauss_legendre(nq, xq, wq);
+    CK(cudaMemcpy(dvert, L.vertices.data(), sizeof(double) * L.vertices.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(drho, L.rho_qp.data(), sizeof(double) * L.rho_qp.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dxq, xq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dwq, wq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice));
+    const int ncomp = dim == 3 ? 7 : 4;
+    CKS(dev_alloc(ctx, &L.geo64, (size_t)L.g.n_cells * ncomp * nqd));
+    CKS(dev_alloc(ctx, &L.geo32, (size_t)L.g.n_cells * ncomp * nqd));
+    CK(launch_geometry(L.g, dvert, drho, dxq, dwq, L.geo64, L.geo32, ctx->stream));
+    const int64_t sz = L.size();
+    CKS(dev_alloc(ctx, &L.f64, sz)); CKS(dev_alloc(ctx, &L.u64, sz)); CKS(dev_alloc(ctx, &L.r64, sz));
+    CKS(dev_alloc(ctx, &L.f32, sz)); CKS(dev_alloc(ctx, &L.u32, sz)); CKS(dev_alloc(ctx, &L.r32, sz));
+    CK(cudaMemsetAsync(L.u64, 0, sizeof(double) * sz, ctx->stream));
+    CK(cudaMemsetAsync(L.u32, 0, sizeof(float) * sz, ctx->stream));
+    L.inv_prec = inv_prec;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  // Krylov workspace (also used by the relaxation estimate)
+  const int64_t n0 = ctx->levels[0].size();
+  ctx->m = o.fgmres_restart;
+  ctx->nvec = std::max(ctx->m, 20) + 1;
+  CKS(dev_alloc(ctx, &ctx->V, (size_t)ctx->nvec * n0));
+  CKS(dev_alloc(ctx, &ctx->Z, (size_t)std::max(ctx->m, 1) * n0));
+  CKS(dev_alloc(ctx, &ctx->partial, (size_t)multidot_blocks() * 80));
+  CKS(dev_alloc(ctx, &ctx->dsm, 512));
+  for (int i = 0; i < 6; ++i) CKS(dev_alloc(ctx, &ctx->tmp[i], ctx->levels[0].g.n_nodes));
+  CKS(dev_alloc(ctx, &ctx->rhs_buf, n0));
+  CKS(dev_alloc(ctx, &ctx->u_buf, n0 * 2 + 4 * ctx->levels[0].g.n_nodes));
+  CK(cudaMallocHost(&ctx->hsm, 512 * sizeof(double)));
+  for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
+    CKS(setup_smoother(ctx, ctx->levels[li]));
+    CKS(setup_transfer(ctx, ctx->levels[li], ctx->levels[li + 1]));
+  }
+  CKS(setup_coarse(ctx, ctx->levels.back()));
+  for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
+    if (o.omega) ctx->levels[li].omega = o.omega[li];
+    else CKS(estimate_omega(ctx, (int)li));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return STMG_OK;
+}
+
+template <typename T>
+stmg_status vcycle_public(stmg_ctx* ctx, const T* r, T* e) {
+  Level& L = ctx->levels[0];
+  CK(cudaMemcpyAsync(fv<T>(L), r, sizeof(T) * L.size(), cudaMemcpyDeviceToDevice, ctx->stream));
+  CKS(run_vcycle<T>(ctx));
+  CK(cudaMemcpyAsync(e, uv<T>(L), sizeof(T) * L.size(), cudaMemcpyDeviceToDevice, ctx->stream));
+  return STMG_OK;
+}
+
+// preconditioner z = B v on the finest level (FP64 in/out), V-cycle in the configured precision
+stmg_status precondition(stmg_ctx* ctx, const double* v, double* z) {
+  Level& L = ctx->levels[0];
+  const int64_t n = L.size();
+  if (ctx->opt.vcycle_precision == STMG_FP32) {
+    CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
+    CKS(run_vcycle<float>(ctx));
+    CK(launch_convert<float, double>(L.u32, z, n, ctx->stream));
+    ctx->launches += 2;
+  } else {
+    CK(cudaMemcpyAsync(L.f64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CKS(run_vcycle<double>(ctx));
+    CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return STMG_OK;
+}
+
+stmg_status norm2(stmg_ctx* ctx, const double* x, int64_t n, double& out) {
+  CKS(dots(ctx, nullptr, 0, x, n, 1, ctx->dsm + 448));
+  ctx->launches += 2;
+  CK(cudaMemcpyAsync(ctx->hsm + 448, ctx->dsm + 448, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out = std::sqrt(std::max(ctx->hsm[448], 0.0));
+  return STMG_OK;
+}
+
+stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_stats* st) {
+  Level& L = ctx->levels[0];
+  const int64_t n = L.size();
+  const int m = ctx->m;
+  const double rtol = ctx->opt.rtol;
+  double bnorm = 0.0;
+  CKS(norm2(ctx, b, n, bnorm));
+  stmg_solve_stats s{};
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st) *st = s;
+    return STMG_OK;
+  }
+  if (!std::isfinite(bnorm)) { ctx->err = "right-hand side is not finite"; return STMG_ERR_NONFINITE; }
+  std::vector<double*> V(m + 1), Z(m);
+  for (int j = 0; j <= m; ++j) V[j] = ctx->V + (size_t)j * n;
+  for (int j = 0; j < m; ++j) Z[j] = ctx->Z + (size_t)j * n;
+  int its = 0;
+  bool first = true;
+  stmg_status result = STMG_OK;
+  while (true) {
+    CKS(op_residual<double>(ctx, L, b, x, V[0]));
+    double beta = 0.0;
+    CKS(norm2(ctx, V[0], n, beta));
+    if (!std::isfinite(beta)) { ctx->err = "residual is not finite"; return STMG_ERR_NONFINITE; }
+    if (first) { s.initial_rel_residual = beta / bnorm; first = false; }
+    s.rel_residual = beta / bnorm;
+    if (beta <= rtol * bnorm) break;
+    if (its >= ctx->opt.max_it) { result = STMG_ERR_NOT_CONVERGED; break; }
+    if (its > 0) s.restarts++;
+    CK(launch_axpby(0.0, V[0], 1.0 / beta, V[0], n, ctx->stream));
+    ctx->launches += 1;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), cs(m, 0.0), sn(m, 0.0);
+    g[0] = beta;
+    int jend = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m; ++j) {
+      CKS(precondition(ctx, V[j], Z[j]));
+      CKS(op_apply<double>(ctx, L, Z[j], V[j + 1]));
+      std::vector<double> h;
+      double hn = 0.0;
+      std::vector<const double*> Vc(V.begin(), V.begin() + j + 1);
+      CKS(orthogonalise(ctx, Vc.data(), j + 1, V[j + 1], n, h, hn));
+      for (int i = 0; i <= j; ++i) {
+        if (!std::isfinite(h[i])) { ctx->err = "preconditioned vector is not finite"; return STMG_ERR_NONFINITE; }
+        H[(size_t)i * m + j] = h[i];
+      }
+      if (!std::isfinite(hn)) { ctx->err = "preconditioned vector is not finite"; return STMG_ERR_NONFINITE; }
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+      cs[j] = H[(size_t)j * m + j] / den;
+      sn[j] = H[(size_t)(j + 1) * m + j] / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      jend = j + 1;
+      if (hn == 0.0) { breakdown = true; break; }
+      if (std::fabs(g[j + 1]) <= rtol * bnorm || its >= ctx->opt.max_it) break;
+    }
+    std::vector<double> y(jend, 0.0);
+    for (int i = jend - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < jend; ++l) t -= H[(size_t)i * m + l] * y[l];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(ctx->dsm + 320, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<const double*> Zc(Z.begin(), Z.begin() + jend);
+    CK(launch_multi_axpy(x, Zc.data(), ctx->dsm + 320, jend, 1.0, n, ctx->stream));
+    ctx->launches += 1;
+    (void)breakdown;
+  }
+  s.iterations = its;
+  if (st) *st = s;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (result != STMG_OK) ctx->err = "FGMRES did not reach rtol within max_it";
+  return result;
+}
+
+// rhs = RM_f (x) M f + RM_f0 M f0 + RA_u0 A u0 + RM_u0 M u0 + RM_v0 M v0, constrained rows 0
+stmg_status rhs_impl(stmg_ctx* ctx, const double* f, const double* f0, const double* u0, const double* v0, double* rhs) {
+  Level& L = ctx->levels[0];
+  const int nt = L.nt;
+  const int64_t nn = L.g.n_nodes;
+  CK(cudaMemsetAsync(rhs, 0, sizeof(double) * L.size(), ctx->stream));
+  OpTab<double> t = L.tab64;
+  for (int i = 0; i < kMaxNT; ++i)
+    for (int j = 0; j < kMaxNT; ++j) {
+      t.TA[i][j] = 0.0;
+      t.TM[i][j] = (i < nt && j < nt) ? L.sc.RM_f[i * nt + j] : 0.0;
+    }
+  t.sign = 1.0;
+  if (f) CK(launch_apply<double>(L.dim, L.n, nt, f, rhs, L.geo64, L.g, t, 0, ctx->stream));
+  ctx->launches += 3;
+  // single-block terms
+  const double* srcs[4] = {f0, u0, u0, v0};
+  const std::vector<double>* coef[4] = {&L.sc.RM_f0, &L.sc.RA_u0, &L.sc.RM_u0, &L.sc.RM_v0};
+  const bool stiff[4] = {false, true, false, false};
+  std::vector<const double*> xs;
+  std::vector<double> C;
+  std::vector<int> used;
+  for (int term = 0; term < 4; ++term) {
+    bool nz = false;
+    for (double c : *coef[term]) nz = nz || c != 0.0;
+    if (!nz || !srcs[term]) continue;
+    double* out = ctx->tmp[term];
+    CK(cudaMemsetAsync(out, 0, sizeof(double) * nn, ctx->stream));
+    OpTab<double> t1 = L.tab64;
+    for (int i = 0; i < kMaxNT; ++i)
+      for (int j = 0; j < kMaxNT; ++j) { t1.TA[i][j] = 0.0; t1.TM[i][j] = 0.0; }
+    if (stiff[term]) t1.TA[0][0] = 1.0; else t1.TM[0][0] = 1.0;
+    t1.sign = 1.0;
+    CK(launch_apply<double>(L.dim, L.n, 1, srcs[term], out, L.geo64, L.g, t1, 0, ctx->stream));
+    ctx->launches += 1;
+    xs.push_back(out);
+    used.push_back(term);
+  }
+  if (!xs.empty()) {
+    const int nin = (int)xs.size();
+    C.assign((size_t)nt * nin, 0.0);
+    for (int i = 0; i < nt; ++i)
+      for (int j = 0; j < nin; ++j) C[(size_t)i * nin + j] = (*coef[used[j]])[i];
+    CK(launch_time_mix(xs.data(), nin, C.data(), nt, rhs, nn, 1, ctx->stream));
+    ctx->launches += 1;
+  }
+  CK(launch_zero_constrained(rhs, L.g, nt, ctx->stream));
+  return STMG_OK;
+}
+
+stmg_status velocity_impl(stmg_ctx* ctx, const double* u, const double* u0, const double* v0, double* v) {
+  Level& L = ctx->levels[0];
+  const int nt = L.nt;
+  const int64_t nn = L.g.n_nodes;
+  std::vector<const double*> xs;
+  std::vector<double> C;
+  for (int j = 0; j < nt; ++j) xs.push_back(u + (int64_t)j * nn);
+  xs.push_back(u0);
+  if (v0) xs.push_back(v0);
+  const int nin = (int)xs.size();
+  C.assign((size_t)nt * nin, 0.0);
+  for (int i = 0; i < nt; ++i) {
+    for (int j = 0; j < nt; ++j) C[(size_t)i * nin + j] = L.sc.VU[i * nt + j];
+    C[(size_t)i * nin + nt] = L.sc.Vu0[i];
+    if (v0) C[(size_t)i * nin + nt + 1] = L.sc.Vv0[i];
+  }
+  CK(launch_time_mix(xs.data(), nin, C.data(), nt, v, nn, 0, ctx->stream));
+  CK(launch_zero_constrained(v, L.g, nt, ctx->stream));
+  return STMG_OK;
+}
+
+// Orders a call's work after the caller's stream and the caller's stream after the call.
+struct StreamJoin {
+  stmg_ctx* c;
+  explicit StreamJoin(stmg_ctx* ctx) : c(ctx) {
+    if (c && c->stream) {
+      cudaEventRecord(c->ev_in, c->user_stream);
+      cudaStreamWaitEvent(c->stream, c->ev_in, 0);
+    }
+  }
+  ~StreamJoin() {
+    if (c && c->stream) {
+      cudaEventRecord(c->ev_out, c->stream);
+      cudaStreamWaitEvent(c->user_stream, c->ev_out, 0);
+    }
+  }
+};
+
+stmg_status check_level(stmg_ctx* ctx, int level, int precision) {
+  if (!ctx) return STMG_ERR_INVALID_ARG;
+  if (level < 0 || level >= (int)ctx->levels.size()) return invalid(ctx, "level out of range");
+  if (precision != STMG_FP32 && precision != STMG_FP64) return invalid(ctx, "precision must be FP32 or FP64");
+  return STMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_problem* problem,
+                        const stmg_options* options, void* stream) {
+  if (!out) return STMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  stmg_ctx* ctx = new stmg_ctx();
+  ctx->user_stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("stream set-up: ") + cudaGetErrorString(e);
+    *out = ctx;
+    return STMG_ERR_CUDA;
+  }
+  stmg_status s;
+  {
+    StreamJoin join(ctx);
+    s = create_impl(ctx, mesh, problem, options);
+  }
+  *out = ctx;  // returned even on error so that stmg_last_error can be read; destroy it
+  return s;
+}
+
+stmg_status stmg_destroy(stmg_ctx* ctx) {
+  if (!ctx) return STMG_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph32) cudaGraphExecDestroy(ctx->graph32);
+  if (ctx->graph64) cudaGraphExecDestroy(ctx->graph64);
+  for (void* p : ctx->allocations) cudaFree(p);
+  if (ctx->hsm) cudaFreeHost(ctx->hsm);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return STMG_OK;
+}
+
+const char* stmg_last_error(const stmg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+stmg_status stmg_sizes(const stmg_ctx* ctx, int64_t* n_nodes, int* n_t, int* n_levels) {
+  if (!ctx || ctx->levels.empty()) return STMG_ERR_INVALID_ARG;
+  if (n_nodes) *n_nodes = ctx->levels[0].g.n_nodes;
+  if (n_t) *n_t = ctx->levels[0].nt;
+  if (n_levels) *n_levels = (int)ctx->levels.size();
+  return STMG_OK;
+}
+
+stmg_status stmg_level_info(const stmg_ctx* ctx, int level, int* p, int* n_cells, int* k, int64_t* n_nodes, int* n_t,
+                            double* omega) {
+  if (!ctx || level < 0 || level >= (int)ctx->levels.size()) return STMG_ERR_INVALID_ARG;
+  const Level& L = ctx->levels[level];
+  if (p) *p = L.p;
+  if (n_cells) *n_cells = L.N;
+  if (k) *k = L.k;
+  if (n_nodes) *n_nodes = L.g.n_nodes;
+  if (n_t) *n_t = L.nt;
+  if (omega) *omega = L.omega;
+  return STMG_OK;
+}
+
+static void map_point(const Level& L, int64_t cell, const double* xi, double* out) {
+  const int dim = L.dim;
+  const int64_t nv1 = L.N + 1;
+  const int64_t cx = cell % L.N, cy = (cell / L.N) % L.N, cz = dim == 3 ? cell / ((int64_t)L.N * L.N) : 0;
+  for (int d = 0; d < dim; ++d) out[d] = 0.0;
+  const int nvert = dim == 3 ? 8 : 4;
+  for (int b = 0; b < nvert; ++b) {
+    const int bits[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+    double f = 1.0;
+    for (int d = 0; d < dim; ++d) f *= bits[d] ? xi[d] : 1.0 - xi[d];
+    const int64_t vid = (cx + bits[0]) + nv1 * ((cy + bits[1]) + nv1 * (cz + bits[2]));
+    for (int d = 0; d < dim; ++d) out[d] += f * L.vertices[vid * dim + d];
+  }
+}
+
+stmg_status stmg_node_coords(const stmg_ctx* ctx, int level, double* xyz) {
+  if (!ctx || !xyz || level < 0 || level >= (int)ctx->levels.size()) return STMG_ERR_INVALID_ARG;
+  const Level& L = ctx->levels[level];
+  std::vector<double> xn = space_nodes(L.p);
+  const int n = L.n, dim = L.dim;
+  const int nb = dim == 3 ? n * n * n : n * n;
+  for (int64_t c = 0; c < L.g.n_cells; ++c) {
+    const int64_t cx = c % L.N, cy = (c / L.N) % L.N, cz = dim == 3 ? c / ((int64_t)L.N * L.N) : 0;
+    for (int a = 0; a < nb; ++a) {
+      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+      const double xi[3] = {xn[ai[0]], xn[ai[1]], dim == 3 ? xn[ai[2]] : 0.0};
+      const int64_t gx = cx * L.p + ai[0], gy = cy * L.p + ai[1], gz = dim == 3 ? cz * L.p + ai[2] : 0;
+      const int64_t node = gx + (int64_t)L.g.nn1 * (gy + (int64_t)L.g.nn1 * gz);
+      map_point(L, c, xi, xyz + node * dim);
+    }
+  }
+  return STMG_OK;
+}
+
+stmg_status stmg_qpoint_coords(const stmg_ctx* ctx, int level, double* xyz) {
+  if (!ctx || !xyz || level < 0 || level >= (int)ctx->levels.size()) return STMG_ERR_INVALID_ARG;
+  const Level& L = ctx->levels[level];
+  std::vector<double> xq, wq;
+  gauss_legendre(L.n, xq, wq);
+  const int n = L.n, dim = L.dim;
+  const int nq = dim == 3 ? n * n * n : n * n;
+  for (int64_t c = 0; c < L.g.n_cells; ++c)
+    for (int q = 0; q < nq; ++q) {
+      const double xi[3] = {xq[q % n], xq[(q / n) % n], dim == 3 ? xq[q / (n * n)] : 0.0};
+      map_point(L, c, xi, xyz + (c * nq + q) * dim);
+    }
+  return STMG_OK;
+}
+
+stmg_status stmg_apply(stmg_ctx* ctx, int level, int precision, const void* x, void* y) {
+  StreamJoin join_(ctx);
+  CKS(check_level(ctx, level, precision));
+  Level& L = ctx->levels[level];
+  if (precision == STMG_FP64) return op_apply<double>(ctx, L, (const double*)x, (double*)y);
+  return op_apply<float>(ctx, L, (const float*)x, (float*)y);
+}
+
+stmg_status stmg_residual(stmg_ctx* ctx, int level, int precision, const void* f, const void* u, void* r) {
+  StreamJoin join_(ctx);
+  CKS(check_level(ctx, level, precision));
+  Level& L = ctx->levels[level];
+  if (precision == STMG_FP64) return op_residual<double>(ctx, L, (const double*)f, (const double*)u, (double*)r);
+  return op_residual<float>(ctx, L, (const float*)f, (const float*)u, (float*)r);
+}
+
+stmg_status stmg_smooth(stmg_ctx* ctx, int level, int precision, int sweeps, const void* f, void* u) {
+  StreamJoin join_(ctx);
+  CKS(check_level(ctx, level, precision));
+  if (level == (int)ctx->levels.size() - 1) return invalid(ctx, "the coarsest level has no smoother");
+  if (sweeps < 0) return invalid(ctx, "sweeps must be >= 0");
+  Level& L = ctx->levels[level];
+  if (precision == STMG_FP64) return op_smooth<double>(ctx, level, sweeps, (const double*)f, (double*)u, L.r64);
+  return op_smooth<float>(ctx, level, sweeps, (const float*)f, (float*)u, L.r32);
+}
+
+stmg_status stmg_restrict(stmg_ctx* ctx, int level, int precision, const void* rf, void* rc) {
+  StreamJoin join_(ctx);
+  CKS(check_level(ctx, level, precision));
+  if (level == (int)ctx->levels.size() - 1) return invalid(ctx, "no coarser level");
+  if (precision == STMG_FP64) return op_restrict<double>(ctx, level, (const double*)rf, (double*)rc);
+  return op_restrict<float>(ctx, level, (const float*)rf, (float*)rc);
+}
+
+stmg_status stmg_prolongate_add(stmg_ctx* ctx, int level, int precision, const void* ec, void* uf) {
+  StreamJoin join_(ctx);
+  CKS(check_level(ctx, level, precision));
+  if (level == (int)ctx->levels.size() - 1) return invalid(ctx, "no coarser level");
+  if (precision == STMG_FP64) return op_prolongate_add<double>(ctx, level, (const double*)ec, (double*)uf);
+  return op_prolongate_add<float>(ctx, level, (const float*)ec, (float*)uf);
+}
+
+stmg_status stmg_vcycle(stmg_ctx* ctx, int precision, const void* r, void* e) {
+  StreamJoin join_(ctx);
+  CKS(check_level(ctx, 0, precision));
+  if (precision == STMG_FP64) return vcycle_public<double>(ctx, (const double*)r, (double*)e);
+  return vcycle_public<float>(ctx, (const float*)r, (float*)e);
+}
+
+stmg_status stmg_rhs(stmg_ctx* ctx, const double* f, const double* f0, const double* u0, const double* v0, double* rhs) {
+  StreamJoin join_(ctx);
+  if (!ctx || !rhs) return STMG_ERR_INVALID_ARG;
+  return rhs_impl(ctx, f, f0, u0, v0, rhs);
+}
+
+stmg_status stmg_solve(stmg_ctx* ctx, const double* rhs, double* u, stmg_solve_stats* stats) {
+  StreamJoin join_(ctx);
+  if (!ctx || !rhs || !u) return STMG_ERR_INVALID_ARG;
+  return solve_impl(ctx, rhs, u, stats);
+}
+
+stmg_status stmg_wave_velocity(stmg_ctx* ctx, const double* u, const double* u0, const double* v0, double* v) {
+  StreamJoin join_(ctx);
+  if (!ctx || !u || !u0 || !v) return STMG_ERR_INVALID_ARG;
+  if (ctx->pde != STMG_WAVE) return invalid(ctx, "velocity update needs the wave equation");
+  return velocity_impl(ctx, u, u0, v0, v);
+}
+
+stmg_status stmg_guess_previous(stmg_ctx* ctx, const double* u0, double* u) {
+  StreamJoin join_(ctx);
+  if (!ctx || !u0 || !u) return STMG_ERR_INVALID_ARG;
+  Level& L = ctx->levels[0];
+  CK(launch_broadcast_time(u0, u, L.nt, L.g.n_nodes, ctx->stream));
+  ctx->launches += 1;
+  return STMG_OK;
+}
+
+stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f0, const double* u0, const double* v0,
+                                 double* u, double* v, stmg_solve_stats* stats) {
+  StreamJoin join_(ctx);
+  if (!ctx || !f || !u0 || !u) return STMG_ERR_INVALID_ARG;
+  Level& L = ctx->levels[0];
+  const int64_t nn = L.g.n_nodes, n = L.size();
+  double* d_f = ctx->u_buf;                 // n
+  double* d_u = ctx->u_buf + n;             // n
+  double* d_f0 = ctx->u_buf + 2 * n;        // nn each
+  double* d_u0 = d_f0 + nn;
+  double* d_v0 = d_u0 + nn;
+  double* d_v = ctx->tmp[4];
+  CK(cudaMemcpyAsync(d_f, f, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d_u0, u0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
+  if (f0) CK(cudaMemcpyAsync(d_f0, f0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
+  if (v0) CK(cudaMemcpyAsync(d_v0, v0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
+  CKS(rhs_impl(ctx, d_f, f0 ? d_f0 : nullptr, d_u0, v0 ? d_v0 : nullptr, ctx->rhs_buf));
+  CK(launch_broadcast_time(d_u0, d_u, L.nt, nn, ctx->stream));
+  ctx->launches += 1;
+  stmg_status s = solve_impl(ctx, ctx->rhs_buf, d_u, stats);
+  if (s != STMG_OK && s != STMG_ERR_NOT_CONVERGED) return s;
+  CK(cudaMemcpyAsync(u, d_u, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  if (v && ctx->pde == STMG_WAVE) {
+    (void)d_v;
+    double* vbuf = ctx->rhs_buf;  // rhs no longer needed
+    CKS(velocity_impl(ctx, d_u, d_u0, v0 ? d_v0 : nullptr, vbuf));
+    CK(cudaMemcpyAsync(v, vbuf, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return s;
+}
+
+stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return STMG_ERR_INVALID_ARG;
+  *count = ctx->launches;
+  return STMG_OK;
+}
+
+stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision, int reps, double* avg_ms) {
+  CKS(check_level(ctx, level, precision));
+  if (reps < 1 || !avg_ms) return invalid(ctx, "reps must be >= 1");
+  if (kernel != STMG_KERNEL_APPLY && kernel != STMG_KERNEL_ASM && kernel != STMG_KERNEL_VCYCLE)
+    return invalid(ctx, "unknown kernel id");
+  if (kernel == STMG_KERNEL_ASM && level == (int)ctx->levels.size() - 1) return invalid(ctx, "no smoother there");
+  Level& L = ctx->levels[level];
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  auto once = [&]() -> stmg_status {
+    if (kernel == STMG_KERNEL_VCYCLE) {
+      if (precision == STMG_FP64) return run_vcycle<double>(ctx);
+      return run_vcycle<float>(ctx);
+    }
+    if (kernel == STMG_KERNEL_APPLY) {
+      if (precision == STMG_FP64) {
+        OpTab<double> t = L.tab64;
+        CK(launch_apply<double>(L.dim, L.n, L.nt, L.u64, L.r64, L.geo64, L.g, t, 1, ctx->stream));
+      } else {
+        OpTab<float> t = L.tab32;
+        CK(launch_apply<float>(L.dim, L.n, L.nt, L.u32, L.r32, L.geo32, L.g, t, 1, ctx->stream));
+      }
+      return STMG_OK;
+    }
+    if (precision == STMG_FP64) return op_asm<double>(ctx, L, L.r64, L.u64, L.omega);
+    return op_asm<float>(ctx, L, L.r32, L.u32, L.omega);
+  };
+  CKS(once());  // warm-up
+  CK(cudaEventRecord(a, ctx->stream));
+  for (int i = 0; i < reps; ++i) CKS(once());
+  CK(cudaEventRecord(b, ctx->stream));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *avg_ms = (double)ms / reps;
+  return STMG_OK;
+}
+
+}  // extern "C"

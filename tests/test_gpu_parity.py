@@ -1,0 +1,161 @@
+"""GPU path (C ABI via the Python binding) against the FP64 oracle, element by element.
+
+Tolerances: FP64 kernels 1e-10 relative (max-norm over the vector, scaled by its
+largest entry), FP32 kernels 2e-5 relative (float rounding of O(100) terms),
+solutions 1e-8 relative L2 after FGMRES to rtol 1e-12.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_cases import CASES, make_context, oracle_hierarchy, rel_err, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 2e-5
+
+
+def _rand(n, seed, bmask=None):
+    x = synth.random_vector(n, seed=seed)
+    if bmask is not None:
+        x[bmask] = 0.0
+    return x
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_apply_every_level(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H)
+    for li, lev in enumerate(H.levels):
+        prob = lev.prob
+        x = _rand(prob.n, 100 + li)  # constrained entries nonzero on purpose: identity rows
+        ref = prob.S @ x
+        for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+            xd = torch.from_numpy(x).to("cuda", dt)
+            yd = torch.empty_like(xd)
+            ctx.apply(xd, yd, level=li)
+            assert rel_err(yd.cpu().numpy(), ref) < tol, (case.name, li, dt)
+        # residual r = f - S u
+        f = _rand(prob.n, 200 + li)
+        fd = torch.from_numpy(f).cuda()
+        ud = torch.from_numpy(x).cuda()
+        rd = torch.empty_like(fd)
+        ctx.residual(fd, ud, rd, level=li)
+        assert rel_err(rd.cpu().numpy(), f - ref) < TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_rhs_and_velocity(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H)
+    prob = H.levels[0].prob
+    nn = prob.grid.n_nodes
+    f = _rand(prob.n, 7).reshape(prob.nt, nn)
+    f0, u0, v0 = (_rand(nn, s, prob.bmask) for s in (8, 9, 10))
+    ref = prob.rhs(f, f0, u0, v0 if case.pde == "wave" else None)
+    dev = "cuda"
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).to(dev)
+    rhs = torch.empty(prob.n, dtype=torch.float64, device=dev)
+    ctx.rhs(t(f), rhs, f0=t(f0), u0=t(u0), v0=t(v0) if case.pde == "wave" else None)
+    assert rel_err(rhs.cpu().numpy(), ref) < TOL64
+    if case.pde == "wave":
+        u = _rand(prob.n, 11).reshape(prob.nt, nn)
+        u[:, prob.bmask] = 0.0
+        vref = prob.velocity(u, u0, v0)
+        vref[:, prob.bmask] = 0.0
+        v = torch.empty(prob.n, dtype=torch.float64, device=dev)
+        ctx.wave_velocity(t(u), t(u0), t(v0), v)
+        assert rel_err(v.cpu().numpy(), vref) < TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_smoother_and_transfers(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H, vcycle_precision=stmg.FP64)
+    for li, lev in enumerate(H.levels[:-1]):
+        prob = lev.prob
+        f = _rand(prob.n, 300 + li, prob.bmask_full)
+        u = _rand(prob.n, 400 + li, prob.bmask_full)
+        ref = u + lev.omega * (lev.B @ (f - prob.S @ u))
+        fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()
+        ctx.smooth(fd, ud, sweeps=1, level=li)
+        assert rel_err(ud.cpu().numpy(), ref) < 1e-9, (case.name, li)
+        # FP32 storage/arithmetic
+        u32 = torch.from_numpy(u).to("cuda", torch.float32)
+        ctx.smooth(fd.float(), u32, sweeps=1, level=li)
+        assert rel_err(u32.cpu().numpy(), ref) < 1e-4
+        # restriction and prolongation
+        c = H.levels[li + 1]
+        rc_ref = lev.P.T @ f
+        rcd = torch.empty(c.prob.n, dtype=torch.float64, device="cuda")
+        ctx.restrict(fd, rcd, level=li)
+        assert rel_err(rcd.cpu().numpy(), rc_ref) < 1e-13
+        e = _rand(c.prob.n, 500 + li, c.prob.bmask_full)
+        uf = torch.from_numpy(u).cuda()
+        ctx.prolongate_add(torch.from_numpy(e).cuda(), uf, level=li)
+        assert rel_err(uf.cpu().numpy(), u + lev.P @ e) < 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_vcycle(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    prob = H.levels[0].prob
+    r = _rand(prob.n, 600, prob.bmask_full)
+    ref = H.vcycle(r)
+    for prec, dt, tol in ((stmg.FP64, torch.float64, 1e-9), (stmg.FP32, torch.float32, 2e-4)):
+        ctx = make_context(stmg, case, H, vcycle_precision=prec)
+        for _ in range(3):  # first call eager, then captured graph, then replay
+            e = torch.empty(prob.n, dtype=dt, device="cuda")
+            ctx.vcycle(torch.from_numpy(r).to("cuda", dt), e)
+            assert rel_err(e.cpu().numpy(), ref) < tol, (case.name, prec)
+        ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_solve_matches_direct_solution(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    prob = H.levels[0].prob
+    b = _rand(prob.n, 700, prob.bmask_full)
+    xd = prob.solve(b).reshape(-1)
+    for prec in (stmg.FP64, stmg.FP32):
+        ctx = make_context(stmg, case, H, vcycle_precision=prec, rtol=1e-12, max_it=300)
+        u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        st = ctx.solve(torch.from_numpy(b).cuda(), u)
+        assert st["converged"] and st["rel_residual"] <= 1e-12
+        err = np.linalg.norm(u.cpu().numpy() - xd) / np.linalg.norm(xd)
+        assert err < 1e-8, (case.name, prec, err, st)
+        ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=lambda c: c.name)
+def test_relaxation_estimate_matches_oracle(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H, omega=None)
+    for li, om in enumerate(H.omegas()):
+        assert abs(ctx.level_info(li)["omega"] - om) < 1e-3 * om, (case.name, li)
+    ctx.close()
+
+
+def test_node_coordinates_match_oracle(env):
+    torch, stmg = env
+    case = CASES[1]
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H)
+    assert np.abs(ctx.node_coords() - H.levels[0].grid.node_coords()).max() < 1e-14
+    assert np.abs(ctx.qpoint_coords() - H.levels[0].grid.quad_points_phys()).max() < 1e-14
+    ctx.close()
