@@ -95,7 +95,7 @@ def oracle_sample(n_cells: int, n_slabs: int, tau: float):
     from oracle import slab, space
     t0 = time.perf_counter()
     V = synth.jittered_vertices(n_cells, 3)
-    rho = synth.block_coefficient(n_cells, 3, blocks=4)
+    rho = synth.block_coefficient(n_cells, 3, blocks=2)
     g = space.Grid(n_cells, 3, 2, V)
     prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, rho), "heat", "dg", 2, tau)
     X = g.node_coords()

@@ -147,7 +147,13 @@ def asm_operator(prob: SlabProblem) -> sp.csr_matrix:
 
 
 def arnoldi_ritz(matvec, v0: np.ndarray, m: int) -> np.ndarray:
-    """Ritz values of an m-step Arnoldi process (modified Gram-Schmidt) started at v0."""
+    """Ritz values of an m-step Arnoldi process started at v0.
+
+    Gram-Schmidt is applied twice per step (modified Gram-Schmidt with one full
+    reorthogonalisation), so that the basis stays orthonormal to rounding even
+    when the Krylov space is exhausted; a single pass can lose orthogonality and
+    produce spurious Ritz values.
+    """
     n = len(v0)
     m = min(m, n)
     V = np.zeros((m + 1, n))
@@ -156,9 +162,11 @@ def arnoldi_ritz(matvec, v0: np.ndarray, m: int) -> np.ndarray:
     steps = m
     for j in range(m):
         w = matvec(V[j])
-        for i in range(j + 1):
-            H[i, j] = np.dot(V[i], w)
-            w = w - H[i, j] * V[i]
+        for _ in range(2):
+            for i in range(j + 1):
+                c = np.dot(V[i], w)
+                H[i, j] += c
+                w = w - c * V[i]
         H[j + 1, j] = np.linalg.norm(w)
         if H[j + 1, j] <= 1e-14 * abs(H[j, j]) + 1e-300:
             steps = j + 1

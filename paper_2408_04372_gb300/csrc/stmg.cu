@@ -420,7 +420,9 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
     lmin = std::min(lmin, e.real());
   }
   if (!(lmax + lmin > 0.0) || !std::isfinite(lmax + lmin)) {
-    ctx->err = "relaxation estimate failed on level " + std::to_string(l);
+    ctx->err = "relaxation estimate failed on level " + std::to_string(l) + " (" + std::to_string(m) + " Arnoldi steps, Ritz values";
+    for (auto& e : ev) ctx->err += " " + std::to_string(e.real()) + "+" + std::to_string(e.imag()) + "i";
+    ctx->err += ")";
     return STMG_ERR_INTERNAL;
   }
   L.omega = 2.0 / (lmax + lmin);

@@ -285,8 +285,8 @@ bool invert_complex(int n, std::vector<cplx>& a) {
 }
 
 // Eigenvalues by Householder reduction to Hessenberg form followed by the
-// single-shift complex QR iteration with Wilkinson shifts (Givens rotations)
-// and deflation at the bottom of the active block.
+// single-shift complex QR iteration with Wilkinson shifts (Givens rotations),
+// deflation at the bottom of the active block and a closed form for the last 2x2 block.
 std::vector<cplx> eigenvalues(int n, const std::vector<double>& ar) {
   std::vector<cplx> a(ar.begin(), ar.end());
   auto A = [&](int i, int j) -> cplx& { return a[i * n + j]; };
@@ -318,24 +318,36 @@ std::vector<cplx> eigenvalues(int n, const std::vector<double>& ar) {
     }
   }
   std::vector<cplx> ev;
+  double anorm = 0.0;
+  for (auto& x : a) anorm = std::max(anorm, std::abs(x));
   int m = n;
-  int guard = 0;
-  while (m > 0 && guard < 10000) {
-    ++guard;
-    if (m == 1) { ev.push_back(A(0, 0)); m = 0; break; }
+  int its = 0;
+  while (m > 0) {
+    if (m == 1) { ev.push_back(A(0, 0)); break; }
+    if (m == 2) {  // closed form for the last 2x2 block
+      cplx a11 = A(0, 0), a12 = A(0, 1), a21 = A(1, 0), a22 = A(1, 1);
+      cplx h = 0.5 * (a11 - a22);
+      cplx disc = std::sqrt(h * h + a12 * a21);
+      ev.push_back(0.5 * (a11 + a22) + disc);
+      ev.push_back(0.5 * (a11 + a22) - disc);
+      break;
+    }
     double scale = std::abs(A(m - 1, m - 1)) + std::abs(A(m - 2, m - 2));
-    if (std::abs(A(m - 1, m - 2)) <= 1e-15 * (scale > 0 ? scale : 1.0)) {
+    if (scale == 0.0) scale = anorm;
+    if (std::abs(A(m - 1, m - 2)) <= 1e-15 * scale || its > 300) {  // deflate (forced after 300 sweeps)
       ev.push_back(A(m - 1, m - 1));
       --m;
+      its = 0;
       continue;
     }
+    ++its;
     // Wilkinson shift from the trailing 2x2 block
     cplx a11 = A(m - 2, m - 2), a12 = A(m - 2, m - 1), a21 = A(m - 1, m - 2), a22 = A(m - 1, m - 1);
-    cplx tr = a11 + a22, det = a11 * a22 - a12 * a21;
-    cplx disc = std::sqrt(tr * tr * 0.25 - det);
-    cplx l1 = tr * 0.5 + disc, l2 = tr * 0.5 - disc;
+    cplx h = 0.5 * (a11 - a22);
+    cplx disc = std::sqrt(h * h + a12 * a21);
+    cplx l1 = 0.5 * (a11 + a22) + disc, l2 = 0.5 * (a11 + a22) - disc;
     cplx mu = (std::abs(l1 - a22) < std::abs(l2 - a22)) ? l1 : l2;
-    if (guard % 11 == 0) mu += cplx(std::abs(a21), 0.0);  // exceptional shift
+    if (its % 11 == 0) mu += cplx(std::abs(a21), 0.0);  // exceptional shift
     for (int i = 0; i < m; ++i) A(i, i) -= mu;
     std::vector<cplx> cs(m), sn(m);
     for (int k = 0; k + 1 < m; ++k) {  // QR by Givens
@@ -343,7 +355,7 @@ std::vector<cplx> eigenvalues(int n, const std::vector<double>& ar) {
       double r = std::sqrt(std::norm(x) + std::norm(y));
       cplx c = r > 0 ? x / r : cplx(1.0, 0.0), s = r > 0 ? y / r : cplx(0.0, 0.0);
       cs[k] = c; sn[k] = s;
-      for (int j = k; j < n; ++j) {
+      for (int j = k; j < m; ++j) {
         cplx t1 = A(k, j), t2 = A(k + 1, j);
         A(k, j) = std::conj(c) * t1 + std::conj(s) * t2;
         A(k + 1, j) = -s * t1 + c * t2;

@@ -145,10 +145,27 @@ def test_solve_matches_direct_solution(env, case):
 def test_relaxation_estimate_matches_oracle(env, case):
     torch, stmg = env
     H = oracle_hierarchy(case)
-    ctx = make_context(stmg, case, H, omega=None)
-    for li, om in enumerate(H.omegas()):
-        assert abs(ctx.level_info(li)["omega"] - om) < 1e-3 * om, (case.name, li)
-    ctx.close()
+    for prec, tol in ((stmg.FP64, 1e-3), (stmg.FP32, 1e-2)):
+        ctx = make_context(stmg, case, H, omega=None, vcycle_precision=prec)
+        for li, om in enumerate(H.omegas()):
+            assert abs(ctx.level_info(li)["omega"] - om) < tol * om, (case.name, li, prec)
+        ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_smoother_fp64_vectors_with_fp32_and_bf16_inverses(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    for inv, tol in ((stmg.FP32, 1e-5), (stmg.BF16, 2e-2)):
+        ctx = make_context(stmg, case, H, vcycle_precision=stmg.FP32, inverse_precision=inv)
+        for li, lev in enumerate(H.levels[:-1]):
+            prob = lev.prob
+            f = _rand(prob.n, 800 + li, prob.bmask_full)
+            ref = lev.omega * (lev.B @ f)
+            u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+            ctx.smooth(torch.from_numpy(f).cuda(), u, sweeps=1, level=li)
+            assert rel_err(u.cpu().numpy(), ref) < tol, (case.name, li, inv)
+        ctx.close()
 
 
 def test_node_coordinates_match_oracle(env):
