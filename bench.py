@@ -329,11 +329,18 @@ def read_peaks():
 
 
 def read_traffic(key):
+    """DRAM bytes per launch from the committed ncu capture; None once the kernel source changed."""
+    import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(key)
-    return None if d is None else d.get("bytes_per_launch")
+    if d is None:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+        return None
+    return d.get("bytes_per_launch")
 
 
 def main():
