@@ -167,6 +167,26 @@ stmg_status stmg_guess_previous(stmg_ctx* ctx, const double* u0, double* u);
 stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f0, const double* u0,
                                  const double* v0, double* u, double* v, stmg_solve_stats* stats);
 
+/* Smoothing without any device allocation.  Same result as stmg_smooth, but the
+ * residual f - S_l u of each sweep is kept in a fixed buffer of
+ * STMG_NOALLOC_SCRATCH_BYTES bytes that is part of the library's device image
+ * instead of the context's per-level work vectors.  Meant for callers that may
+ * not call cudaMalloc (or any allocating routine) on the path that smooths, for
+ * example code whose device memory is fully handed to another allocator once
+ * the context exists, or code that must not touch the context's own scratch.
+ * Every GPU that loads the library holds the buffer until the process exits.
+ * The paper has no counterpart; this is an interface variant only.
+ * - Returns STMG_ERR_INVALID_ARG, before any device work, when N_t * n_nodes of
+ *   the level times the element size (8 for FP64, 4 for FP32) exceeds the buffer.
+ * - The first call on a device looks up the buffer's device address on that
+ *   device (the device must be current); make that first call before any
+ *   stream capture.
+ * - All calls share the one buffer and it keeps the last call's contents:
+ *   calls that overlap on the GPU (other streams, other contexts, other
+ *   threads) race; order them on one stream. */
+#define STMG_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+stmg_status stmg_smooth_noalloc(stmg_ctx* ctx, int level, int precision, int sweeps, const void* f, void* u);
+
 /* Number of kernels this context has launched so far (a captured V-cycle graph
  * counts its kernel nodes at every replay).  Host-side counter, no device work. */
 stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count);

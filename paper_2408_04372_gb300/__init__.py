@@ -26,7 +26,7 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_node_coords", "stmg_qpoint_coords", "stmg_apply", "stmg_residual", "stmg_smooth",
            "stmg_restrict", "stmg_prolongate_add", "stmg_vcycle", "stmg_rhs", "stmg_solve",
            "stmg_wave_velocity", "stmg_guess_previous", "stmg_solve_slab_host", "stmg_launch_count",
-           "stmg_time_kernel"]
+           "stmg_time_kernel", "stmg_smooth_noalloc"]
 KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
 
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "stmg_guess_previous": [vp, vp, vp],
         "stmg_solve_slab_host": [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SolveStats)],
         "stmg_launch_count": [vp, ctypes.POINTER(i64)],
+        "stmg_smooth_noalloc": [vp, i32, i32, i32, vp, vp],
         "stmg_time_kernel": [vp, i32, i32, i32, i32, dp],
     }
     for name, args in sig.items():
@@ -208,6 +209,11 @@ class Context:
     def smooth(self, f, u, sweeps=1, level=0):
         self._vec(f, level); self._vec(u, level)
         self._check(self.lib.stmg_smooth(self.h, level, self._prec(u), sweeps, _ptr(f), _ptr(u)))
+
+    def smooth_noalloc(self, f, u, sweeps=1, level=0):
+        """stmg_smooth without device allocation: residual scratch in the library's fixed buffer."""
+        self._vec(f, level); self._vec(u, level)
+        self._check(self.lib.stmg_smooth_noalloc(self.h, level, self._prec(u), sweeps, _ptr(f), _ptr(u)))
 
     def restrict(self, r_fine, r_coarse, level=0):
         self._vec(r_fine, level); self._vec(r_coarse, level + 1)

@@ -950,6 +950,32 @@ stmg_status check_level(stmg_ctx* ctx, int level, int precision) {
 
 }  // namespace
 
+// Fixed scratch for stmg_smooth_noalloc: part of the module image, so every GPU that
+// loads the library holds it until the process exits.  Host code must not use the
+// symbol as a pointer; it asks the runtime for the device address instead.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STMG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the fixed scratch on the current device (looked up once per device).
+stmg_status noalloc_scratch(stmg_ctx* ctx, void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return invalid(ctx, "device index out of range for the fixed scratch");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return STMG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_problem* problem,
@@ -1168,6 +1194,25 @@ stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return s;
+}
+
+stmg_status stmg_smooth_noalloc(stmg_ctx* ctx, int level, int precision, int sweeps, const void* f, void* u) {
+  CKS(check_level(ctx, level, precision));
+  if (level == (int)ctx->levels.size() - 1) return invalid(ctx, "the coarsest level has no smoother");
+  if (sweeps < 0) return invalid(ctx, "sweeps must be >= 0");
+  Level& L = ctx->levels[level];
+  const size_t bytes = (size_t)L.size() * (precision == STMG_FP64 ? sizeof(double) : sizeof(float));
+  if (bytes > (size_t)STMG_NOALLOC_SCRATCH_BYTES)
+    return invalid(ctx, "stmg_smooth_noalloc: level needs " + std::to_string(bytes) +
+                            " bytes of residual scratch, more than the fixed " +
+                            std::to_string((long long)STMG_NOALLOC_SCRATCH_BYTES) + " bytes");
+  void* scratch = nullptr;
+  CKS(noalloc_scratch(ctx, &scratch));
+  StreamJoin join_(ctx);
+  // every sweep overwrites the whole residual before reading it: nothing to clear
+  if (precision == STMG_FP64)
+    return op_smooth<double>(ctx, level, sweeps, (const double*)f, (double*)u, reinterpret_cast<double*>(scratch));
+  return op_smooth<float>(ctx, level, sweeps, (const float*)f, (float*)u, reinterpret_cast<float*>(scratch));
 }
 
 stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {
