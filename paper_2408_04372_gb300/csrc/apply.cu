@@ -1,4 +1,6 @@
 // Matrix-free space-time operator y (+)= sign * (TA (x) A_h + TM (x) M_h) x   (Section 3.1).
+// TA must be diagonal: it is M_tau, diagonal for the Lagrange time bases at quadrature
+// nodes of dG(k) and cGP(k) (the host checks this at set-up).
 //
 // One group of n^(dim-1) threads per cell ("pencil" threads, one per (x,y) node
 // column in 3D, one per x node line in 2D), several cells per CTA.  Per cell and
@@ -112,13 +114,12 @@ apply3d_kernel(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__
     const T m = gc[6 * N3 + q];
 #pragma unroll
     for (int it = 0; it < NT; ++it) {
-      T gx_ = 0, gy_ = 0, gz_ = 0, v = 0;
+      // TA = M_tau is diagonal (Lagrange time basis at the quadrature nodes): no mixing of gradients
+      const T ta = tab.TA[it][it];
+      const T gx_ = ta * ux[it], gy_ = ta * uy[it], gz_ = ta * uz[it];
+      T v = 0;
 #pragma unroll
-      for (int jt = 0; jt < NT; ++jt) {
-        const T ta = tab.TA[it][jt], tm = tab.TM[it][jt];
-        gx_ += ta * ux[jt]; gy_ += ta * uy[jt]; gz_ += ta * uz[jt];
-        v += tm * u[jt][qz];
-      }
+      for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qz];
       s1[I4(it, qz, j, i)] = G00 * gx_ + G01 * gy_ + G02 * gz_;
       s2[I4(it, qz, j, i)] = G01 * gx_ + G11 * gy_ + G12 * gz_;
       fz[it][qz] = G02 * gx_ + G12 * gy_ + G22 * gz_;
@@ -253,13 +254,11 @@ apply2d_kernel(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__
     const T G00 = gc[0 * N2 + q], G01 = gc[1 * N2 + q], G11 = gc[2 * N2 + q], m = gc[3 * N2 + q];
 #pragma unroll
     for (int it = 0; it < NT; ++it) {
-      T gx_ = 0, gy_ = 0, v = 0;
+      const T ta = tab.TA[it][it];
+      const T gx_ = ta * ux[it], gy_ = ta * uy[it];
+      T v = 0;
 #pragma unroll
-      for (int jt = 0; jt < NT; ++jt) {
-        gx_ += tab.TA[it][jt] * ux[jt];
-        gy_ += tab.TA[it][jt] * uy[jt];
-        v += tab.TM[it][jt] * u[jt][qy];
-      }
+      for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qy];
       s0[I3(it, qy, i)] = G00 * gx_ + G01 * gy_;
       fy[it][qy] = G01 * gx_ + G11 * gy_;
       val[it][qy] = m * v;

@@ -12,8 +12,10 @@
 // rounding) and takes N_t times less memory than the dense (N_t (p+1)^dim)^2 block.
 // Constrained (Dirichlet) nodes get identity rows/columns and zero residual.
 //
-// asm_apply: u += omega * sum_T R_T^T L_T^-1 R_T r, one warp-multiple per cell,
-// reading the planes column by column (coalesced); the additive sum over
+// asm_apply: u += omega * sum_T R_T^T L_T^-1 R_T r, one warp-multiple per cell:
+// time transform of the residual, the planes' matrix-vector products with the
+// inverse rows streamed from HBM (the kernel is bound by this stream: N_t
+// (p+1)^(2 dim) numbers per cell), inverse transform; the additive sum over
 // overlapping cells uses atomic adds.
 #include <algorithm>
 
@@ -28,6 +30,10 @@ template <int DIM, int N>
 struct Shape {
   static constexpr int NB = DIM == 3 ? N * N * N : N * N;
 };
+
+// Elements per cell in the inverse store: N_t planes of NB x NB, padded to a multiple
+// of 8 elements so that every cell block starts on a 16-byte boundary (FP32/BF16/FP64).
+__host__ __device__ constexpr int64_t cell_stride(int nb, int nt) { return ((int64_t)nt * nb * nb + 7) / 8 * 8; }
 
 __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ inline double2 cinv(double2 a) {
@@ -174,7 +180,7 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
     // store column-major planes: element (a, b) at b * NB + a
     const int nplanes = m < nreal ? 1 : 2;
     for (int pl = 0; pl < nplanes; ++pl) {
-      const int64_t base = ((int64_t)cell * nt + plane + pl) * NB * NB;
+      const int64_t base = (int64_t)cell * cell_stride(NB, nt) + (int64_t)(plane + pl) * NB * NB;
       for (int pr = tid; pr < NB * NB; pr += blockDim.x) {
         const int b = pr / NB, a = pr % NB;
         const double2 v = C[a * NB + b];
@@ -189,13 +195,36 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
   }
 }
 
+template <typename TI> __device__ inline float to_f(TI v);
+template <typename TI> __device__ inline TI ldg_inv(const TI* p) { return __ldg(p); }
+template <> __device__ inline __nv_bfloat16 ldg_inv<__nv_bfloat16>(const __nv_bfloat16* p) {
+  const unsigned short v = __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __ushort_as_bfloat16(v);
+}
+template <> __device__ inline float to_f<float>(float v) { return v; }
+template <> __device__ inline float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T, typename TI> __device__ inline T inv_val(TI v) { return (T)to_f<TI>(v); }
+template <> __device__ inline double inv_val<double, double>(double v) { return v; }
+template <> __device__ inline float inv_val<float, double>(double v) { return (float)v; }
+
+template <int DIM, int N, int NT, typename TI>
+struct AsmCfg {
+  static constexpr int NB = Shape<DIM, N>::NB;
+  static constexpr int TPC = (NB + 31) / 32 * 32;
+  static constexpr int64_t CS = cell_stride(NB, NT);
+  static constexpr int CPB = TPC >= 128 ? 1 : 128 / TPC;
+};
+
+// One warp-multiple per cell, thread a = local row.  Each thread streams its row of
+// every plane straight from HBM; the column loop is fully unrolled so that all NB
+// loads of a plane are in flight together (the kernel is bound by this stream).
 template <int DIM, int N, int NT, typename T, typename TI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(AsmCfg<DIM, N, NT, TI>::CPB * AsmCfg<DIM, N, NT, TI>::TPC)
 asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g, ModeTab<T> mt) {
-  constexpr int NB = Shape<DIM, N>::NB;
-  constexpr int TPC = (NB + 31) / 32 * 32;
-  constexpr int CPB = TPC >= 128 ? 1 : 128 / TPC;
-  __shared__ T sr[CPB][NT][NB];
+  using C = AsmCfg<DIM, N, NT, TI>;
+  constexpr int NB = C::NB, TPC = C::TPC, CPB = C::CPB;
+  constexpr int64_t CS = C::CS;
+  __shared__ T s_r[CPB][NT][NB];
   const int slot = threadIdx.x / TPC;
   const int a = threadIdx.x - slot * TPC;
   const int64_t cell = (int64_t)blockIdx.x * CPB + slot;
@@ -216,38 +245,38 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
   if (a < NB) {
 #pragma unroll
     for (int m = 0; m < NT; ++m) {
-      // plane m: real mode m (m < nreal) or re/im of complex mode (m - nreal) / 2
+      // plane m: real mode m (m < nreal) or re/im part of complex mode nreal + (m - nreal) / 2
       const bool is_real = m < mt.nreal;
       const int mode = is_real ? m : mt.nreal + (m - mt.nreal) / 2;
       const bool im_part = !is_real && ((m - mt.nreal) & 1);
       T v = 0;
 #pragma unroll
       for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[t];
-      sr[slot][m][a] = v;
+      s_r[slot][m][a] = v;
     }
   }
   __syncthreads();
   if (!live) return;
-  const TI* ic = inv + (size_t)cell * NT * NB * NB;
+  const TI* ic = inv + cell * CS;
   T z[NT];
 #pragma unroll
   for (int m = 0; m < NT; ++m) z[m] = 0;
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
     if (m < mt.nreal) {
-      const TI* pl = ic + (size_t)m * NB * NB;
+      const TI* pl = ic + m * NB * NB + a;
       T acc = 0;
-#pragma unroll 9
-      for (int b = 0; b < NB; ++b) acc += (T)load_f(pl + b * NB + a) * sr[slot][m][b];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) acc += inv_val<T, TI>(ldg_inv(pl + b * NB)) * s_r[slot][m][b];
       z[m] = acc;
     } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
-      const TI* pr_ = ic + (size_t)m * NB * NB;
+      const TI* pr_ = ic + m * NB * NB + a;
       const TI* pi_ = pr_ + NB * NB;
       T zr = 0, zi = 0;
-#pragma unroll 9
+#pragma unroll
       for (int b = 0; b < NB; ++b) {
-        const T ir = (T)load_f(pr_ + b * NB + a), ii = (T)load_f(pi_ + b * NB + a);
-        const T sre = sr[slot][m][b], sim = sr[slot][m + 1][b];
+        const T ir = inv_val<T, TI>(ldg_inv(pr_ + b * NB)), ii = inv_val<T, TI>(ldg_inv(pi_ + b * NB));
+        const T sre = s_r[slot][m][b], sim = s_r[slot][m + 1][b];
         zr += ir * sre - ii * sim;
         zi += ir * sim + ii * sre;
       }
@@ -286,15 +315,15 @@ cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, 
 
 template <int DIM, int N, int NT, typename T, typename TI>
 cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s) {
-  constexpr int NB = Shape<DIM, N>::NB;
-  constexpr int TPC = (NB + 31) / 32 * 32;
-  constexpr int CPB = TPC >= 128 ? 1 : 128 / TPC;
-  const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
-  asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, CPB * TPC, 0, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt);
+  using C = AsmCfg<DIM, N, NT, TI>;
+  const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
+  asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, C::CPB * C::TPC, 0, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+int64_t asm_cell_stride(int dim, int n, int nt) { return cell_stride(dim == 3 ? n * n * n : n * n, nt); }
 
 cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
                              const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,

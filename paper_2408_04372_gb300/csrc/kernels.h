@@ -32,6 +32,8 @@ struct LocalTab {        // 1D tables of the nodal basis at Gauss points (setup 
 cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
                              const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
                              int inv_prec, cudaStream_t s);
+// elements per cell in the inverse store (N_t planes, padded to a 16-byte multiple)
+int64_t asm_cell_stride(int dim, int n, int nt);
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
                              const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s);

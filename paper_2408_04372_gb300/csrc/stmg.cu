@@ -480,7 +480,8 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     return STMG_ERR_UNSUPPORTED;
   }
   const size_t esz = L.inv_prec == 0 ? 8 : L.inv_prec == 1 ? 4 : 2;
-  const size_t count = (size_t)L.g.n_cells * nt * NB * NB;
+  (void)NB;
+  const size_t count = (size_t)L.g.n_cells * asm_cell_stride(L.dim, L.n, nt);
   void* inv = nullptr;
   cudaError_t e = cudaMalloc(&inv, count * esz);
   if (e != cudaSuccess) { ctx->err = std::string("cudaMalloc inverses: ") + cudaGetErrorString(e); return STMG_ERR_OOM; }
@@ -648,6 +649,12 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     L.g.n_nodes = dim == 3 ? (int64_t)L.g.nn1 * L.g.nn1 * L.g.nn1 : (int64_t)L.g.nn1 * L.g.nn1;
     L.g.n_cells = dim == 3 ? (int64_t)L.N * L.N * L.N : (int64_t)L.N * L.N;
     L.sc = slab_coeffs(pr->pde, pr->time_scheme, L.k, pr->tau);
+    for (int i = 0; i < L.nt; ++i)
+      for (int j = 0; j < L.nt; ++j)
+        if (i != j && std::fabs(L.sc.TA[i * L.nt + j]) > 1e-13 * std::fabs(L.sc.TA[i * L.nt + i])) {
+          ctx->err = "time mass matrix is not diagonal";
+          return STMG_ERR_INTERNAL;
+        }
     fill_tables(L);
     // vertices: every (N/N_l)-th fine vertex
     const int r = N / L.N;

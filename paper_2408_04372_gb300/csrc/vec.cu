@@ -1,5 +1,6 @@
 // Vector kernels of the FP64 outer FGMRES and small helpers: conversions,
-// deterministic multi-dot products (two-stage reduction in a fixed order),
+// deterministic multi-dot products (two-stage reduction in a fixed order: per-block
+// partial sums in a scratch buffer, then one block per product),
 // multi-AXPY, time-only mixing of nodal blocks, the dense coarsest-level solve.
 #include <algorithm>
 
@@ -50,14 +51,14 @@ __device__ inline double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-// stage 1: partial[b * stride + j] = sum over block b's slice of V_j . w ; j = nv holds w . w
+// stage 1: partial[j * nblocks + b] = sum over block b's fixed slice of V_j . w ; j = nv holds w . w
 __global__ void __launch_bounds__(kDotThreads)
-multidot_stage1(PtrList V, int nv, const double* __restrict__ w, int64_t n, int with_norm, double* __restrict__ partial,
-                int stride) {
-  __shared__ double red[kDotThreads / 32];
+multidot_stage1(PtrList V, int nv, const double* __restrict__ w, int64_t n, int with_norm, double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32][kChunk];
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * per, hi = std::min<int64_t>(n, lo + per);
   const int ntot = nv + (with_norm ? 1 : 0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j0 = 0; j0 < ntot; j0 += kChunk) {
     double acc[kChunk];
 #pragma unroll
@@ -67,26 +68,35 @@ multidot_stage1(PtrList V, int nv, const double* __restrict__ w, int64_t n, int 
 #pragma unroll
       for (int c = 0; c < kChunk; ++c) {
         const int j = j0 + c;
-        if (j < nv) acc[c] += V.p[j][i] * wi;
+        if (j < nv) acc[c] += __ldg(V.p[j] + i) * wi;
         else if (j == nv && with_norm) acc[c] += wi * wi;
       }
     }
 #pragma unroll
     for (int c = 0; c < kChunk; ++c) {
-      if (j0 + c >= ntot) break;
-      const double s = block_sum(acc[c], red);
-      if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * stride + j0 + c] = s;
+      double v = acc[c];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][c] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < kChunk && j0 + (int)threadIdx.x < ntot) {
+      double s = 0.0;
+      for (int wv = 0; wv < kDotThreads / 32; ++wv) s += red[wv][threadIdx.x];
+      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
   }
 }
 
-__global__ void multidot_stage2(const double* __restrict__ partial, int nblocks, int stride, int ntot,
-                                double* __restrict__ out) {
-  for (int j = threadIdx.x; j < ntot; j += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * stride + j];
-    out[j] = s;
-  }
+// stage 2: block j sums partial[j][0..nblocks) by a fixed-order tree
+__global__ void __launch_bounds__(kDotThreads)
+multidot_stage2(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  __shared__ double red[kDotThreads / 32];
+  const double* p = partial + (int64_t)blockIdx.x * nblocks;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += p[b];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 __global__ void multi_axpy_kernel(double* __restrict__ w, PtrList V, const double* __restrict__ h, int nv, double sign,
@@ -175,9 +185,8 @@ cudaError_t launch_multidot(const double* const* V, int nv, const double* w, int
   PtrList pl{};
   for (int j = 0; j < nv; ++j) pl.p[j] = V[j];
   const int ntot = nv + (with_norm ? 1 : 0);
-  const int stride = ntot;
-  multidot_stage1<<<nblocks, kDotThreads, 0, s>>>(pl, nv, w, n, with_norm, partial, stride);
-  multidot_stage2<<<1, 128, 0, s>>>(partial, nblocks, stride, ntot, out);
+  multidot_stage1<<<nblocks, kDotThreads, 0, s>>>(pl, nv, w, n, with_norm, partial);
+  multidot_stage2<<<ntot, kDotThreads, 0, s>>>(partial, nblocks, out);
   return cudaGetLastError();
 }
 
