@@ -238,11 +238,7 @@ def run_ours(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launch_count() - launches0
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
-    value = world * dofs_per_step * args.steps / (ms / 1e3)
+    ms, value = aggregate_replicas(ms, dofs_per_step, args.steps, world, dev)
 
     # end to end through the C ABI from pinned host buffers (H2D of f and u0, D2H of u each step)
     Fh = torch.empty((n_slabs, nt * nn), dtype=torch.float64).pin_memory()
@@ -307,6 +303,17 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def aggregate_replicas(ms_local, dofs_per_step, steps, world, device):
+    """Replicas only: slowest rank's time, every rank's DoFs.  Returns (max ms, whole-job DoF/s)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * dofs_per_step * steps / (ms / 1e3)
 
 
 def radau_nodes(k):

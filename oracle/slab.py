@@ -13,6 +13,8 @@ The source enters as its nodal interpolant at the space-time nodes
 """
 from __future__ import annotations
 
+import itertools
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -153,3 +155,64 @@ def l2l2_error(prob: SlabProblem, sols, exact, u_init, t0=0.0) -> float:
             err2 += s.tau * wtq[it] * np.sum(jw * (uh - ue) ** 2)
         u_prev = u[-1]
     return float(np.sqrt(err2))
+
+
+def sampled_rows(grid: Grid, rho_qp: np.ndarray, pde: str, scheme: str, k: int, tau: float,
+                 x: np.ndarray, samples) -> np.ndarray:
+    """(S x)[t, node] for a list of (t, node) pairs, from the element matrices of the touching cells only.
+
+    Same definition as SlabProblem.S (identity on constrained rows, constrained columns ignored),
+    for grids too large to assemble.  x has shape (N_t, n_nodes).
+    """
+    sysm = timeint.slab_system(pde, scheme, k, tau)
+    nn1, p, N, dim = grid.nn1, grid.p, grid.N, grid.dim
+    bmask = grid.boundary_mask()
+    xm = np.where(bmask[None, :], 0.0, x)
+    out = []
+    for t, node in samples:
+        if bmask[node]:
+            out.append(x[t, node])
+            continue
+        g = [(node // nn1 ** d) % nn1 for d in range(dim)]
+        cands = [[] for _ in range(dim)]
+        for d in range(dim):
+            c0 = g[d] // p
+            cands[d] = sorted({c for c in (c0 - 1, c0) if 0 <= c < N and c * p <= g[d] <= (c + 1) * p})
+        cells = np.array([sum(c[d] * N ** d for d in range(dim)) for c in itertools.product(*cands)])
+        A_e, M_e = grid.element_matrices(rho_qp, cells=cells)
+        dofs = grid.node_id(grid.cells[cells][:, None, :] * p + grid.local[None, :, :])
+        val = 0.0
+        for ci in range(len(cells)):
+            a = int(np.nonzero(dofs[ci] == node)[0][0])
+            for j in range(sysm.tw.nt):
+                xl = xm[j, dofs[ci]]
+                val += sysm.TA[t, j] * (A_e[ci, a] @ xl) + sysm.TM[t, j] * (M_e[ci, a] @ xl)
+        out.append(val)
+    return np.array(out)
+
+
+def kron_apply(grid: Grid, rho_qp: np.ndarray, TA: np.ndarray, TM: np.ndarray, x: np.ndarray,
+               constrained: bool = True, A_e=None, M_e=None) -> np.ndarray:
+    """y = (TA (x) A_h + TM (x) M_h) x cell by cell from element matrices (no global assembly).
+
+    TA, TM: (n_out, n_in); x: (n_in, n_nodes).  constrained=True gives the slab operator
+    convention (identity on constrained rows, constrained columns ignored, needs n_in == n_out);
+    constrained=False applies the plain matrices and zeroes constrained rows (right-hand sides).
+    """
+    if A_e is None:
+        A_e, M_e = grid.element_matrices(rho_qp)
+    dofs = grid.cell_dofs()
+    bmask = grid.boundary_mask()
+    xm = np.where(bmask[None, :], 0.0, x) if constrained else x
+    xc = xm[:, dofs]                                    # (n_in, cells, nb)
+    yA = np.einsum("cab,jcb->jca", A_e, xc)
+    yM = np.einsum("cab,jcb->jca", M_e, xc)
+    yc = np.einsum("ij,jca->ica", TA, yA) + np.einsum("ij,jca->ica", TM, yM)
+    y = np.zeros((TA.shape[0], grid.n_nodes))
+    for i in range(TA.shape[0]):
+        y[i] = np.bincount(dofs.reshape(-1), weights=yc[i].reshape(-1), minlength=grid.n_nodes)
+    if constrained:
+        y[:, bmask] = x[:, bmask]
+    else:
+        y[:, bmask] = 0.0
+    return y

@@ -72,10 +72,11 @@ class Grid:
         return idx
 
     # ---- Q1 geometry ----
-    def cell_vertices(self) -> np.ndarray:
+    def cell_vertices(self, cells=None) -> np.ndarray:
         """(ncells, 2^dim, dim) vertex coordinates, vertex bits lexicographic (x fastest)."""
         bits = lex_indices(2, self.dim)
-        vid = self.vertex_id(self.cells[:, None, :] + bits[None, :, :])
+        cidx = self.cells if cells is None else self.cells[cells]
+        vid = self.vertex_id(cidx[:, None, :] + bits[None, :, :])
         return self.vertices[vid]
 
     def q1_shape(self, xi: np.ndarray):
@@ -98,10 +99,10 @@ class Grid:
         val, _ = self.q1_shape(xi)
         return np.einsum("mv,cvd->cmd", val, self.cell_vertices())
 
-    def jacobians(self, xi: np.ndarray) -> np.ndarray:
+    def jacobians(self, xi: np.ndarray, cells=None) -> np.ndarray:
         """J[c, m, d, e] = d x_d / d xi_e at reference points xi."""
         _, grad = self.q1_shape(xi)
-        return np.einsum("mve,cvd->cmde", grad, self.cell_vertices())
+        return np.einsum("mve,cvd->cmde", grad, self.cell_vertices(cells))
 
     def quad_points_ref(self) -> np.ndarray:
         return self.xq[self.qloc]                  # (nq^dim, dim)
@@ -139,14 +140,16 @@ class Grid:
         return phi, dphi
 
     # ---- element and global matrices ----
-    def element_matrices(self, rho_qp: np.ndarray):
-        """A_e, M_e (ncells, nb, nb) by Gauss quadrature on the Q1-mapped cells.
+    def element_matrices(self, rho_qp: np.ndarray, cells=None):
+        """A_e, M_e (ncells, nb, nb) by Gauss quadrature on the Q1-mapped cells (or a subset `cells`).
 
         A_e[a, b] = sum_q w_q |det J| rho_q (J^-T grad phi_a) . (J^-T grad phi_b)
         M_e[a, b] = sum_q w_q |det J| phi_a phi_b
         """
         phi, dphi = self.ref_basis()
-        J = self.jacobians(self.quad_points_ref())         # (c, q, d, e)
+        J = self.jacobians(self.quad_points_ref(), cells)  # (c, q, d, e)
+        if cells is not None:
+            rho_qp = rho_qp[cells]
         det = np.linalg.det(J)
         Jinv = np.linalg.inv(J)                            # (c, q, e, d)
         w = self.quad_weights()

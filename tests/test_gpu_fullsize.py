@@ -1,0 +1,171 @@
+"""GPU path at the workload sizes the bench times, and slab marching against the oracle.
+
+Full-size grids are too large for the oracle's direct solve: the operator is compared on
+sampled rows (computed from the element matrices of the touching cells), and full-size
+solves are checked by the property the method guarantees (FP64 residual below rtol, with the
+residual evaluated by the oracle's own assembled matrices where they fit in host memory).
+The marching tests run the whole slab loop (right-hand side, previous-slab guess, FGMRES,
+velocity update) on GPU and oracle and compare every slab.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_cases import rel_err, require_gpu
+from oracle import mg, slab, space
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+def _samples(nt, n_nodes, count, seed):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(nt)), int(rng.integers(n_nodes))) for _ in range(count)]
+
+
+WORKLOADS = {
+    # name: (dim, N, p, k, pde, scheme, tau, vertices, rho_cell)
+    "c2_heat3d_q2_dg2_32": lambda: (3, 32, 2, 2, "heat", "dg", 1 / 32, synth.jittered_vertices(32, 3),
+                                    synth.block_coefficient(32, 3, blocks=4)),
+    "c3_wave3d_q3_cgp2_24": lambda: (3, 24, 3, 2, "wave", "cgp", 1 / 64, synth.jittered_vertices(24, 3),
+                                     synth.layer_coefficient(24, 3, 1.0, 16.0)),
+    "c5_heat3d_q2_dg1_48": lambda: (3, 48, 2, 1, "heat", "dg", 1 / 256, synth.cartesian_vertices(48, 3),
+                                    np.ones(48 ** 3)),
+}
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_full_size_apply_on_sampled_rows(env, name):
+    torch, stmg = env
+    dim, N, p, k, pde, scheme, tau, V, rho = WORKLOADS[name]()
+    ctx = stmg.Context(dim, N, p, k, tau, pde=stmg.HEAT if pde == "heat" else stmg.WAVE,
+                       scheme=stmg.DG if scheme == "dg" else stmg.CGP, vertices=V, coeff=rho,
+                       omega=[0.2] * 16)
+    nt, nn = ctx.nt, ctx.n_nodes
+    x = synth.random_vector((nt, nn), seed=21)
+    g = space.Grid(N, dim, p, V)
+    rq = space.rho_qp_from_cells(g, rho)
+    samples = _samples(nt, nn, 60, seed=22)
+    # include constrained rows and a corner region
+    samples += [(0, 0), (nt - 1, nn - 1), (nt - 1, g.nn1 * g.nn1 + g.nn1 + 1)]
+    ref = slab.sampled_rows(g, rq, pde, scheme, k, tau, x, samples)
+    for dt, tol in ((torch.float64, 1e-10), (torch.float32, 2e-5)):
+        xd = torch.from_numpy(x.reshape(-1)).to("cuda", dt)
+        yd = torch.empty_like(xd)
+        ctx.apply(xd, yd)
+        y = yd.cpu().numpy().astype(np.float64).reshape(nt, nn)
+        got = np.array([y[t, n] for t, n in samples])
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() < tol * scale, (name, dt)
+    ctx.close()
+
+
+def test_full_size_bench_slab_solve_meets_rtol_in_oracle_residual(env):
+    """Bench workload, one slab from the previous-slab guess: the oracle's assembled S confirms rtol."""
+    torch, stmg = env
+    dim, N, p, k, pde, scheme, tau, V, rho = WORKLOADS["c2_heat3d_q2_dg2_32"]()
+    ctx = stmg.Context(dim, N, p, k, tau, vertices=V, coeff=rho, vcycle_precision=stmg.FP32, rtol=1e-8)
+    nt, nn = ctx.nt, ctx.n_nodes
+    X = ctx.node_coords()
+    from oracle import fe1d
+    tn = fe1d.gauss_radau_right(k + 1)[0]
+    f = np.stack([synth.heat_sine_source(X, tau * (3 + th)) for th in tn])
+    u0 = synth.heat_sine_solution(X, 3 * tau)
+    g = space.Grid(N, dim, p, V)
+    bm = g.boundary_mask()
+    u0[bm] = 0.0
+    fd = torch.from_numpy(f.reshape(-1).copy()).cuda()
+    u0d = torch.from_numpy(u0).cuda()
+    rhs = torch.empty(nt * nn, dtype=torch.float64, device="cuda")
+    ctx.rhs(fd, rhs, u0=u0d)
+    u = torch.empty_like(rhs)
+    ctx.guess_previous(u0d, u)
+    st = ctx.solve(rhs, u)
+    assert st["converged"] and st["rel_residual"] <= 1e-8
+    from oracle import timeint
+    s = timeint.slab_system(pde, scheme, k, tau)
+    rq = space.rho_qp_from_cells(g, rho)
+    A_e, M_e = g.element_matrices(rq)
+    Z = np.zeros((nt, nt))
+    rhs_ref = slab.kron_apply(g, rq, Z, s.RM_f, f, constrained=False, A_e=A_e, M_e=M_e)
+    rhs_ref += slab.kron_apply(g, rq, np.zeros((nt, 1)), s.RM_u0[:, None], u0[None, :], constrained=False,
+                               A_e=A_e, M_e=M_e)
+    assert rel_err(rhs.cpu().numpy(), rhs_ref) < 1e-12
+    Su = slab.kron_apply(g, rq, s.TA, s.TM, u.cpu().numpy().reshape(nt, nn), A_e=A_e, M_e=M_e)
+    r = rhs_ref - Su
+    assert np.linalg.norm(r) <= 1.05e-8 * np.linalg.norm(rhs_ref)
+    ctx.close()
+
+
+def _march_gpu(ctx, torch, f_slabs, f0_slabs, u_init, v_init, wave):
+    nt, nn = ctx.nt, ctx.n_nodes
+    u_prev = torch.from_numpy(u_init.copy()).cuda()
+    v_prev = torch.from_numpy(v_init.copy()).cuda() if wave else None
+    rhs = torch.empty(nt * nn, dtype=torch.float64, device="cuda")
+    out_u, out_v = [], []
+    for n in range(len(f_slabs)):
+        fd = torch.from_numpy(f_slabs[n].reshape(-1).copy()).cuda()
+        f0 = None if f0_slabs is None else torch.from_numpy(f0_slabs[n].copy()).cuda()
+        ctx.rhs(fd, rhs, f0=f0, u0=u_prev, v0=v_prev)
+        u = torch.empty_like(rhs)
+        ctx.guess_previous(u_prev, u)
+        st = ctx.solve(rhs, u)
+        assert st["converged"], st
+        out_u.append(u.cpu().numpy().reshape(nt, nn))
+        if wave:
+            v = torch.empty_like(rhs)
+            ctx.wave_velocity(u, u_prev, v_prev, v)
+            out_v.append(v.cpu().numpy().reshape(nt, nn))
+            v_prev = v[(nt - 1) * nn:].clone()
+        u_prev = u[(nt - 1) * nn:].clone()
+    return out_u, out_v
+
+
+def test_c1_heat2d_marching_matches_oracle(env):
+    """Config 1 at full size: 2D Q2 on 16^2, dG(1), 16 slabs, rtol 1e-10."""
+    torch, stmg = env
+    dim, N, p, k, tau, slabs = 2, 16, 2, 1, 1 / 16, 16
+    V = synth.cartesian_vertices(N, dim)
+    H = mg.Hierarchy(dim, N, p, k, "heat", "dg", tau, V, estimate=False, omegas=[0.4] * 8)
+    prob = H.levels[0].prob
+    sols, _ = slab.march(prob, slabs, synth.heat_sine_source)
+    X = prob.grid.node_coords()
+    tn = prob.sys.tw.nodes
+    fs = [np.stack([synth.heat_sine_source(X, tau * (n + th)) for th in tn]) for n in range(slabs)]
+    for prec in (stmg.FP64, stmg.FP32):
+        ctx = stmg.Context(dim, N, p, k, tau, vertices=V, vcycle_precision=prec, rtol=1e-10)
+        gu, _ = _march_gpu(ctx, torch, fs, None, np.zeros(prob.grid.n_nodes), None, False)
+        for n in range(slabs):
+            err = np.linalg.norm(gu[n] - sols[n]) / np.linalg.norm(sols[n])
+            assert err < 1e-8, (prec, n, err)
+        ctx.close()
+    # the discrete solution converges to the manufactured one (order 3 in h at this tau is masked
+    # by the dG(1) time error; the error level is what the paper's figures show for Q2/dG(1))
+    assert slab.l2l2_error(prob, sols, synth.heat_sine_solution, np.zeros(prob.grid.n_nodes)) < 5e-3
+
+
+def test_c3_wave_marching_matches_oracle_on_reduced_grid(env):
+    """Config 3 family (Q3, cGP(2) wave, two layers, jittered) on 6^3 cells, 8 slabs, with velocities."""
+    torch, stmg = env
+    dim, N, p, k, tau, slabs = 3, 6, 3, 2, 1 / 64, 8
+    V = synth.jittered_vertices(N, dim)
+    rho = synth.layer_coefficient(N, dim, 1.0, 16.0)
+    g = space.Grid(N, dim, p, V)
+    prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, rho), "wave", "cgp", k, tau)
+    X = g.node_coords()
+    u_init = synth.wave_pulse(X)
+    u_init[prob.bmask] = 0.0
+    sols, vels = slab.march(prob, slabs, None, u_init=u_init)
+    zero = [np.zeros((prob.nt, g.n_nodes))] * slabs
+    zero0 = [np.zeros(g.n_nodes)] * slabs
+    ctx = stmg.Context(dim, N, p, k, tau, pde=stmg.WAVE, scheme=stmg.CGP, vertices=V, coeff=rho,
+                       vcycle_precision=stmg.FP32, rtol=1e-12, max_it=400)
+    gu, gv = _march_gpu(ctx, torch, zero, zero0, u_init, np.zeros(g.n_nodes), True)
+    for n in range(slabs):
+        assert np.linalg.norm(gu[n] - sols[n]) < 1e-8 * np.linalg.norm(sols[n]), n
+        assert np.linalg.norm(gv[n] - vels[n]) < 1e-7 * np.linalg.norm(vels[n]), n
+    ctx.close()

@@ -91,3 +91,22 @@ def test_wave_cgp2_time_order():
         sols, _ = slab.march(prob, n, None, u_init=u_init)
         errs.append(slab.l2l2_error(prob, sols, exact, u_init))
     assert abs(math.log2(errs[0] / errs[1]) - 3.0) < 0.3
+
+
+def test_matrix_free_and_sampled_rows_equal_assembled_operator():
+    g = space.Grid(4, 3, 2, synth.jittered_vertices(4, 3))
+    rho = space.rho_qp_from_cells(g, synth.block_coefficient(4, 3, blocks=2))
+    prob = slab.SlabProblem(g, rho, "heat", "dg", 2, 0.1)
+    x = synth.random_vector((3, g.n_nodes))
+    ref = prob.apply(x)
+    assert np.abs(slab.kron_apply(g, rho, prob.sys.TA, prob.sys.TM, x) - ref).max() < 1e-12 * np.abs(ref).max()
+    rng = np.random.default_rng(1)
+    samples = [(int(rng.integers(3)), int(rng.integers(g.n_nodes))) for _ in range(30)] + [(0, 0)]
+    got = slab.sampled_rows(g, rho, "heat", "dg", 2, 0.1, x, samples)
+    assert np.abs(got - np.array([ref[t, n] for t, n in samples])).max() < 1e-12 * np.abs(ref).max()
+    f = synth.random_vector((3, g.n_nodes))
+    u0 = synth.random_vector(g.n_nodes)
+    u0[prob.bmask] = 0.0
+    rhs = slab.kron_apply(g, rho, np.zeros((3, 3)), prob.sys.RM_f, f, constrained=False)
+    rhs += slab.kron_apply(g, rho, np.zeros((3, 1)), prob.sys.RM_u0[:, None], u0[None, :], constrained=False)
+    assert np.abs(rhs - prob.rhs(f, None, u0)).max() < 1e-13
