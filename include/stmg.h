@@ -167,6 +167,35 @@ stmg_status stmg_guess_previous(stmg_ctx* ctx, const double* u0, double* u);
 stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f0, const double* u0,
                                  const double* v0, double* u, double* v, stmg_solve_stats* stats);
 
+/* ---- Learned initial guess (not in the paper) ----
+ * A chain of `layers` 3x3x3 convolutions on the finest node grid (zero padding),
+ * ReLU between layers, BF16 activations and weights with FP32 accumulation on the
+ * tensor cores; trained with Adam on FP32 master weights by the library's own
+ * forward and backward kernels.  Input channels: the previous slab's N_t time
+ * blocks times scales[0] and the slab's source at its N_t time nodes times
+ * scales[1]; output: N_t channels c, the guess is u_prev_end + c / scales[2] on
+ * unconstrained nodes (u_prev_end = last time block of the previous slab).
+ * channels: layers+1 counts (channels[0] = 2 N_t, channels[layers] = N_t, all <= 64);
+ * weights: HOST FP64, per layer [co][ci][27] concatenated, tap = (dx+1)+3(dy+1)+9(dz+1);
+ * biases: HOST FP64, per layer [co] concatenated.  All vectors: device FP64 [N_t][n_nodes]. */
+typedef struct stmg_net stmg_net;
+stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int* channels, const double* weights,
+                            const double* biases, const double* scales);
+stmg_status stmg_net_destroy(stmg_net* net);
+/* u_guess = network guess for the slab after u_prev, from the slab's source f. */
+stmg_status stmg_net_predict(stmg_net* net, const double* u_prev, const double* f, double* u_guess);
+/* One Adam step (lr) on the mean squared error against the scaled target
+ * (u_target - u_prev_end) * scales[2] over unconstrained nodes; *loss (host) receives the loss
+ * before the step.  Synchronous. */
+stmg_status stmg_net_train_step(stmg_net* net, const double* u_prev, const double* f, const double* u_target,
+                                double lr, double* loss);
+/* Loss, parameter gradients (HOST, same layouts as weights/biases) and the raw network output
+ * (HOST [N_t][n_nodes], before scaling back) without updating; any output may be NULL.  Synchronous. */
+stmg_status stmg_net_gradients(stmg_net* net, const double* u_prev, const double* f, const double* u_target,
+                               double* loss, double* grad_w, double* grad_b, double* out);
+/* Current FP32 master parameters (HOST, FP64 arrays in the layouts of stmg_net_create). */
+stmg_status stmg_net_weights(stmg_net* net, double* weights, double* biases);
+
 /* Smoothing without any device allocation.  Same result as stmg_smooth, but the
  * residual f - S_l u of each sweep is kept in a fixed buffer of
  * STMG_NOALLOC_SCRATCH_BYTES bytes that is part of the library's device image

@@ -26,7 +26,8 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_node_coords", "stmg_qpoint_coords", "stmg_apply", "stmg_residual", "stmg_smooth",
            "stmg_restrict", "stmg_prolongate_add", "stmg_vcycle", "stmg_rhs", "stmg_solve",
            "stmg_wave_velocity", "stmg_guess_previous", "stmg_solve_slab_host", "stmg_launch_count",
-           "stmg_time_kernel", "stmg_smooth_noalloc"]
+           "stmg_time_kernel", "stmg_smooth_noalloc", "stmg_net_create", "stmg_net_destroy", "stmg_net_predict",
+           "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights"]
 KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
 
 
@@ -90,6 +91,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "stmg_solve_slab_host": [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SolveStats)],
         "stmg_launch_count": [vp, ctypes.POINTER(i64)],
         "stmg_smooth_noalloc": [vp, i32, i32, i32, vp, vp],
+        "stmg_net_create": [ctypes.POINTER(vp), vp, i32, ctypes.POINTER(i32), dp, dp, dp],
+        "stmg_net_destroy": [vp],
+        "stmg_net_predict": [vp, vp, vp, vp],
+        "stmg_net_train_step": [vp, vp, vp, vp, ctypes.c_double, dp],
+        "stmg_net_gradients": [vp, vp, vp, vp, dp, dp, dp, dp],
+        "stmg_net_weights": [vp, dp, dp],
         "stmg_time_kernel": [vp, i32, i32, i32, i32, dp],
     }
     for name, args in sig.items():
@@ -271,3 +278,63 @@ class Context:
             self._check(code)
         stats = dict(iterations=st.iterations, rel_residual=st.rel_residual, converged=code == 0)
         return (u, v, stats) if want_v else (u, stats)
+
+
+class Net:
+    """Learned initial guess bound to a context (stmg_net_* in include/stmg.h)."""
+
+    def __init__(self, ctx: Context, channels, weights, biases, scales):
+        import numpy as np
+        self.ctx, self.lib = ctx, ctx.lib
+        self.channels = list(channels)
+        self.L = len(channels) - 1
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in weights]))
+        b = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in biases]))
+        sc = np.ascontiguousarray(np.asarray(scales, np.float64))
+        ch = (ctypes.c_int * len(channels))(*channels)
+        h = ctypes.c_void_p()
+        ctx._check(self.lib.stmg_net_create(ctypes.byref(h), ctx.h, self.L, ch, _dptr(w), _dptr(b), _dptr(sc)))
+        self.h = h
+        self._nw, self._nb = w.size, b.size
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stmg_net_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _split(self, flat_w, flat_b):
+        W, B, ow, ob = [], [], 0, 0
+        for l in range(self.L):
+            ci, co = self.channels[l], self.channels[l + 1]
+            W.append(flat_w[ow:ow + co * ci * 27].reshape(co, ci, 27))
+            B.append(flat_b[ob:ob + co])
+            ow += co * ci * 27
+            ob += co
+        return W, B
+
+    def predict(self, u_prev, f, guess):
+        self.ctx._check(self.lib.stmg_net_predict(self.h, _ptr(u_prev), _ptr(f), _ptr(guess)))
+
+    def train_step(self, u_prev, f, u_target, lr):
+        loss = ctypes.c_double()
+        self.ctx._check(self.lib.stmg_net_train_step(self.h, _ptr(u_prev), _ptr(f), _ptr(u_target), lr,
+                                                     ctypes.byref(loss)))
+        return loss.value
+
+    def gradients(self, u_prev, f, u_target):
+        import numpy as np
+        gw, gb = np.zeros(self._nw), np.zeros(self._nb)
+        out = np.zeros((self.ctx.nt, self.ctx.n_nodes))
+        loss = ctypes.c_double()
+        self.ctx._check(self.lib.stmg_net_gradients(self.h, _ptr(u_prev), _ptr(f), _ptr(u_target), ctypes.byref(loss),
+                                                    _dptr(gw), _dptr(gb), _dptr(out)))
+        W, B = self._split(gw, gb)
+        return loss.value, W, B, out
+
+    def weights(self):
+        import numpy as np
+        w, b = np.zeros(self._nw), np.zeros(self._nb)
+        self.ctx._check(self.lib.stmg_net_weights(self.h, _dptr(w), _dptr(b)))
+        return self._split(w, b)

@@ -10,6 +10,7 @@
 #include "../../include/stmg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "net.h"
 #include "tables.h"
 
 using namespace stmg;
@@ -1220,6 +1221,190 @@ stmg_status stmg_smooth_noalloc(stmg_ctx* ctx, int level, int precision, int swe
   if (precision == STMG_FP64)
     return op_smooth<double>(ctx, level, sweeps, (const double*)f, (double*)u, reinterpret_cast<double*>(scratch));
   return op_smooth<float>(ctx, level, sweeps, (const float*)f, (float*)u, reinterpret_cast<float*>(scratch));
+}
+
+
+// ------------------------------------------------------------------ learned initial guess
+struct stmg_net {
+  stmg_ctx* ctx = nullptr;
+  NetDev d;
+  std::vector<void*> allocs;
+  std::vector<int> ch;
+};
+
+static stmg_status net_alloc(stmg_net* net, void** p, size_t bytes) {
+  stmg_ctx* ctx = net->ctx;
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    ctx->err = std::string("cudaMalloc (net): ") + cudaGetErrorString(e);
+    return STMG_ERR_OOM;
+  }
+  net->allocs.push_back(*p);
+  return cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), ctx->stream) == cudaSuccess ? STMG_OK : STMG_ERR_CUDA;
+}
+
+stmg_status stmg_net_destroy(stmg_net* net) {
+  if (!net) return STMG_OK;
+  if (net->ctx && net->ctx->stream) cudaStreamSynchronize(net->ctx->stream);
+  for (void* p : net->allocs) cudaFree(p);
+  delete net;
+  return STMG_OK;
+}
+
+stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int* channels, const double* weights,
+                            const double* biases, const double* scales) {
+  if (!out || !ctx || !channels || !weights || !biases || !scales) return STMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  Level& L0 = ctx->levels[0];
+  if (layers < 1 || layers > kNetMaxLayers) return invalid(ctx, "layers must be in 1..8");
+  if (channels[0] != 2 * L0.nt || channels[layers] != L0.nt)
+    return invalid(ctx, "network must map 2 N_t input channels to N_t output channels");
+  for (int l = 0; l <= layers; ++l)
+    if (channels[l] < 1 || channels[l] > 64) return invalid(ctx, "channel counts must be in 1..64");
+  StreamJoin join_(ctx);
+  stmg_net* net = new stmg_net();
+  net->ctx = ctx;
+  NetDev& d = net->d;
+  d.L = layers;
+  d.nt = L0.nt;
+  d.nx = L0.g.nn1;
+  d.ny = L0.g.nn1;
+  d.nz = L0.dim == 3 ? L0.g.nn1 : 1;
+  d.V = L0.g.n_nodes;
+  d.su = (float)scales[0];
+  d.sf = (float)scales[1];
+  d.so = (float)scales[2];
+  for (int l = 0; l <= layers; ++l) { d.ch[l] = channels[l]; d.cp[l] = net_pad(channels[l]); net->ch.push_back(channels[l]); }
+  auto fail = [&](stmg_status st) { stmg_net_destroy(net); return st; };
+  size_t woff = 0, boff = 0;
+  for (int l = 0; l < layers; ++l) {
+    const int ci = d.ch[l], co = d.ch[l + 1], cip = d.cp[l], cop = d.cp[l + 1];
+    const size_t nw = (size_t)27 * cop * cip;
+    std::vector<float> w(nw, 0.f), b(cop, 0.f);
+    for (int o = 0; o < co; ++o) {
+      for (int c = 0; c < ci; ++c)
+        for (int t = 0; t < 27; ++t) w[((size_t)t * cop + o) * cip + c] = (float)weights[woff + ((size_t)o * ci + c) * 27 + t];
+      b[o] = (float)biases[boff + o];
+    }
+    woff += (size_t)co * ci * 27;
+    boff += co;
+    stmg_status st;
+    if ((st = net_alloc(net, (void**)&d.w32[l], nw * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.wt[l], nw * 2)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.wtT[l], nw * 2)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.gw[l], nw * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.mw[l], nw * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.vw[l], nw * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.bias[l], cop * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.gb[l], cop * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.mb[l], cop * 4)) != STMG_OK) return fail(st);
+    if ((st = net_alloc(net, (void**)&d.vb[l], cop * 4)) != STMG_OK) return fail(st);
+    if (cudaMemcpyAsync(d.w32[l], w.data(), nw * 4, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d.bias[l], b.data(), cop * 4, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      return fail(STMG_ERR_CUDA);
+  }
+  for (int l = 0; l <= layers; ++l) {
+    stmg_status st;
+    if (l < layers && (st = net_alloc(net, (void**)&d.act[l], (size_t)d.V * d.cp[l] * 2)) != STMG_OK) return fail(st);
+    if (l >= 1 && (st = net_alloc(net, (void**)&d.grad[l], (size_t)d.V * d.cp[l] * 2)) != STMG_OK) return fail(st);
+  }
+  stmg_status st;
+  if ((st = net_alloc(net, (void**)&d.out, (size_t)d.V * d.cp[layers] * 4)) != STMG_OK) return fail(st);
+  if ((st = net_alloc(net, (void**)&d.loss, 8)) != STMG_OK) return fail(st);
+  if (net_refresh_bf16(d, ctx->stream) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return fail(STMG_ERR_CUDA);
+  *out = net;
+  return STMG_OK;
+}
+
+stmg_status stmg_net_predict(stmg_net* net, const double* u_prev, const double* f, double* u_guess) {
+  if (!net || !u_prev || !f || !u_guess) return STMG_ERR_INVALID_ARG;
+  stmg_ctx* ctx = net->ctx;
+  StreamJoin join_(ctx);
+  CK(net_forward(net->d, u_prev, f, ctx->stream));
+  CK(net_guess(net->d, u_prev, u_guess, ctx->stream));
+  ctx->launches += 2 + net->d.L;
+  return STMG_OK;
+}
+
+static stmg_status net_fb(stmg_net* net, const double* u_prev, const double* f, const double* u_target, double* loss) {
+  stmg_ctx* ctx = net->ctx;
+  CK(net_forward(net->d, u_prev, f, ctx->stream));
+  CK(net_backward(net->d, u_prev, u_target, net->d.loss, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->hsm + 500, net->d.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (loss) *loss = ctx->hsm[500];
+  ctx->launches += 1 + 2 * net->d.L + 1 + 3 * net->d.L;
+  return STMG_OK;
+}
+
+stmg_status stmg_net_train_step(stmg_net* net, const double* u_prev, const double* f, const double* u_target, double lr,
+                                double* loss) {
+  if (!net || !u_prev || !f || !u_target) return STMG_ERR_INVALID_ARG;
+  stmg_ctx* ctx = net->ctx;
+  StreamJoin join_(ctx);
+  CKS(net_fb(net, u_prev, f, u_target, loss));
+  if (!std::isfinite(ctx->hsm[500])) { ctx->err = "network loss is not finite"; return STMG_ERR_NONFINITE; }
+  CK(net_adam(net->d, (float)lr, ctx->stream));
+  ctx->launches += 3 * net->d.L;
+  return STMG_OK;
+}
+
+stmg_status stmg_net_gradients(stmg_net* net, const double* u_prev, const double* f, const double* u_target,
+                               double* loss, double* grad_w, double* grad_b, double* out_host) {
+  if (!net || !u_prev || !f || !u_target) return STMG_ERR_INVALID_ARG;
+  stmg_ctx* ctx = net->ctx;
+  StreamJoin join_(ctx);
+  CKS(net_fb(net, u_prev, f, u_target, loss));
+  const NetDev& d = net->d;
+  size_t woff = 0, boff = 0;
+  for (int l = 0; l < d.L; ++l) {
+    const int ci = d.ch[l], co = d.ch[l + 1], cip = d.cp[l], cop = d.cp[l + 1];
+    std::vector<float> gw((size_t)27 * cop * cip), gb(cop);
+    CK(cudaMemcpy(gw.data(), d.gw[l], gw.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(gb.data(), d.gb[l], gb.size() * 4, cudaMemcpyDeviceToHost));
+    if (grad_w)
+      for (int o = 0; o < co; ++o)
+        for (int c = 0; c < ci; ++c)
+          for (int t = 0; t < 27; ++t) grad_w[woff + ((size_t)o * ci + c) * 27 + t] = gw[((size_t)t * cop + o) * cip + c];
+    if (grad_b)
+      for (int o = 0; o < co; ++o) grad_b[boff + o] = gb[o];
+    woff += (size_t)co * ci * 27;
+    boff += co;
+  }
+  if (out_host) {
+    const int cpl = d.cp[d.L];
+    std::vector<float> o((size_t)d.V * cpl);
+    CK(cudaMemcpy(o.data(), d.out, o.size() * 4, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < d.ch[d.L]; ++c)
+      for (int64_t v = 0; v < d.V; ++v) out_host[(size_t)c * d.V + v] = o[(size_t)v * cpl + c];
+  }
+  return STMG_OK;
+}
+
+stmg_status stmg_net_weights(stmg_net* net, double* w, double* b) {
+  if (!net) return STMG_ERR_INVALID_ARG;
+  stmg_ctx* ctx = net->ctx;
+  StreamJoin join_(ctx);
+  CK(cudaStreamSynchronize(ctx->stream));
+  const NetDev& d = net->d;
+  size_t woff = 0, boff = 0;
+  for (int l = 0; l < d.L; ++l) {
+    const int ci = d.ch[l], co = d.ch[l + 1], cip = d.cp[l], cop = d.cp[l + 1];
+    std::vector<float> hw((size_t)27 * cop * cip), hb(cop);
+    CK(cudaMemcpy(hw.data(), d.w32[l], hw.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hb.data(), d.bias[l], hb.size() * 4, cudaMemcpyDeviceToHost));
+    if (w)
+      for (int o = 0; o < co; ++o)
+        for (int c = 0; c < ci; ++c)
+          for (int t = 0; t < 27; ++t) w[woff + ((size_t)o * ci + c) * 27 + t] = hw[((size_t)t * cop + o) * cip + c];
+    if (b)
+      for (int o = 0; o < co; ++o) b[boff + o] = hb[o];
+    woff += (size_t)co * ci * 27;
+    boff += co;
+  }
+  return STMG_OK;
 }
 
 stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {

@@ -152,3 +152,18 @@ class MovingGaussians:
                 r2 = r2 + (x[..., d] - c[d]) ** 2
             f = f + self.amp[g] * np.exp(-r2 / (2.0 * self.width ** 2))
         return f
+
+
+def conv_net_init(channels=(4, 60, 60, 60, 2), seed=15, last_scale=0.1):
+    """He-normal weights (Co, Ci, 27) and zero biases for a chain of 3x3x3 convolutions."""
+    rng = np.random.default_rng(seed)
+    W, b = [], []
+    for l in range(len(channels) - 1):
+        ci, co = channels[l], channels[l + 1]
+        std = math.sqrt(2.0 / (27 * ci))
+        w = rng.standard_normal((co, ci, 27)) * std
+        if l == len(channels) - 2:
+            w *= last_scale
+        W.append(w)
+        b.append(np.zeros(co))
+    return W, b

@@ -1,0 +1,138 @@
+"""Learned initial guess: tensor-core convolution kernels against the FP64 oracle network,
+Adam against its definition, and what the trained network gains over the previous-slab guess.
+
+Tolerances: BF16 activations and weights (8-bit mantissa) with FP32 accumulation through four
+layers: outputs within 3e-2 of the largest output, gradients within 5e-2 relative (2-norm per
+layer) and cosine similarity above 0.998; Adam in FP32 against FP64: 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_cases import require_gpu
+from oracle import conv, fe1d
+
+pytestmark = pytest.mark.gpu
+
+CHANNELS = (4, 60, 60, 60, 2)
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _setup(stmg, torch, N=3):
+    ctx = stmg.Context(3, N, 2, 1, 0.05, omega=[0.2] * 8)
+    nn1 = 2 * N + 1
+    W, b = synth.conv_net_init(CHANNELS, seed=5, last_scale=1.0)
+    b = [np.random.default_rng(30 + l).standard_normal(len(x)) * 0.05 for l, x in enumerate(b)]
+    rng = np.random.default_rng(2)
+    u_prev = rng.standard_normal((2, ctx.n_nodes))
+    f = rng.standard_normal((2, ctx.n_nodes))
+    u_t = rng.standard_normal((2, ctx.n_nodes))
+    return ctx, nn1, W, b, u_prev, f, u_t
+
+
+def test_network_output_loss_and_gradients_match_oracle(env):
+    torch, stmg = env
+    ctx, nn1, W, b, u_prev, f, u_t = _setup(stmg, torch)
+    scales = (0.7, 1.3, 2.0)
+    net = stmg.Net(ctx, CHANNELS, W, b, scales)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+    loss, gW, gb, out = net.gradients(d(u_prev), d(f), d(u_t))
+    # oracle on the same BF16-rounded parameters
+    onet = conv.Net([_bf16(w) for w in W], [np.asarray(x, np.float64) for x in b])
+    shape = (nn1, nn1, nn1)
+    x0 = np.concatenate([u_prev * scales[0], f * scales[1]]).reshape((4,) + shape)
+    target = ((u_t - u_prev[-1][None, :]) * scales[2]).reshape((2,) + shape)
+    mask = np.zeros(shape, bool)
+    mask[1:-1, 1:-1, 1:-1] = True
+    ref_out, _ = onet.forward(x0)
+    ref_loss, rW, rb = onet.loss_and_grads(x0, target, mask)
+    assert np.abs(out.reshape(ref_out.shape) - ref_out).max() < 3e-2 * np.abs(ref_out).max()
+    assert abs(loss - ref_loss) < 3e-2 * ref_loss
+    for l in range(len(W)):
+        for g, r in ((gW[l], rW[l]), (gb[l], rb[l])):
+            rel = np.linalg.norm(g - r) / np.linalg.norm(r)
+            cos = float(np.dot(g.ravel(), r.ravel()) / (np.linalg.norm(g) * np.linalg.norm(r)))
+            assert rel < 5e-2 and cos > 0.998, (l, rel, cos)
+    net.close()
+    ctx.close()
+
+
+def test_adam_step_matches_definition(env):
+    torch, stmg = env
+    ctx, nn1, W, b, u_prev, f, u_t = _setup(stmg, torch)
+    net = stmg.Net(ctx, CHANNELS, W, b, (1.0, 1.0, 1.0))
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+    _, gW, gb, _ = net.gradients(d(u_prev), d(f), d(u_t))
+    W0, b0 = net.weights()
+    net.train_step(d(u_prev), d(f), d(u_t), 1e-3)
+    W1, b1 = net.weights()
+    opt = conv.Adam(W0 + b0, lr=1e-3)
+    ref = opt.step(W0 + b0, gW + gb)
+    for got, r, p0 in zip(W1 + b1, ref, W0 + b0):
+        assert np.abs(got - r).max() <= 1e-5 * max(np.abs(p0).max(), 1e-3) + 1e-7
+    net.close()
+    ctx.close()
+
+
+def test_trained_guess_beats_previous_slab_guess(env):
+    """Heat dG(1), Q2 on 8^3 cells, moving Gaussian sources: train on slabs 0-15, evaluate 16-23."""
+    torch, stmg = env
+    N, k, tau, n_train, n_eval = 8, 1, 1.0 / 64, 16, 8
+    ctx = stmg.Context(3, N, 2, k, tau, vcycle_precision=stmg.FP32, rtol=1e-8)
+    nt, nn = ctx.nt, ctx.n_nodes
+    X = ctx.node_coords()
+    src = synth.MovingGaussians()
+    tn = fe1d.gauss_radau_right(k + 1)[0]
+    F = [np.stack([src(X, tau * (s + th)) for th in tn]) for s in range(n_train + n_eval)]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+    sols = []
+    u_prev = torch.zeros(nn, dtype=torch.float64, device="cuda")
+    rhs = torch.empty(nt * nn, dtype=torch.float64, device="cuda")
+    for s in range(n_train + n_eval):
+        ctx.rhs(dev(F[s]), rhs, u0=u_prev)
+        u = torch.empty_like(rhs)
+        ctx.guess_previous(u_prev, u)
+        assert ctx.solve(rhs, u)["converged"]
+        sols.append(u.clone())
+        u_prev = u[(nt - 1) * nn:].clone()
+    prev = [torch.zeros(nt * nn, dtype=torch.float64, device="cuda")] + sols[:-1]
+    su = 1.0 / float(torch.stack(sols[:n_train]).pow(2).mean().sqrt())
+    sf = 1.0 / float(np.sqrt(np.mean([np.mean(x ** 2) for x in F[:n_train]])))
+    so = 1.0 / float(torch.stack([sols[s] - prev[s][(nt - 1) * nn:].repeat(nt) for s in range(n_train)]).pow(2).mean().sqrt())
+    W, b = synth.conv_net_init(CHANNELS, seed=15)
+    net = stmg.Net(ctx, CHANNELS, W, b, (su, sf, so))
+    losses = []
+    for epoch in range(60):
+        for s in range(1, n_train):
+            losses.append(net.train_step(prev[s], dev(F[s]), sols[s], 2e-3))
+    assert np.mean(losses[-n_train:]) < 0.2 * np.mean(losses[:n_train])
+    res_net, res_prev, it_net, it_prev = [], [], [], []
+    for s in range(n_train, n_train + n_eval):
+        ctx.rhs(dev(F[s]), rhs, u0=prev[s][(nt - 1) * nn:])
+        for use_net in (True, False):
+            u = torch.empty_like(rhs)
+            if use_net:
+                net.predict(prev[s], dev(F[s]), u)
+            else:
+                ctx.guess_previous(prev[s][(nt - 1) * nn:].contiguous(), u)
+            st = ctx.solve(rhs, u)
+            assert st["converged"]
+            (res_net if use_net else res_prev).append(st["initial_rel_residual"])
+            (it_net if use_net else it_prev).append(st["iterations"])
+            if use_net:
+                # the accepted solution is judged by the residual, not the guess
+                assert torch.linalg.norm(u - sols[s]) < 1e-6 * torch.linalg.norm(sols[s])
+    print("initial residual net/prev", np.mean(res_net), np.mean(res_prev), "its", np.mean(it_net), np.mean(it_prev))
+    assert np.mean(res_net) < 0.5 * np.mean(res_prev)
+    assert np.mean(it_net) <= np.mean(it_prev)
+    net.close()
+    ctx.close()
