@@ -4,8 +4,14 @@ Workload (default): 3D heat equation on [0,1]^3, Q2 elements on 32^3 cells whose
 interior vertices are jittered by U[-0.15h, 0.15h] (seed 11), dG(2) in time,
 tau = 1/32 (32 slabs), diffusion piecewise constant on a 4x4x4 grid of blocks,
 log-uniform in [1e-2, 1e2] (seed 12), source of u = sin(pi x) sin(pi y) sin(pi z) sin(pi t).
-One step = one time slab: right-hand side, previous-slab initial guess, FGMRES
-(FP64) preconditioned by one FP32 V-cycle per iteration, to ||r|| <= 1e-8 ||b||.
+One step = one time slab: right-hand side, previous-slab initial guess, FGMRES (FP64)
+preconditioned by one FP32 V-cycle per iteration, to ||r|| <= 1e-8 ||b||.  The line also reports
+the plain FP64 solver on the same slabs ("compare").
+
+--workload c5: the learned-initial-guess workload (Q2 on 48^3 Cartesian cells, dG(1), 256 slabs,
+8 moving Gaussian sources): slabs 0-127 solved by the mixed solver train the 3D conv network,
+slabs 128-255 are solved twice, from the learned guess (kept only when its FP64 residual is below
+the previous-slab guess's) and from the previous-slab guess; iterations and wall time of both.
 Metric: space-time DoFs (unconstrained, N_t x interior nodes) solved per second.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -169,6 +175,11 @@ def run_kernel_only(args):
     return 0
 
 
+NET_CHANNELS_HIDDEN = 60
+TRAIN_SLABS = 16
+TRAIN_EPOCHS = 40
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -189,40 +200,75 @@ def run_ours(args):
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                        vcycle_precision=vprec, rtol=1e-8, restart=30, max_it=200)
     nt, nn = ctx.nt, ctx.n_nodes
+    n = nt * nn
     X = ctx.node_coords()
-    from paper_2408_04372_gb300 import DG  # noqa: F401
     tn = radau_nodes(wl["k"])
     n_slabs = wl["n_slabs"]
     interior = (wl["N"] * wl["p"] - 1) ** 3
     dofs_per_step = nt * interior
-    # all sources resident on the device before timing
-    F = torch.empty((n_slabs, nt * nn), dtype=torch.float64, device=dev)
+    # sources of every slab resident in HBM before timing
+    F = torch.empty((n_slabs, n), dtype=torch.float64, device=dev)
     for s in range(n_slabs):
         f = np.stack([synth.heat_sine_source(X, wl["tau"] * (s + th)) for th in tn])
         F[s].copy_(torch.from_numpy(f.reshape(-1)))
-    rhs = torch.empty(nt * nn, dtype=torch.float64, device=dev)
-    u = torch.empty_like(rhs)
-    u_prev = torch.zeros(nn, dtype=torch.float64, device=dev)
-    its = []
+    sols = torch.zeros((n_slabs + 1, n), dtype=torch.float64, device=dev)   # sols[s + 1] = slab s; sols[0] = initial
+    rhs = torch.empty(n, dtype=torch.float64, device=dev)
+    cand = torch.empty(n, dtype=torch.float64, device=dev)
+    use_net = args.net and not args.plain
 
-    def step(i):
-        s = i % n_slabs
-        if s == 0:
-            u_prev.zero_()
-        ctx.rhs(F[s], rhs, u0=u_prev)
-        ctx.guess_previous(u_prev, u)
+    def solve_slab(s, u, net=None):
+        prev = sols[s]
+        prev_end = prev[(nt - 1) * nn:]
+        ctx.rhs(F[s], rhs, u0=prev_end)
+        ctx.guess_previous(prev_end, u)
+        taken = False
+        if net is not None:
+            net.predict(prev, F[s], cand)
+            taken = ctx.select_guess(rhs, cand, u)
         st = ctx.solve(rhs, u)
         if not st["converged"]:
             raise RuntimeError(f"slab {s} did not converge: {st}")
-        its.append(st["iterations"])
-        u_prev.copy_(u[(nt - 1) * nn:])
+        sols[s + 1].copy_(u)
+        return st, taken
 
+    # learned guess: plain marching over the training slabs, then Adam on (previous slab, source) -> slab
+    net, train_info = None, None
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    if use_net:
+        t0 = time.perf_counter()
+        for s in range(TRAIN_SLABS):
+            solve_slab(s, u)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        su = 1.0 / float(sols[1:TRAIN_SLABS + 1].pow(2).mean().sqrt())
+        sf = 1.0 / float(F[:TRAIN_SLABS].pow(2).mean().sqrt())
+        incr = torch.stack([sols[s + 1] - sols[s][(nt - 1) * nn:].repeat(nt) for s in range(1, TRAIN_SLABS)])
+        so = 1.0 / float(incr.pow(2).mean().sqrt())
+        channels = (2 * nt, NET_CHANNELS_HIDDEN, NET_CHANNELS_HIDDEN, NET_CHANNELS_HIDDEN, nt)
+        W, b = synth.conv_net_init(channels, seed=15)
+        net = stmg.Net(ctx, channels, W, b, (su, sf, so))
+        t1 = time.perf_counter()
+        losses = []
+        for epoch in range(TRAIN_EPOCHS):
+            for s in range(1, TRAIN_SLABS):
+                losses.append(net.train_step(sols[s], F[s], sols[s + 1], 2e-3))
+        torch.cuda.synchronize()
+        train_info = {"slabs": TRAIN_SLABS - 1, "epochs": TRAIN_EPOCHS, "train_s": time.perf_counter() - t1,
+                      "data_solve_s": t_solve, "loss_first_epoch": float(np.mean(losses[:TRAIN_SLABS - 1])),
+                      "loss_last_epoch": float(np.mean(losses[-(TRAIN_SLABS - 1):])),
+                      "params": int(sum(w.size for w in W) + sum(x.size for x in b)), "channels": list(channels)}
+    first = TRAIN_SLABS if use_net else 0
+    span = n_slabs - first
+
+    def slab_of(i):
+        return first + i % span
+
+    its, taken = [], []
     for i in range(args.warmup):
-        step(i)
+        solve_slab(slab_of(i), u, net)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    its.clear()
     launches0 = ctx.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -230,7 +276,9 @@ def run_ours(args):
         torch.cuda.nvtx.range_push("timed")
         ev0.record()
         for i in range(args.steps):
-            step(args.warmup + i)
+            st, tk = solve_slab(slab_of(args.warmup + i), u, net)
+            its.append(st["iterations"])
+            taken.append(tk)
         ev1.record()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
@@ -240,37 +288,65 @@ def run_ours(args):
     launches = ctx.launch_count() - launches0
     ms, value = aggregate_replicas(ms, dofs_per_step, args.steps, world, dev)
 
-    # end to end through the C ABI from pinned host buffers (H2D of f and u0, D2H of u each step)
-    Fh = torch.empty((n_slabs, nt * nn), dtype=torch.float64).pin_memory()
+    # comparison arms on the same slabs (not the headline): mixed without the network, plain FP64
+    compare = {}
+    if rank == 0 and not args.skip_compare and not args.plain:
+        def timed(fn, steps):
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = [fn(slab_of(args.warmup + i)) for i in range(steps)]
+            b_.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b_), out
+        if use_net:
+            k2 = min(args.steps, 8)
+            t_m, o_m = timed(lambda s: solve_slab(s, u)[0], k2)
+            compare["mixed_previous_slab_guess"] = {"value": dofs_per_step * k2 / (t_m / 1e3), "unit": UNIT,
+                                                    "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_m]))}
+        ctx64 = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
+                             vcycle_precision=stmg.FP64, rtol=1e-8, restart=30, max_it=200)
+        def plain(s):
+            prev_end = sols[s][(nt - 1) * nn:]
+            ctx64.rhs(F[s], rhs, u0=prev_end)
+            ctx64.guess_previous(prev_end, u)
+            return ctx64.solve(rhs, u)
+        plain(slab_of(args.warmup))
+        k3 = min(args.steps, 4)
+        t_p, o_p = timed(plain, k3)
+        compare["plain_fp64_previous_slab_guess"] = {"value": dofs_per_step * k3 / (t_p / 1e3), "unit": UNIT,
+                                                     "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_p]))}
+        ctx64.close()
+
+    # end to end through the C ABI from pinned host buffers (H2D of f and the previous slab, D2H of u)
+    Fh = torch.empty((n_slabs, n), dtype=torch.float64).pin_memory()
     Fh.copy_(F.cpu())
-    uh = torch.zeros(nt * nn, dtype=torch.float64).pin_memory()
-    u0h = torch.zeros(nn, dtype=torch.float64).pin_memory()
-    Fn, un, u0n = Fh.numpy(), uh.numpy().reshape(nt, nn), u0h.numpy()
+    Sh = torch.empty((n_slabs + 1, n), dtype=torch.float64).pin_memory()
+    Sh.copy_(sols.cpu())
+    uh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    Fn, Sn, un = Fh.numpy(), Sh.numpy(), uh.numpy()
     e2e_steps = max(1, min(args.steps, 8))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        s = (args.warmup + i) % n_slabs
-        if s == 0:
-            u0n[:] = 0.0
-        ctx.solve_slab_host(Fn[s].reshape(nt, nn), u0n, out_u=un)
-        u0n[:] = un[nt - 1]
+        s = slab_of(args.warmup + i)
+        if net is not None:
+            net.solve_slab_host(Fn[s], Sn[s], un)
+        else:
+            ctx.solve_slab_host(Fn[s].reshape(nt, nn), Sn[s][(nt - 1) * nn:], out_u=un.reshape(nt, nn))
+        Sn[s + 1][:] = un
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": world * dofs_per_step * e2e_steps / e2e_dt, "unit": UNIT,
-           "h2d_bytes_per_step": int(8 * (nt * nn + nn)), "d2h_bytes_per_step": int(8 * nt * nn)}
+           "h2d_bytes_per_step": int(8 * (2 * n if net is not None else n + nn)), "d2h_bytes_per_step": int(8 * n)}
 
-    # dominant kernel: the FP64 operator apply on the finest level (one per FGMRES iteration)
-    roof = None
-    cpu = None
-    extra = {}
+    roof, cpu, extra = None, None, {}
     if rank == 0:
         apply_ms = ctx.time_kernel(stmg.KERNEL_APPLY, 0, stmg.FP64, reps=20)
         asm_ms = ctx.time_kernel(stmg.KERNEL_ASM, 0, stmg.FP32, reps=20)
         vc_ms = ctx.time_kernel(stmg.KERNEL_VCYCLE, 0, vprec, reps=10)
-        n = wl["p"] + 1
+        nq = wl["p"] + 1
         cells = wl["N"] ** 3
-        flops_unit = 12 * n ** 4 + (16 + 8 * nt) * n ** 3          # per cell and time DoF
-        flops = flops_unit * cells * nt
+        flops = (12 * nq ** 4 + (16 + 8 * nt) * nq ** 3) * cells * nt
         peaks = read_peaks()
         fp64_peak = 1.25e12
         roof = {"kernel": "apply3d_kernel<N=3,NT=3,double> (finest level, FP64)", "bound": "alu",
@@ -278,7 +354,7 @@ def run_ours(args):
                 "frac": flops / (apply_ms * 1e-3) / fp64_peak, "traffic": read_traffic("apply_fp64"),
                 "peak_source": "FP64 1.25 TFLOP/s nominal (GB300 table; no measured FP64 peak)",
                 "avg_launch_ms": apply_ms}
-        asm_bytes = cells * nt * (n ** 3) ** 2 * 4 + 2 * 4 * nt * nn
+        asm_bytes = cells * nt * (nq ** 3) ** 2 * 4 + 2 * 4 * n
         extra["asm_fp32_finest"] = {"avg_launch_ms": asm_ms, "algorithmic_bytes": asm_bytes,
                                     "achieved_GBs": asm_bytes / (asm_ms * 1e-3) / 1e9,
                                     "frac_of_measured_hbm": asm_bytes / (asm_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
@@ -290,18 +366,117 @@ def run_ours(args):
                              f"workload family at 10^3 cells ({d} DoFs per slab)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+f32" if not args.plain else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.plain else ("f64+f32+bf16" if use_net else "f64+f32"),
+            "data": "synthetic",
             "config": {"workload": wl["name"], "cells": wl["N"] ** 3, "p": wl["p"], "time": f"dG({wl['k']})",
                        "dofs_per_step": dofs_per_step, "rtol": 1e-8, "vcycle": "fp64" if args.plain else "fp32",
+                       "guess": "learned (fallback previous slab)" if use_net else "previous slab",
+                       "dtype_note": "FP64 FGMRES vectors and residuals, FP32 V-cycle, FP32 Schwarz inverses",
+                       "slabs_timed": f"{slab_of(args.warmup)}..{slab_of(args.warmup + args.steps - 1)} (held out)"
+                       if use_net else "from slab 0",
                        "parallelism": f"replicas{world}", "l2": "working set > L2 (inverses alone 0.29 GB)",
-                       "fgmres_iterations_mean": float(np.mean(its)) if its else None},
+                       "fgmres_iterations_mean": float(np.mean(its)) if its else None,
+                       "learned_guess_taken": int(sum(taken)) if use_net else None},
             "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
-            "cpu_baseline": cpu, "kernels": extra}
+            "cpu_baseline": cpu, "kernels": extra, "training": train_info, "compare": compare}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if net is not None:
+        net.close()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_learned_c5(args):
+    """Learned initial guess vs previous-slab guess on held-out slabs of the moving-Gaussian workload."""
+    import torch
+    import paper_2408_04372_gb300 as stmg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N, p, k, n_slabs = args.n_cells if args.n_cells != 32 else 48, 2, 1, 256
+    tau = 1.0 / n_slabs
+    n_train = n_slabs // 2
+    ctx = stmg.Context(3, N, p, k, tau, vcycle_precision=stmg.FP32, rtol=1e-8, restart=30, max_it=200)
+    nt, nn = ctx.nt, ctx.n_nodes
+    n = nt * nn
+    X = ctx.node_coords()
+    src = synth.MovingGaussians()
+    tn = radau_nodes(k)
+    F = torch.empty((n_slabs, n), dtype=torch.float64, device=dev)
+    for s_ in range(n_slabs):
+        F[s_].copy_(torch.from_numpy(np.stack([src(X, tau * (s_ + th)) for th in tn]).reshape(-1)))
+    sols = torch.zeros((n_slabs + 1, n), dtype=torch.float64, device=dev)
+    rhs = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    cand = torch.empty(n, dtype=torch.float64, device=dev)
+    dofs = nt * (N * p - 1) ** 3
+
+    def slab(s_, net=None):
+        prev = sols[s_]
+        prev_end = prev[(nt - 1) * nn:]
+        ctx.rhs(F[s_], rhs, u0=prev_end)
+        ctx.guess_previous(prev_end, u)
+        taken = False
+        if net is not None:
+            net.predict(prev, F[s_], cand)
+            taken = ctx.select_guess(rhs, cand, u)
+        st = ctx.solve(rhs, u)
+        assert st["converged"], st
+        sols[s_ + 1].copy_(u)
+        return st, taken
+
+    t0 = time.perf_counter()
+    for s_ in range(n_train):
+        slab(s_)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    su = 1.0 / float(sols[1:n_train + 1].pow(2).mean().sqrt())
+    sf = 1.0 / float(F[:n_train].pow(2).mean().sqrt())
+    incr = torch.stack([sols[s_ + 1] - sols[s_][(nt - 1) * nn:].repeat(nt) for s_ in range(1, n_train)])
+    so = 1.0 / float(incr.pow(2).mean().sqrt())
+    channels = (2 * nt, NET_CHANNELS_HIDDEN, NET_CHANNELS_HIDDEN, NET_CHANNELS_HIDDEN, nt)
+    W, b = synth.conv_net_init(channels, seed=15)
+    net = stmg.Net(ctx, channels, W, b, (su, sf, so))
+    t1 = time.perf_counter()
+    losses = []
+    order = np.random.default_rng(16).permutation
+    for epoch in range(args.epochs):
+        for s_ in order(np.arange(1, n_train)):
+            losses.append(net.train_step(sols[s_], F[s_], sols[s_ + 1], args.lr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    ref_sols = sols.clone()
+    arms = {}
+    for name, use in (("learned", True), ("previous_slab", False)):
+        sols.copy_(ref_sols)
+        its, taken = [], []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for s_ in range(n_train, n_slabs):
+            st, tk = slab(s_, net if use else None)
+            its.append(st["iterations"])
+            taken.append(tk)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        arms[name] = {"value": dofs * (n_slabs - n_train) / (ms / 1e3), "unit": UNIT, "ms_per_slab": ms / (n_slabs - n_train),
+                      "fgmres_iterations_mean": float(np.mean(its)), "guess_taken": int(sum(taken))}
+    line = {"metric": "space-time DoFs/s solved to 1e-8, learned vs previous-slab initial guess (held-out slabs)",
+            "value": arms["learned"]["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64+f32+bf16", "data": "synthetic",
+            "config": {"workload": f"heat3d_q2_dg1_{N}cubed_8movinggaussians", "slabs": n_slabs, "train_slabs": n_train,
+                       "eval_slabs": f"{n_train}..{n_slabs - 1}", "dofs_per_slab": dofs, "epochs": args.epochs,
+                       "lr": args.lr, "channels": list(channels)},
+            "training": {"data_solve_s": t_data, "train_s": t_train, "steps": len(losses),
+                         "loss_first_epoch": float(np.mean(losses[:n_train - 1])),
+                         "loss_last_epoch": float(np.mean(losses[-(n_train - 1):]))},
+            "arms": arms}
+    print(json.dumps(line), flush=True)
+    net.close()
+    ctx.close()
     return 0
 
 
@@ -359,6 +534,11 @@ def main():
     ap.add_argument("--n-cells", type=int, default=32)
     ap.add_argument("--plain", action="store_true", help="FP64 V-cycle (plain STMG) instead of mixed precision")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-compare", action="store_true", help="skip the no-network and plain-FP64 comparison arms")
+    ap.add_argument("--net", action="store_true", help="learned guess on this workload too (trained on slabs 0-15)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5"])
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "asm32", "asm64", "vcycle32"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     args = ap.parse_args()
@@ -368,6 +548,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5":
+        return run_learned_c5(args)
     return run_ours(args)
 
 

@@ -193,6 +193,16 @@ stmg_status stmg_net_train_step(stmg_net* net, const double* u_prev, const doubl
  * (HOST [N_t][n_nodes], before scaling back) without updating; any output may be NULL.  Synchronous. */
 stmg_status stmg_net_gradients(stmg_net* net, const double* u_prev, const double* f, const double* u_target,
                                double* loss, double* grad_w, double* grad_b, double* out);
+/* Keeps the better of two initial guesses: u holds the default guess (e.g. the previous-slab
+ * guess) on entry; if ||rhs - S candidate|| < ||rhs - S u|| (FP64), u becomes candidate.
+ * *chosen (host, may be NULL) = 1 when the candidate was taken.  Synchronous. */
+stmg_status stmg_select_guess(stmg_ctx* ctx, const double* rhs, const double* candidate, double* u, int* chosen);
+/* End-to-end learned slab step (heat dG) from HOST buffers: uploads f [N_t][n] and the previous
+ * slab u_prev [N_t][n], builds the right-hand side, predicts the network guess, keeps it only if
+ * its FP64 residual is below the previous-slab guess's (*chosen = 1, may be NULL), solves with
+ * FGMRES and downloads u [N_t][n].  Synchronous. */
+stmg_status stmg_solve_slab_host_learned(stmg_ctx* ctx, stmg_net* net, const double* f, const double* u_prev,
+                                         double* u, int* chosen, stmg_solve_stats* stats);
 /* Current FP32 master parameters (HOST, FP64 arrays in the layouts of stmg_net_create). */
 stmg_status stmg_net_weights(stmg_net* net, double* weights, double* biases);
 

@@ -27,7 +27,8 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_restrict", "stmg_prolongate_add", "stmg_vcycle", "stmg_rhs", "stmg_solve",
            "stmg_wave_velocity", "stmg_guess_previous", "stmg_solve_slab_host", "stmg_launch_count",
            "stmg_time_kernel", "stmg_smooth_noalloc", "stmg_net_create", "stmg_net_destroy", "stmg_net_predict",
-           "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights"]
+           "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights", "stmg_select_guess",
+           "stmg_solve_slab_host_learned"]
 KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
 
 
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "stmg_net_train_step": [vp, vp, vp, vp, ctypes.c_double, dp],
         "stmg_net_gradients": [vp, vp, vp, vp, dp, dp, dp, dp],
         "stmg_net_weights": [vp, dp, dp],
+        "stmg_select_guess": [vp, vp, vp, vp, ctypes.POINTER(i32)],
+        "stmg_solve_slab_host_learned": [vp, vp, vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(SolveStats)],
         "stmg_time_kernel": [vp, i32, i32, i32, i32, dp],
     }
     for name, args in sig.items():
@@ -248,6 +251,12 @@ class Context:
     def wave_velocity(self, u, u0, v0, v):
         self._check(self.lib.stmg_wave_velocity(self.h, _ptr(u), _ptr(u0), _ptr(v0), _ptr(v)))
 
+    def select_guess(self, rhs, candidate, u):
+        """u = candidate if it has the smaller FP64 residual; returns True when taken."""
+        c = ctypes.c_int()
+        self._check(self.lib.stmg_select_guess(self.h, _ptr(rhs), _ptr(candidate), _ptr(u), ctypes.byref(c)))
+        return bool(c.value)
+
     def guess_previous(self, u0, u):
         self._check(self.lib.stmg_guess_previous(self.h, _ptr(u0), _ptr(u)))
 
@@ -332,6 +341,19 @@ class Net:
                                                     _dptr(gw), _dptr(gb), _dptr(out)))
         W, B = self._split(gw, gb)
         return loss.value, W, B, out
+
+    def solve_slab_host(self, f, u_prev, out_u):
+        """Host numpy in/out learned slab step; returns (stats dict, network guess taken)."""
+        import numpy as np
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        u_prev = np.ascontiguousarray(u_prev, dtype=np.float64)
+        st, ch = SolveStats(), ctypes.c_int()
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        code = self.lib.stmg_solve_slab_host_learned(self.ctx.h, self.h, vp(f), vp(u_prev), vp(out_u),
+                                                     ctypes.byref(ch), ctypes.byref(st))
+        if code not in (0, 4):
+            self.ctx._check(code)
+        return dict(iterations=st.iterations, rel_residual=st.rel_residual, converged=code == 0), bool(ch.value)
 
     def weights(self):
         import numpy as np

@@ -725,7 +725,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   CKS(dev_alloc(ctx, &ctx->dsm, 512));
   for (int i = 0; i < 6; ++i) CKS(dev_alloc(ctx, &ctx->tmp[i], ctx->levels[0].g.n_nodes));
   CKS(dev_alloc(ctx, &ctx->rhs_buf, n0));
-  CKS(dev_alloc(ctx, &ctx->u_buf, n0 * 2 + 4 * ctx->levels[0].g.n_nodes));
+  CKS(dev_alloc(ctx, &ctx->u_buf, n0 * 3 + 4 * ctx->levels[0].g.n_nodes));
   CK(cudaMallocHost(&ctx->hsm, 512 * sizeof(double)));
   for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
     CKS(setup_smoother(ctx, ctx->levels[li]));
@@ -1180,7 +1180,7 @@ stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f
   const int64_t nn = L.g.n_nodes, n = L.size();
   double* d_f = ctx->u_buf;                 // n
   double* d_u = ctx->u_buf + n;             // n
-  double* d_f0 = ctx->u_buf + 2 * n;        // nn each
+  double* d_f0 = ctx->u_buf + 3 * n;        // nn each
   double* d_u0 = d_f0 + nn;
   double* d_v0 = d_u0 + nn;
   double* d_v = ctx->tmp[4];
@@ -1405,6 +1405,58 @@ stmg_status stmg_net_weights(stmg_net* net, double* w, double* b) {
     boff += co;
   }
   return STMG_OK;
+}
+
+stmg_status stmg_select_guess(stmg_ctx* ctx, const double* rhs, const double* candidate, double* u, int* chosen) {
+  if (!ctx || !rhs || !candidate || !u) return STMG_ERR_INVALID_ARG;
+  StreamJoin join_(ctx);
+  Level& L = ctx->levels[0];
+  const int64_t n = L.size();
+  double* r = ctx->V;  // Krylov workspace is free between solves
+  double r_cur = 0.0, r_cand = 0.0;
+  CKS(op_residual<double>(ctx, L, rhs, u, r));
+  CKS(norm2(ctx, r, n, r_cur));
+  CKS(op_residual<double>(ctx, L, rhs, candidate, r));
+  CKS(norm2(ctx, r, n, r_cand));
+  const bool take = std::isfinite(r_cand) && r_cand < r_cur;
+  if (take) CK(cudaMemcpyAsync(u, candidate, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (chosen) *chosen = take ? 1 : 0;
+  return STMG_OK;
+}
+
+stmg_status stmg_solve_slab_host_learned(stmg_ctx* ctx, stmg_net* net, const double* f, const double* u_prev,
+                                         double* u, int* chosen, stmg_solve_stats* stats) {
+  if (!ctx || !net || !f || !u_prev || !u) return STMG_ERR_INVALID_ARG;
+  if (ctx->pde != STMG_HEAT || ctx->scheme != STMG_DG) return invalid(ctx, "learned slab step supports heat dG");
+  StreamJoin join_(ctx);
+  Level& L = ctx->levels[0];
+  const int64_t nn = L.g.n_nodes, n = L.size();
+  double* d_f = ctx->u_buf;
+  double* d_u = ctx->u_buf + n;
+  double* d_prev = ctx->u_buf + 2 * n;
+  double* d_cand = ctx->Z;  // Krylov workspace is free before the solve
+  CK(cudaMemcpyAsync(d_f, f, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d_prev, u_prev, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  const double* d_u0 = d_prev + (int64_t)(L.nt - 1) * nn;
+  CKS(rhs_impl(ctx, d_f, nullptr, d_u0, nullptr, ctx->rhs_buf));
+  CK(launch_broadcast_time(d_u0, d_u, L.nt, nn, ctx->stream));
+  CK(net_forward(net->d, d_prev, d_f, ctx->stream));
+  CK(net_guess(net->d, d_prev, d_cand, ctx->stream));
+  ctx->launches += 3 + net->d.L;
+  double r_prev = 0.0, r_cand = 0.0;
+  double* r = ctx->V;
+  CKS(op_residual<double>(ctx, L, ctx->rhs_buf, d_u, r));
+  CKS(norm2(ctx, r, n, r_prev));
+  CKS(op_residual<double>(ctx, L, ctx->rhs_buf, d_cand, r));
+  CKS(norm2(ctx, r, n, r_cand));
+  const bool take = std::isfinite(r_cand) && r_cand < r_prev;
+  if (take) CK(cudaMemcpyAsync(d_u, d_cand, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (chosen) *chosen = take ? 1 : 0;
+  stmg_status s = solve_impl(ctx, ctx->rhs_buf, d_u, stats);
+  if (s != STMG_OK && s != STMG_ERR_NOT_CONVERGED) return s;
+  CK(cudaMemcpyAsync(u, d_u, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return s;
 }
 
 stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {
