@@ -128,7 +128,7 @@ class Context:
 
     def __init__(self, dim, n_cells, p, k, tau, pde=HEAT, scheme=DG, vertices=None, coeff=None,
                  coeff_mode=COEFF_PER_CELL, nu_pre=1, nu_post=1, vcycle_precision=FP32, inverse_precision=0,
-                 omega=None, restart=30, rtol=1e-8, max_it=200, stream=None):
+                 omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO):
         import numpy as np
         import torch
         self.lib = load()
@@ -139,7 +139,8 @@ class Context:
         self._keep += [v, c, om]
         mesh = Mesh(dim, n_cells, _dptr(v))
         prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c))
-        opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, 0, _dptr(om), restart, rtol, max_it)
+        opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, smoother_kind, _dptr(om), restart, rtol,
+                       max_it)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -44,7 +44,16 @@ struct ModeTab {
   int nreal, ncplx;
   T Wr[kMaxNT][kMaxNT], Wi[kMaxNT][kMaxNT];
   T Vr[kMaxNT][kMaxNT], Vi[kMaxNT][kMaxNT];
+  T lre[kMaxNT], lim[kMaxNT];   // eigenvalues of the representative modes
   T omega;
+};
+
+// Fast diagonalisation tables for the three 1D cell types (first, interior, last cell):
+// S[t][a][i] = component a of the M1-orthonormal eigenvector i, lam[t][i] its eigenvalue.
+template <typename T>
+struct FDTab {
+  T S[3][kMaxN][kMaxN];
+  T lam[3][kMaxN];
 };
 
 template <typename T> __device__ inline T to_t(float v);

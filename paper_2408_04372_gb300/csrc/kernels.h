@@ -38,6 +38,11 @@ template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
                              const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s);
 
+// ---- fast diagonalisation local solves (fd.cu), 3D Cartesian cells ----
+template <typename T>
+cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho_cell, const GridDesc& g, const FDTab<T>& fd,
+                            const ModeTab<T>& mt, cudaStream_t s);
+
 // ---- transfers (transfer.cu) ----
 struct Transfer1D {
   int width_p;           // coarse window width (pc + 1)

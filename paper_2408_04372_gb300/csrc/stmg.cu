@@ -34,6 +34,11 @@ struct Level {
   ModeTab<float> mt32{};
   void* inv = nullptr;
   int inv_prec = 1;
+  bool fd = false;             // fast diagonalisation instead of stored inverses
+  FDTab<double> fd64{};
+  FDTab<float> fd32{};
+  double* rho_cell64 = nullptr;
+  float* rho_cell32 = nullptr;
   double omega = 1.0;
   // work vectors
   double *f64 = nullptr, *u64 = nullptr, *r64 = nullptr;
@@ -172,6 +177,12 @@ template <> float* uv<float>(Level& L) { return L.u32; }
 template <typename T> T* rv(Level& L);
 template <> double* rv<double>(Level& L) { return L.r64; }
 template <> float* rv<float>(Level& L) { return L.r32; }
+template <typename T> const FDTab<T>& fd_of(const Level& L);
+template <> const FDTab<double>& fd_of<double>(const Level& L) { return L.fd64; }
+template <> const FDTab<float>& fd_of<float>(const Level& L) { return L.fd32; }
+template <typename T> const T* rho_of(const Level& L);
+template <> const double* rho_of<double>(const Level& L) { return L.rho_cell64; }
+template <> const float* rho_of<float>(const Level& L) { return L.rho_cell32; }
 template <typename T> const T* cinv_of(const Level& L);
 template <> const double* cinv_of<double>(const Level& L) { return L.cinv64; }
 template <> const float* cinv_of<float>(const Level& L) { return L.cinv32; }
@@ -203,6 +214,10 @@ stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega) {
   ModeTab<T> mt = mt_of<T>(L);
   mt.omega = (T)omega;
   ctx->launches += 1;
+  if (L.fd) {
+    CK(launch_fd_apply<T>(L.n, L.nt, r, u, rho_of<T>(L), L.g, fd_of<T>(L), mt, ctx->stream));
+    return STMG_OK;
+  }
   CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, ctx->stream));
   return STMG_OK;
 }
@@ -457,6 +472,8 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     const int m = reps[r];
     lr.push_back(lam[m].real());
     li.push_back(lam[m].imag());
+    mt.lre[r] = lam[m].real();
+    mt.lim[r] = lam[m].imag();
     for (int t = 0; t < nt; ++t) {
       cplx w = 0.0;  // W = V^-1 TA^-1
       for (int l = 0; l < nt; ++l) w += Vinv[m * nt + l] * TAi[l * nt + t];
@@ -473,8 +490,40 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
       mf.Wr[a][b] = (float)mt.Wr[a][b]; mf.Wi[a][b] = (float)mt.Wi[a][b];
       mf.Vr[a][b] = (float)mt.Vr[a][b]; mf.Vi[a][b] = (float)mt.Vi[a][b];
     }
+  for (int a = 0; a < kMaxNT; ++a) { mf.lre[a] = (float)mt.lre[a]; mf.lim[a] = (float)mt.lim[a]; }
   mf.omega = 1.0f;
   L.mt32 = mf;
+  if (L.fd) {
+    std::vector<double> S, lamfd;
+    fd_tables_1d(L.p, L.N, S, lamfd);
+    FDTab<double> f64{};
+    FDTab<float> f32{};
+    for (int t = 0; t < 3; ++t)
+      for (int a = 0; a < L.n; ++a) {
+        f64.lam[t][a] = lamfd[t * L.n + a];
+        f32.lam[t][a] = (float)lamfd[t * L.n + a];
+        for (int i = 0; i < L.n; ++i) {
+          f64.S[t][a][i] = S[(t * L.n + a) * L.n + i];
+          f32.S[t][a][i] = (float)S[(t * L.n + a) * L.n + i];
+        }
+      }
+    L.fd64 = f64;
+    L.fd32 = f32;
+    const int nqd = L.n * L.n * L.n;
+    std::vector<double> rc(L.g.n_cells);
+    std::vector<float> rcf(L.g.n_cells);
+    for (int64_t c = 0; c < L.g.n_cells; ++c) {
+      double sum = 0.0;
+      for (int q = 0; q < nqd; ++q) sum += L.rho_qp[c * nqd + q];
+      rc[c] = sum / nqd;
+      rcf[c] = (float)rc[c];
+    }
+    CKS(dev_alloc(ctx, &L.rho_cell64, L.g.n_cells));
+    CKS(dev_alloc(ctx, &L.rho_cell32, L.g.n_cells));
+    CK(cudaMemcpy(L.rho_cell64, rc.data(), sizeof(double) * rc.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.rho_cell32, rcf.data(), sizeof(float) * rcf.size(), cudaMemcpyHostToDevice));
+    return STMG_OK;
+  }
   const int NB = L.dim == 3 ? L.n * L.n * L.n : L.n * L.n;
   if (L.dim == 3 && L.n > 4) {
     ctx->err = "dense additive Schwarz setup supports p <= 3 in 3D";
@@ -727,6 +776,39 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   CKS(dev_alloc(ctx, &ctx->rhs_buf, n0));
   CKS(dev_alloc(ctx, &ctx->u_buf, n0 * 3 + 4 * ctx->levels[0].g.n_nodes));
   CK(cudaMallocHost(&ctx->hsm, 512 * sizeof(double)));
+  // local solver per level: fast diagonalisation on Cartesian 3D grids where it is exact (rho constant
+  // on every cell patch) or where stored inverses are not supported (p = 4), else stored inverses
+  bool cartesian = true;
+  if (mesh->vertices) {
+    for (int64_t v = 0; v < nverts && cartesian; ++v) {
+      int64_t r = v;
+      for (int d = 0; d < dim; ++d) {
+        if (std::fabs(verts[v * dim + d] - (double)(r % nv1) / N) > 1e-14) cartesian = false;
+        r /= nv1;
+      }
+    }
+  }
+  if (o.smoother_kind == STMG_SMOOTHER_FD && (dim != 3 || !cartesian))
+    return invalid(ctx, "fast diagonalisation needs a 3D Cartesian grid");
+  for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
+    Level& L = ctx->levels[li];
+    bool patch_const = true;
+    const int nqd = dim == 3 ? L.n * L.n * L.n : L.n * L.n;
+    for (int64_t c = 0; c < L.g.n_cells && patch_const; ++c) {
+      const double r0 = L.rho_qp[c * nqd];
+      for (int q = 0; q < nqd && patch_const; ++q) patch_const = L.rho_qp[c * nqd + q] == r0;
+      if (dim != 3) continue;
+      const int64_t cx = c % L.N, cy = (c / L.N) % L.N, cz = c / ((int64_t)L.N * L.N);
+      for (int o3 = 0; o3 < 27 && patch_const; ++o3) {
+        const int64_t nx = cx + o3 % 3 - 1, ny = cy + (o3 / 3) % 3 - 1, nz = cz + o3 / 9 - 1;
+        if (nx < 0 || ny < 0 || nz < 0 || nx >= L.N || ny >= L.N || nz >= L.N) continue;
+        patch_const = L.rho_qp[(nx + L.N * (ny + L.N * nz)) * nqd] == r0;
+      }
+    }
+    if (o.smoother_kind == STMG_SMOOTHER_FD) L.fd = true;
+    else if (o.smoother_kind == STMG_SMOOTHER_DENSE) L.fd = false;
+    else L.fd = dim == 3 && cartesian && (patch_const || L.n > 4);
+  }
   for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
     CKS(setup_smoother(ctx, ctx->levels[li]));
     CKS(setup_transfer(ctx, ctx->levels[li], ctx->levels[li + 1]));

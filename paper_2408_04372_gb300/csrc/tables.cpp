@@ -451,4 +451,107 @@ std::vector<double> time_prolongation(int scheme, int kf, int kc) {
   return P;
 }
 
+void jacobi_eigen(int n, std::vector<double> a, std::vector<double>& w, std::vector<double>& V) {
+  V.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) (i == j ? diag : off) += a[i * n + j] * a[i * n + j];
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // a <- a J (columns p, q)
+          const double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = c * akp - s * akq;
+          a[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // a <- J^T a (rows p, q)
+          const double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = c * apk - s * aqk;
+          a[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = a[i * n + i];
+}
+
+void fd_tables_1d(int p, int N, std::vector<double>& S, std::vector<double>& lam) {
+  const int n = p + 1;
+  const double h = 1.0 / N;
+  std::vector<double> xn = space_nodes(p), xq, wq;
+  gauss_legendre(n, xq, wq);
+  std::vector<double> Me(n * n, 0.0), Ae(n * n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int q = 0; q < n; ++q) {
+        Me[a * n + b] += h * wq[q] * lagrange(xn, a, xq[q]) * lagrange(xn, b, xq[q]);
+        Ae[a * n + b] += wq[q] * lagrange_deriv(xn, a, xq[q]) * lagrange_deriv(xn, b, xq[q]) / h;
+      }
+  S.assign(3 * n * n, 0.0);
+  lam.assign(3 * n, 1.0);
+  for (int t = 0; t < 3; ++t) {
+    std::vector<double> M = Me, A = Ae;
+    const bool has_left = t != 0 || N == 1 ? (t != 0) : false;
+    const bool has_right = t != 2;
+    if (has_left) { M[0] += Me[p * n + p]; A[0] += Ae[p * n + p]; }      // node 0 shared with the left cell
+    if (has_right) { M[p * n + p] += Me[0]; A[p * n + p] += Ae[0]; }     // node p shared with the right cell
+    std::vector<int> free_nodes;
+    for (int a = 0; a < n; ++a)
+      if (!((t == 0 && a == 0) || (t == 2 && a == p))) free_nodes.push_back(a);
+    const int m = (int)free_nodes.size();
+    std::vector<double> Mf(m * m), Af(m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        Mf[i * m + j] = M[free_nodes[i] * n + free_nodes[j]];
+        Af[i * m + j] = A[free_nodes[i] * n + free_nodes[j]];
+      }
+    // Cholesky M = L L^T, C = L^-1 A L^-T, C Q = Q w, S = L^-T Q
+    std::vector<double> L(m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double sum = Mf[i * m + j];
+        for (int k = 0; k < j; ++k) sum -= L[i * m + k] * L[j * m + k];
+        L[i * m + j] = (i == j) ? std::sqrt(sum) : sum / L[j * m + j];
+      }
+    std::vector<double> Li(m * m, 0.0);  // L^-1 by forward substitution
+    for (int c = 0; c < m; ++c)
+      for (int i = 0; i < m; ++i) {
+        double sum = (i == c) ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) sum -= L[i * m + k] * Li[k * m + c];
+        Li[i * m + c] = sum / L[i * m + i];
+      }
+    std::vector<double> C(m * m, 0.0), T(m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        for (int k = 0; k < m; ++k) T[i * m + j] += Li[i * m + k] * Af[k * m + j];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        for (int k = 0; k < m; ++k) C[i * m + j] += T[i * m + k] * Li[j * m + k];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < i; ++j) { const double v = 0.5 * (C[i * m + j] + C[j * m + i]); C[i * m + j] = C[j * m + i] = v; }
+    std::vector<double> w, Q;
+    jacobi_eigen(m, C, w, Q);
+    for (int i = 0; i < m; ++i) {
+      lam[t * n + i] = w[i];
+      for (int a = 0; a < m; ++a) {
+        double sv = 0.0;  // (L^-T Q)[a][i] = sum_k Li[k][a] Q[k][i]
+        for (int k = 0; k < m; ++k) sv += Li[k * m + a] * Q[k * m + i];
+        S[(t * n + free_nodes[a]) * n + i] = sv;
+      }
+    }
+  }
+}
+
 }  // namespace stmg

@@ -55,4 +55,13 @@ void prolongation_1d(int pf, int Nf, int pc, int Nc, std::vector<int>& start, st
 // Time prolongation P_tau (nt_f x nt_c, row-major).
 std::vector<double> time_prolongation(int scheme, int kf, int kc);
 
+// Fast diagonalisation tables of one direction of a uniform Cartesian grid (N cells of size h):
+// for cell type t (0: first cell, left node constrained; 1: interior; 2: last cell, right node
+// constrained) the global 1D mass M and stiffness A restricted to the cell's p+1 nodes (neighbour
+// halves included), and the generalized eigenpairs A s = lambda M s on the unconstrained nodes with
+// s^T M s = 1.  S[t][a][i] = component a of eigenvector i (0 on constrained nodes and unused i).
+void fd_tables_1d(int p, int N, std::vector<double>& S, std::vector<double>& lam);
+// Symmetric eigen-decomposition (cyclic Jacobi): a (n x n, symmetric) -> eigenvalues w, vectors V (columns).
+void jacobi_eigen(int n, std::vector<double> a, std::vector<double>& w, std::vector<double>& V);
+
 }  // namespace stmg

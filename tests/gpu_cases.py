@@ -45,6 +45,10 @@ CASES = [
     Case("heat3d_q1_dg0", 3, 2, 1, 0, "heat", "dg", 0.1, False, "one"),
     Case("heat3d_q2_cgp1_jit", 3, 4, 2, 1, "heat", "cgp", 1 / 16, True, "blocks"),
     Case("wave2d_q2_dg1", 2, 4, 2, 1, "wave", "dg", 1 / 32, True, "layers"),
+    # 3D Cartesian grids with a constant coefficient: the library picks fast diagonalisation (exact here)
+    Case("heat3d_q3_dg1_cart_fd", 3, 4, 3, 1, "heat", "dg", 1 / 16, False, "one"),
+    Case("wave3d_q2_cgp2_cart_fd", 3, 4, 2, 2, "wave", "cgp", 1 / 32, False, "one"),
+    Case("heat3d_q4_dg3_cart_fd", 3, 2, 4, 3, "heat", "dg", 1 / 8, False, "one"),
 ]
 
 _HIER = {}
