@@ -480,6 +480,70 @@ def run_learned_c5(args):
     return 0
 
 
+def run_c4(args):
+    """Config 4: heat, Q4 on 64^3 Cartesian cells, dG(3), smooth coefficient at the Gauss points,
+    fast-diagonalisation local solves; mixed (FP32 V-cycle) and plain FP64 solvers, 8 slabs."""
+    import torch
+    import paper_2408_04372_gb300 as stmg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N = args.n_cells if args.n_cells != 32 else 64
+    p, k, n_slabs = 4, 3, 8
+    tau = 1.0 / n_slabs
+    V = synth.cartesian_vertices(N, 3)
+    a, phi = synth.smooth_coefficient_params(3)
+    # the coefficient is evaluated at the Gauss points of the Cartesian cells
+    xq = np.polynomial.legendre.leggauss(p + 1)[0] * 0.5 + 0.5
+    ql = np.indices((p + 1,) * 3).reshape(3, -1)[::-1].T
+    cells = np.indices((N,) * 3).reshape(3, -1)[::-1].T
+    pts = (cells[:, None, :] + xq[ql][None, :, :]) / N
+    rho_qp = synth.smooth_coefficient_at(pts, a, phi)
+    out = {}
+    tn = radau_nodes(k)
+    for name, prec in (("mixed_fp32_vcycle", stmg.FP32), ("plain_fp64", stmg.FP64)):
+        t0 = time.perf_counter()
+        ctx = stmg.Context(3, N, p, k, tau, vertices=None, coeff=rho_qp.reshape(-1), coeff_mode=stmg.COEFF_PER_QPOINT,
+                           vcycle_precision=prec, rtol=1e-8, restart=30, max_it=200)
+        t_setup = time.perf_counter() - t0
+        nt, nn = ctx.nt, ctx.n_nodes
+        X = ctx.node_coords()
+        rhs = torch.empty(nt * nn, dtype=torch.float64, device=dev)
+        u = torch.empty_like(rhs)
+        u_prev = torch.zeros(nn, dtype=torch.float64, device=dev)
+        steps = n_slabs if prec == stmg.FP32 else min(2, n_slabs)
+        its = []
+        ms = 0.0
+        for s_ in range(steps):
+            f = torch.from_numpy(np.stack([synth.heat_sine_source(X, tau * (s_ + th)) for th in tn]).reshape(-1)).to(dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.rhs(f, rhs, u0=u_prev)
+            ctx.guess_previous(u_prev, u)
+            st = ctx.solve(rhs, u)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            assert st["converged"], st
+            its.append(st["iterations"])
+            u_prev.copy_(u[(nt - 1) * nn:])
+        dofs = nt * (N * p - 1) ** 3
+        out[name] = {"value": dofs * steps / (ms / 1e3), "unit": UNIT, "ms_per_slab": ms / steps,
+                     "fgmres_iterations_mean": float(np.mean(its)), "slabs": steps, "setup_s": t_setup,
+                     "apply_fp64_ms": ctx.time_kernel(stmg.KERNEL_APPLY, 0, stmg.FP64, reps=5),
+                     "apply_fp32_ms": ctx.time_kernel(stmg.KERNEL_APPLY, 0, stmg.FP32, reps=5),
+                     "fd_smoother_fp32_ms": ctx.time_kernel(stmg.KERNEL_ASM, 0, stmg.FP32, reps=5),
+                     "vcycle_ms": ctx.time_kernel(stmg.KERNEL_VCYCLE, 0, prec, reps=3)}
+        ctx.close()
+    line = {"metric": "space-time DoFs/s solved to 1e-8 rel. residual", "value": out["mixed_fp32_vcycle"]["value"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"heat3d_q4_dg3_{N}cubed_cartesian_smoothrho", "dofs_per_slab": nt * (N * p - 1) ** 3,
+                       "smoother": "fast diagonalisation (cell-mean coefficient)"},
+            "arms": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def aggregate_replicas(ms_local, dofs_per_step, steps, world, device):
     """Replicas only: slowest rank's time, every rank's DoFs.  Returns (max ms, whole-job DoF/s)."""
     import torch
@@ -536,7 +600,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-compare", action="store_true", help="skip the no-network and plain-FP64 comparison arms")
     ap.add_argument("--net", action="store_true", help="learned guess on this workload too (trained on slabs 0-15)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"])
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "asm32", "asm64", "vcycle32"],
@@ -550,6 +614,8 @@ def main():
         return run_reference(args)
     if args.workload == "c5":
         return run_learned_c5(args)
+    if args.workload == "c4":
+        return run_c4(args)
     return run_ours(args)
 
 

@@ -44,13 +44,17 @@ cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho_cell, 
                             const ModeTab<T>& mt, cudaStream_t s);
 
 // ---- transfers (transfer.cu) ----
+// 1D lists of the separable transfers, Dirichlet masks folded in: prolongation rows of fine
+// boundary nodes and columns of coarse boundary nodes are dropped, likewise for the restriction.
 struct Transfer1D {
-  int width_p;           // coarse window width (pc + 1)
+  int width_p;           // max coarse entries per fine node
   int width_r;           // max fine entries per coarse node
-  const int* p_start;    // [nn1_f]
+  const int* p_idx;      // [nn1_f][width_p]  (coarse index, -1 padding)
   const double* p_w;     // [nn1_f][width_p]
   const int* r_idx;      // [nn1_c][width_r]  (fine index, -1 padding)
   const double* r_w;     // [nn1_c][width_r]
+  void* tmp1;            // scratch: nt * nn1_f^2 * nn1_c doubles each
+  void* tmp2;
 };
 template <typename T>
 cudaError_t launch_prolong_space_add(T* uf, const T* ec, const GridDesc& gf, const GridDesc& gc, int nt,

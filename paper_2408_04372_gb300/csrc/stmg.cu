@@ -237,7 +237,10 @@ stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc) {
   Level& F = ctx->levels[l];
   Level& C = ctx->levels[l + 1];
   ctx->launches += 1;
-  if (F.tkind == 1) CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, ctx->stream));
+  if (F.tkind == 1) {
+    CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, ctx->stream));
+    ctx->launches += F.dim - 1;
+  }
   else CK(launch_restrict_time<T>(rc, rf, F.g, F.tt, ctx->stream));
   return STMG_OK;
 }
@@ -247,7 +250,10 @@ stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf) {
   Level& F = ctx->levels[l];
   Level& C = ctx->levels[l + 1];
   ctx->launches += 1;
-  if (F.tkind == 1) CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, ctx->stream));
+  if (F.tkind == 1) {
+    CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, ctx->stream));
+    ctx->launches += F.dim - 1;
+  }
   else CK(launch_prolong_time_add<T>(uf, ec, F.g, F.tt, ctx->stream));
   return STMG_OK;
 }
@@ -563,34 +569,44 @@ stmg_status setup_transfer(stmg_ctx* ctx, Level& F, const Level& C) {
   prolongation_1d(F.p, F.N, C.p, C.N, start, w);
   const int W = C.p + 1;
   const int nf = F.g.nn1, nc = C.g.nn1;
-  std::vector<std::vector<std::pair<int, double>>> lists(nc);
-  for (int gf = 0; gf < nf; ++gf)
+  // 1D lists with the Dirichlet masks folded in (fine and coarse end nodes dropped)
+  std::vector<std::vector<std::pair<int, double>>> plist(nf), rlist(nc);
+  for (int gf = 1; gf < nf - 1; ++gf)
     for (int b = 0; b < W; ++b) {
+      const int gc = start[gf] + b;
       const double v = w[(size_t)gf * W + b];
-      if (v != 0.0) lists[start[gf] + b].push_back({gf, v});
+      if (v == 0.0 || gc == 0 || gc == nc - 1) continue;
+      plist[gf].push_back({gc, v});
+      rlist[gc].push_back({gf, v});
     }
-  int R = 1;
-  for (auto& l : lists) R = std::max<int>(R, (int)l.size());
-  std::vector<int> ridx((size_t)nc * R, -1);
-  std::vector<double> rw((size_t)nc * R, 0.0);
-  for (int G = 0; G < nc; ++G)
-    for (size_t c = 0; c < lists[G].size(); ++c) { ridx[(size_t)G * R + c] = lists[G][c].first; rw[(size_t)G * R + c] = lists[G][c].second; }
-  int *d_start = nullptr, *d_ridx = nullptr;
-  double *d_w = nullptr, *d_rw = nullptr;
-  CKS(dev_alloc(ctx, &d_start, nf));
-  CKS(dev_alloc(ctx, &d_w, (size_t)nf * W));
-  CKS(dev_alloc(ctx, &d_ridx, (size_t)nc * R));
-  CKS(dev_alloc(ctx, &d_rw, (size_t)nc * R));
-  CK(cudaMemcpy(d_start, start.data(), sizeof(int) * nf, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_w, w.data(), sizeof(double) * nf * W, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_ridx, ridx.data(), sizeof(int) * nc * R, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_rw, rw.data(), sizeof(double) * nc * R, cudaMemcpyHostToDevice));
-  F.tr.width_p = W;
-  F.tr.width_r = R;
-  F.tr.p_start = d_start;
-  F.tr.p_w = d_w;
-  F.tr.r_idx = d_ridx;
-  F.tr.r_w = d_rw;
+  auto pack = [&](const std::vector<std::vector<std::pair<int, double>>>& lists, int& R, int** d_idx,
+                  double** d_w) -> stmg_status {
+    R = 1;
+    for (auto& l : lists) R = std::max<int>(R, (int)l.size());
+    std::vector<int> idx(lists.size() * R, -1);
+    std::vector<double> wt(lists.size() * R, 0.0);
+    for (size_t i = 0; i < lists.size(); ++i)
+      for (size_t c = 0; c < lists[i].size(); ++c) { idx[i * R + c] = lists[i][c].first; wt[i * R + c] = lists[i][c].second; }
+    CKS(dev_alloc(ctx, d_idx, idx.size()));
+    CKS(dev_alloc(ctx, d_w, wt.size()));
+    CK(cudaMemcpy(*d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(*d_w, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
+    return STMG_OK;
+  };
+  int *pi = nullptr, *ri = nullptr;
+  double *pw = nullptr, *rw = nullptr;
+  CKS(pack(plist, F.tr.width_p, &pi, &pw));
+  CKS(pack(rlist, F.tr.width_r, &ri, &rw));
+  F.tr.p_idx = pi;
+  F.tr.p_w = pw;
+  F.tr.r_idx = ri;
+  F.tr.r_w = rw;
+  const size_t tmp = (size_t)F.nt * nf * (size_t)(F.dim == 3 ? nf : 1) * nc;
+  double *t1 = nullptr, *t2 = nullptr;
+  CKS(dev_alloc(ctx, &t1, tmp));
+  CKS(dev_alloc(ctx, &t2, tmp));
+  F.tr.tmp1 = t1;
+  F.tr.tmp2 = t2;
   return STMG_OK;
 }
 
