@@ -80,6 +80,8 @@ struct stmg_ctx {
   double* u_buf = nullptr;
   cudaGraphExec_t graph32 = nullptr, graph64 = nullptr;
   int64_t graph32_kernels = 0, graph64_kernels = 0;
+  std::vector<cudaGraphExec_t> iter_graphs;      // one FGMRES iteration per Krylov index j
+  std::vector<int64_t> iter_graph_kernels;
   bool warmed32 = false, warmed64 = false;
   int64_t launches = 0;  // kernels issued by this context (graph replays count their kernel nodes)
 };
@@ -370,10 +372,8 @@ __global__ void finalize_arnoldi_kernel(const double* h1, const double* h2, int 
   }
 }
 
-// One Arnoldi/FGMRES orthogonalisation step (classical Gram-Schmidt, twice):
-// w <- w - V h, h = [V^T w]_1 + [V^T w]_2 ; hn = ||w|| ; w <- w / hn.  Host gets h (nv) and hn.
-stmg_status orthogonalise(stmg_ctx* ctx, const double* const* Vp, int nv, double* w, int64_t n, std::vector<double>& h,
-                          double& hn) {
+// enqueue part: no host synchronisation (capturable)
+stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* const* Vp, int nv, double* w, int64_t n) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
   double* d_n = ctx->dsm + 256;
@@ -388,10 +388,22 @@ stmg_status orthogonalise(stmg_ctx* ctx, const double* const* Vp, int nv, double
   CK(cudaGetLastError());
   CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream));
   CK(cudaMemcpyAsync(ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
+  return STMG_OK;
+}
+
+stmg_status orthogonalise_read(stmg_ctx* ctx, int nv, std::vector<double>& h, double& hn) {
   CK(cudaStreamSynchronize(ctx->stream));
   h.assign(ctx->hsm, ctx->hsm + nv);
   hn = ctx->hsm[nv];
   return STMG_OK;
+}
+
+// One Arnoldi/FGMRES orthogonalisation step (classical Gram-Schmidt, twice):
+// w <- w - V h, h = [V^T w]_1 + [V^T w]_2 ; hn = ||w|| ; w <- w / hn.  Host gets h (nv) and hn.
+stmg_status orthogonalise(stmg_ctx* ctx, const double* const* Vp, int nv, double* w, int64_t n, std::vector<double>& h,
+                          double& hn) {
+  CKS(orthogonalise_enqueue(ctx, Vp, nv, w, n));
+  return orthogonalise_read(ctx, nv, h, hn);
 }
 
 stmg_status estimate_omega(stmg_ctx* ctx, int l) {
@@ -864,6 +876,67 @@ stmg_status precondition(stmg_ctx* ctx, const double* v, double* z) {
   return STMG_OK;
 }
 
+// z_j = B v_j, v_{j+1} = S z_j, CGS2 against v_0..v_j, Hessenberg column to the host buffer
+stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
+  Level& L = ctx->levels[0];
+  const int64_t n = L.size();
+  double* v = ctx->V + (size_t)j * n;
+  double* z = ctx->Z + (size_t)j * n;
+  double* w = ctx->V + (size_t)(j + 1) * n;
+  if (ctx->opt.vcycle_precision == STMG_FP32) {
+    CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
+    if (in_capture) CKS(vcycle_level<float>(ctx, 0));
+    else CKS(run_vcycle<float>(ctx));
+    CK(launch_convert<float, double>(L.u32, z, n, ctx->stream));
+    ctx->launches += 2;
+  } else {
+    CK(cudaMemcpyAsync(L.f64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (in_capture) CKS(vcycle_level<double>(ctx, 0));
+    else CKS(run_vcycle<double>(ctx));
+    CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CKS(op_apply<double>(ctx, L, z, w));
+  std::vector<const double*> Vc(j + 1);
+  for (int i = 0; i <= j; ++i) Vc[i] = ctx->V + (size_t)i * n;
+  return orthogonalise_enqueue(ctx, Vc.data(), j + 1, w, n);
+}
+
+stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
+  const bool warmed = ctx->opt.vcycle_precision == STMG_FP32 ? ctx->warmed32 : ctx->warmed64;
+  if (!warmed) return fgmres_iteration_enqueue(ctx, j, false);  // first V-cycle runs eagerly
+  if ((int)ctx->iter_graphs.size() < ctx->m) {
+    ctx->iter_graphs.assign(ctx->m, nullptr);
+    ctx->iter_graph_kernels.assign(ctx->m, 0);
+  }
+  if (!ctx->iter_graphs[j]) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t saved = ctx->launches;
+    stmg_status st = fgmres_iteration_enqueue(ctx, j, true);
+    ctx->launches = saved;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != STMG_OK) return st;
+    if (e != cudaSuccess) { ctx->err = std::string("capture: ") + cudaGetErrorString(e); return STMG_ERR_CUDA; }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int64_t nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      if (ty == cudaGraphNodeTypeKernel) ++nk;
+    }
+    e = cudaGraphInstantiate(&ctx->iter_graphs[j], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { ctx->err = std::string("instantiate: ") + cudaGetErrorString(e); ctx->iter_graphs[j] = nullptr; return STMG_ERR_CUDA; }
+    ctx->iter_graph_kernels[j] = nk;
+  }
+  CK(cudaGraphLaunch(ctx->iter_graphs[j], ctx->stream));
+  ctx->launches += ctx->iter_graph_kernels[j];
+  return STMG_OK;
+}
+
 stmg_status norm2(stmg_ctx* ctx, const double* x, int64_t n, double& out) {
   CKS(dots(ctx, nullptr, 0, x, n, 1, ctx->dsm + 448));
   ctx->launches += 2;
@@ -911,12 +984,10 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     int jend = 0;
     bool breakdown = false;
     for (int j = 0; j < m; ++j) {
-      CKS(precondition(ctx, V[j], Z[j]));
-      CKS(op_apply<double>(ctx, L, Z[j], V[j + 1]));
+      CKS(fgmres_iteration(ctx, j));
       std::vector<double> h;
       double hn = 0.0;
-      std::vector<const double*> Vc(V.begin(), V.begin() + j + 1);
-      CKS(orthogonalise(ctx, Vc.data(), j + 1, V[j + 1], n, h, hn));
+      CKS(orthogonalise_read(ctx, j + 1, h, hn));
       for (int i = 0; i <= j; ++i) {
         if (!std::isfinite(h[i])) { ctx->err = "preconditioned vector is not finite"; return STMG_ERR_NONFINITE; }
         H[(size_t)i * m + j] = h[i];
@@ -1110,6 +1181,8 @@ stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_proble
 stmg_status stmg_destroy(stmg_ctx* ctx) {
   if (!ctx) return STMG_OK;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto g : ctx->iter_graphs)
+    if (g) cudaGraphExecDestroy(g);
   if (ctx->graph32) cudaGraphExecDestroy(ctx->graph32);
   if (ctx->graph64) cudaGraphExecDestroy(ctx->graph64);
   for (void* p : ctx->allocations) cudaFree(p);
