@@ -73,11 +73,12 @@ template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s);
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64_t n, cudaStream_t s);
-// partial[b][j] = sum over the block's range of V[j] . w (j < nv), plus partial[b][nv] = w.w if with_norm
-cudaError_t launch_multidot(const double* const* V, int nv, const double* w, int64_t n, int with_norm,
+// out[j] = V_j . w (j < nv, V_j = V0 + j * stride), plus out[nv] = w.w if with_norm; deterministic
+// two-stage reduction through `partial` (nblocks x (nv + 1) scratch)
+cudaError_t launch_multidot(const double* V0, int64_t stride, int nv, const double* w, int64_t n, int with_norm,
                             double* partial, int nblocks, double* out, cudaStream_t s);
-// w -= sum_j h[j] V[j]  (h on the device)
-cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int nv, double sign,
+// w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride)
+cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,
                               int64_t n, cudaStream_t s);
 cudaError_t launch_broadcast_time(const double* u0, double* u, int nt, int64_t n_nodes, cudaStream_t s);
 // y[i][node] = sum_j C[i][j] x_j[node] over nin vectors (time-only mixing)

@@ -234,6 +234,8 @@ stmg_status op_smooth(stmg_ctx* ctx, int l, int sweeps, const T* f, T* u, T* r) 
   return STMG_OK;
 }
 
+bool transfer_fused_host(int terms, int64_t n_out) { return terms <= 8 || (terms <= 27 && n_out < (int64_t)4 << 20); }
+
 template <typename T>
 stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc) {
   Level& F = ctx->levels[l];
@@ -241,7 +243,8 @@ stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc) {
   ctx->launches += 1;
   if (F.tkind == 1) {
     CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, ctx->stream));
-    ctx->launches += F.dim - 1;
+    const int R = F.tr.width_r;
+    if (!transfer_fused_host(F.dim == 3 ? R * R * R : R * R, C.size())) ctx->launches += F.dim - 1;
   }
   else CK(launch_restrict_time<T>(rc, rf, F.g, F.tt, ctx->stream));
   return STMG_OK;
@@ -254,7 +257,8 @@ stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf) {
   ctx->launches += 1;
   if (F.tkind == 1) {
     CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, ctx->stream));
-    ctx->launches += F.dim - 1;
+    const int R = F.tr.width_p;
+    if (!transfer_fused_host(F.dim == 3 ? R * R * R : R * R, F.size())) ctx->launches += F.dim - 1;
   }
   else CK(launch_prolong_time_add<T>(uf, ec, F.g, F.tt, ctx->stream));
   return STMG_OK;
@@ -357,9 +361,9 @@ bool node_constrained(const Level& L, int64_t node) {
   return rest == 0 || rest == nn1 - 1;
 }
 
-// device multi-dot helper: out[0..nv) = V_j . w (+ w.w at nv)
-stmg_status dots(stmg_ctx* ctx, const double* const* V, int nv, const double* w, int64_t n, int with_norm, double* out) {
-  CK(launch_multidot(V, nv, w, n, with_norm, ctx->partial, multidot_blocks(), out, ctx->stream));
+// device multi-dot helper: out[0..nv) = V_j . w (+ w.w at nv), V_j = V0 + j * n
+stmg_status dots(stmg_ctx* ctx, const double* V0, int nv, const double* w, int64_t n, int with_norm, double* out) {
+  CK(launch_multidot(V0, n, nv, w, n, with_norm, ctx->partial, multidot_blocks(), out, ctx->stream));
   return STMG_OK;
 }
 
@@ -373,15 +377,15 @@ __global__ void finalize_arnoldi_kernel(const double* h1, const double* h2, int 
 }
 
 // enqueue part: no host synchronisation (capturable)
-stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* const* Vp, int nv, double* w, int64_t n) {
+stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int nv, double* w, int64_t n) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
   double* d_n = ctx->dsm + 256;
   double* d_out = ctx->dsm + 384;
-  CKS(dots(ctx, Vp, nv, w, n, 0, d_h1));
-  CK(launch_multi_axpy(w, Vp, d_h1, nv, -1.0, n, ctx->stream));
-  CKS(dots(ctx, Vp, nv, w, n, 0, d_h2));
-  CK(launch_multi_axpy(w, Vp, d_h2, nv, -1.0, n, ctx->stream));
+  CKS(dots(ctx, V0, nv, w, n, 0, d_h1));
+  CK(launch_multi_axpy(w, V0, n, d_h1, nv, -1.0, n, ctx->stream));
+  CKS(dots(ctx, V0, nv, w, n, 0, d_h2));
+  CK(launch_multi_axpy(w, V0, n, d_h2, nv, -1.0, n, ctx->stream));
   CKS(dots(ctx, nullptr, 0, w, n, 1, d_n));
   finalize_arnoldi_kernel<<<1, 1, 0, ctx->stream>>>(d_h1, d_h2, nv, d_n, d_out);
   ctx->launches += 10;
@@ -400,9 +404,9 @@ stmg_status orthogonalise_read(stmg_ctx* ctx, int nv, std::vector<double>& h, do
 
 // One Arnoldi/FGMRES orthogonalisation step (classical Gram-Schmidt, twice):
 // w <- w - V h, h = [V^T w]_1 + [V^T w]_2 ; hn = ||w|| ; w <- w / hn.  Host gets h (nv) and hn.
-stmg_status orthogonalise(stmg_ctx* ctx, const double* const* Vp, int nv, double* w, int64_t n, std::vector<double>& h,
+stmg_status orthogonalise(stmg_ctx* ctx, const double* V0, int nv, double* w, int64_t n, std::vector<double>& h,
                           double& hn) {
-  CKS(orthogonalise_enqueue(ctx, Vp, nv, w, n));
+  CKS(orthogonalise_enqueue(ctx, V0, nv, w, n));
   return orthogonalise_read(ctx, nv, h, hn);
 }
 
@@ -437,8 +441,7 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
     CKS(op_apply<double>(ctx, L, z, V[j + 1]));
     std::vector<double> h;
     double hn = 0.0;
-    std::vector<const double*> Vc(V.begin(), V.begin() + j + 1);
-    CKS(orthogonalise(ctx, Vc.data(), j + 1, V[j + 1], n, h, hn));
+    CKS(orthogonalise(ctx, V[0], j + 1, V[j + 1], n, h, hn));
     for (int i = 0; i <= j; ++i) H[i * steps + j] = h[i];
     H[(j + 1) * steps + j] = hn;
     if (hn <= 1e-14 * std::fabs(H[j * steps + j]) + 1e-300) { m = j + 1; break; }
@@ -896,9 +899,7 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
     CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   CKS(op_apply<double>(ctx, L, z, w));
-  std::vector<const double*> Vc(j + 1);
-  for (int i = 0; i <= j; ++i) Vc[i] = ctx->V + (size_t)i * n;
-  return orthogonalise_enqueue(ctx, Vc.data(), j + 1, w, n);
+  return orthogonalise_enqueue(ctx, ctx->V, j + 1, w, n);
 }
 
 stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
@@ -1018,8 +1019,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
       y[i] = t / H[(size_t)i * m + i];
     }
     CK(cudaMemcpyAsync(ctx->dsm + 320, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, ctx->stream));
-    std::vector<const double*> Zc(Z.begin(), Z.begin() + jend);
-    CK(launch_multi_axpy(x, Zc.data(), ctx->dsm + 320, jend, 1.0, n, ctx->stream));
+    CK(launch_multi_axpy(x, ctx->Z, n, ctx->dsm + 320, jend, 1.0, n, ctx->stream));
     ctx->launches += 1;
     (void)breakdown;
   }

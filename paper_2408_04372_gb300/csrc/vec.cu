@@ -12,7 +12,6 @@ namespace stmg {
 namespace {
 
 constexpr int kMaxVec = 72;
-struct PtrList { const double* p[kMaxVec]; };
 constexpr int kDotBlocks = 152 * 4;
 constexpr int kDotThreads = 256;
 constexpr int kChunk = 8;
@@ -53,7 +52,8 @@ __device__ inline double block_sum(double v, double* red) {
 
 // stage 1: partial[j * nblocks + b] = sum over block b's fixed slice of V_j . w ; j = nv holds w . w
 __global__ void __launch_bounds__(kDotThreads)
-multidot_stage1(PtrList V, int nv, const double* __restrict__ w, int64_t n, int with_norm, double* __restrict__ partial) {
+multidot_stage1(const double* __restrict__ V0, int64_t stride, int nv, const double* __restrict__ w, int64_t n,
+                int with_norm, double* __restrict__ partial) {
   __shared__ double red[kDotThreads / 32][kChunk];
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * per, hi = std::min<int64_t>(n, lo + per);
@@ -68,7 +68,7 @@ multidot_stage1(PtrList V, int nv, const double* __restrict__ w, int64_t n, int 
 #pragma unroll
       for (int c = 0; c < kChunk; ++c) {
         const int j = j0 + c;
-        if (j < nv) acc[c] += __ldg(V.p[j] + i) * wi;
+        if (j < nv) acc[c] += __ldg(V0 + j * stride + i) * wi;
         else if (j == nv && with_norm) acc[c] += wi * wi;
       }
     }
@@ -99,14 +99,14 @@ multidot_stage2(const double* __restrict__ partial, int nblocks, double* __restr
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-__global__ void multi_axpy_kernel(double* __restrict__ w, PtrList V, const double* __restrict__ h, int nv, double sign,
-                                  int64_t n) {
+__global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V0, int64_t stride,
+                                  const double* __restrict__ h, int nv, double sign, int64_t n) {
   __shared__ double sh[kMaxVec];
   for (int j = threadIdx.x; j < nv; j += blockDim.x) sh[j] = h[j];
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int j = 0; j < nv; ++j) s += sh[j] * V.p[j][i];
+    for (int j = 0; j < nv; ++j) s += sh[j] * __ldg(V0 + j * stride + i);
     w[i] += sign * s;
   }
 }
@@ -179,23 +179,19 @@ cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_multidot(const double* const* V, int nv, const double* w, int64_t n, int with_norm, double* partial,
-                            int nblocks, double* out, cudaStream_t s) {
+cudaError_t launch_multidot(const double* V0, int64_t stride, int nv, const double* w, int64_t n, int with_norm,
+                            double* partial, int nblocks, double* out, cudaStream_t s) {
   if (nv > kMaxVec || nblocks < 1) return cudaErrorInvalidValue;
-  PtrList pl{};
-  for (int j = 0; j < nv; ++j) pl.p[j] = V[j];
   const int ntot = nv + (with_norm ? 1 : 0);
-  multidot_stage1<<<nblocks, kDotThreads, 0, s>>>(pl, nv, w, n, with_norm, partial);
+  multidot_stage1<<<nblocks, kDotThreads, 0, s>>>(V0, stride, nv, w, n, with_norm, partial);
   multidot_stage2<<<ntot, kDotThreads, 0, s>>>(partial, nblocks, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_axpy(double* w, const double* const* V, const double* h, int nv, double sign, int64_t n,
-                              cudaStream_t s) {
+cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,
+                              int64_t n, cudaStream_t s) {
   if (nv > kMaxVec) return cudaErrorInvalidValue;
-  PtrList pl{};
-  for (int j = 0; j < nv; ++j) pl.p[j] = V[j];
-  multi_axpy_kernel<<<grid_blocks(n), 256, 0, s>>>(w, pl, h, nv, sign, n);
+  multi_axpy_kernel<<<grid_blocks(n), 256, 0, s>>>(w, V0, stride, h, nv, sign, n);
   return cudaGetLastError();
 }
 
