@@ -220,7 +220,8 @@ struct AsmCfg {
 // loads of a plane are in flight together (the kernel is bound by this stream).
 template <int DIM, int N, int NT, typename T, typename TI>
 __global__ void __launch_bounds__(AsmCfg<DIM, N, NT, TI>::CPB * AsmCfg<DIM, N, NT, TI>::TPC)
-asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g, ModeTab<T> mt) {
+asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g, ModeTab<T> mt,
+                 const T* __restrict__ copy_src, T* __restrict__ copy_dst) {
   using C = AsmCfg<DIM, N, NT, TI>;
   constexpr int NB = C::NB, TPC = C::TPC, CPB = C::CPB;
   constexpr int64_t CS = C::CS;
@@ -242,6 +243,10 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
   T rr[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
+  if (copy_dst && active) {  // side job for the V-cycle: copy_dst := copy_src on this cell's nodes
+#pragma unroll
+    for (int t = 0; t < NT; ++t) copy_dst[t * g.n_nodes + node] = copy_src[t * g.n_nodes + node];
+  }
   if (a < NB) {
 #pragma unroll
     for (int m = 0; m < NT; ++m) {
@@ -314,10 +319,12 @@ cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, 
 }
 
 template <int DIM, int N, int NT, typename T, typename TI>
-cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s) {
+cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd,
+                    cudaStream_t s) {
   using C = AsmCfg<DIM, N, NT, TI>;
   const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
-  asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, C::CPB * C::TPC, 0, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt);
+  asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, C::CPB * C::TPC, 0, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt,
+                                                                                 cs, cd);
   return cudaGetLastError();
 }
 
@@ -344,14 +351,14 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
 
 #define STMG_ASM_CASE(DIM, N, NT)                                                                  \
   if (dim == DIM && n == N && nt == NT) {                                                          \
-    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, s);                 \
-    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, s);                  \
-    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, s);                             \
+    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, s);         \
+    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, s);          \
+    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, s);                     \
   }
 
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
-                             const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s) {
+                             const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd, cudaStream_t s) {
   STMG_ASM_CASE(3, 2, 1) STMG_ASM_CASE(3, 2, 2) STMG_ASM_CASE(3, 2, 3) STMG_ASM_CASE(3, 2, 4)
   STMG_ASM_CASE(3, 3, 1) STMG_ASM_CASE(3, 3, 2) STMG_ASM_CASE(3, 3, 3) STMG_ASM_CASE(3, 3, 4)
   STMG_ASM_CASE(3, 4, 1) STMG_ASM_CASE(3, 4, 2) STMG_ASM_CASE(3, 4, 3) STMG_ASM_CASE(3, 4, 4)
@@ -363,8 +370,9 @@ cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const voi
 }
 
 template cudaError_t launch_asm_apply<float>(int, int, int, const float*, float*, const void*, int, const GridDesc&,
-                                             const ModeTab<float>&, cudaStream_t);
+                                             const ModeTab<float>&, const float*, float*, cudaStream_t);
 template cudaError_t launch_asm_apply<double>(int, int, int, const double*, double*, const void*, int,
-                                              const GridDesc&, const ModeTab<double>&, cudaStream_t);
+                                              const GridDesc&, const ModeTab<double>&, const double*, double*,
+                                              cudaStream_t);
 
 }  // namespace stmg

@@ -20,7 +20,7 @@ template <int N> constexpr int fd_cells_per_block() { return N == 2 ? 32 : N == 
 template <int N, int NT, typename T, int CPB>
 __global__ void __launch_bounds__(CPB * N * N)
 fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict__ rho_cell, GridDesc g, FDTab<T> fd,
-                ModeTab<T> mt) {
+                ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst) {
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
@@ -50,6 +50,10 @@ fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict_
     T rr[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
+    if (copy_dst && active) {  // side job for the V-cycle: copy_dst := copy_src on this cell's nodes
+#pragma unroll
+      for (int t = 0; t < NT; ++t) copy_dst[t * g.n_nodes + node] = copy_src[t * g.n_nodes + node];
+    }
 #pragma unroll
     for (int m = 0; m < NT; ++m) {
       const bool is_real = m < mt.nreal;
@@ -171,7 +175,7 @@ fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict_
 
 template <int N, int NT, typename T>
 cudaError_t fd_t(const T* r, T* u, const T* rho, const GridDesc& g, const FDTab<T>& fd, const ModeTab<T>& mt,
-                 cudaStream_t s) {
+                 const T* cs, T* cd, cudaStream_t s) {
   constexpr int CPB = fd_cells_per_block<N>();
   const size_t smem = (size_t)CPB * 2 * NT * N * N * N * sizeof(T);
   auto k = fd_apply_kernel<N, NT, T, CPB>;
@@ -182,18 +186,18 @@ cudaError_t fd_t(const T* r, T* u, const T* rho, const GridDesc& g, const FDTab<
     attr = true;
   }
   const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
-  k<<<(unsigned)blocks, CPB * N * N, smem, s>>>(r, u, rho, g, fd, mt);
+  k<<<(unsigned)blocks, CPB * N * N, smem, s>>>(r, u, rho, g, fd, mt, cs, cd);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 #define STMG_FD_CASE(N, NT) \
-  if (n == N && nt == NT) return fd_t<N, NT, T>(r, u, rho, g, fd, mt, s);
+  if (n == N && nt == NT) return fd_t<N, NT, T>(r, u, rho, g, fd, mt, cs, cd, s);
 
 template <typename T>
 cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho, const GridDesc& g, const FDTab<T>& fd,
-                            const ModeTab<T>& mt, cudaStream_t s) {
+                            const ModeTab<T>& mt, const T* cs, T* cd, cudaStream_t s) {
   STMG_FD_CASE(2, 1) STMG_FD_CASE(2, 2) STMG_FD_CASE(2, 3) STMG_FD_CASE(2, 4)
   STMG_FD_CASE(3, 1) STMG_FD_CASE(3, 2) STMG_FD_CASE(3, 3) STMG_FD_CASE(3, 4)
   STMG_FD_CASE(4, 1) STMG_FD_CASE(4, 2) STMG_FD_CASE(4, 3) STMG_FD_CASE(4, 4)
@@ -202,8 +206,10 @@ cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho, const
 }
 
 template cudaError_t launch_fd_apply<float>(int, int, const float*, float*, const float*, const GridDesc&,
-                                            const FDTab<float>&, const ModeTab<float>&, cudaStream_t);
+                                            const FDTab<float>&, const ModeTab<float>&, const float*, float*,
+                                            cudaStream_t);
 template cudaError_t launch_fd_apply<double>(int, int, const double*, double*, const double*, const GridDesc&,
-                                             const FDTab<double>&, const ModeTab<double>&, cudaStream_t);
+                                             const FDTab<double>&, const ModeTab<double>&, const double*, double*,
+                                             cudaStream_t);
 
 }  // namespace stmg

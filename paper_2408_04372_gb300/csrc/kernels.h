@@ -34,14 +34,15 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
                              int inv_prec, cudaStream_t s);
 // elements per cell in the inverse store (N_t planes, padded to a 16-byte multiple)
 int64_t asm_cell_stride(int dim, int n, int nt);
+// copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
-                             const GridDesc& g, const ModeTab<T>& mt, cudaStream_t s);
+                             const GridDesc& g, const ModeTab<T>& mt, const T* copy_src, T* copy_dst, cudaStream_t s);
 
 // ---- fast diagonalisation local solves (fd.cu), 3D Cartesian cells ----
 template <typename T>
 cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho_cell, const GridDesc& g, const FDTab<T>& fd,
-                            const ModeTab<T>& mt, cudaStream_t s);
+                            const ModeTab<T>& mt, const T* copy_src, T* copy_dst, cudaStream_t s);
 
 // ---- transfers (transfer.cu) ----
 // 1D lists of the separable transfers, Dirichlet masks folded in: prolongation rows of fine
@@ -56,17 +57,21 @@ struct Transfer1D {
   void* tmp1;            // scratch: nt * nn1_f^2 * nn1_c doubles each
   void* tmp2;
 };
+// Side jobs for the V-cycle (pointers may be NULL): prolongations also copy copy_src -> copy_dst over
+// the fine vector, restrictions also zero zero_dst over the coarse vector.
 template <typename T>
 cudaError_t launch_prolong_space_add(T* uf, const T* ec, const GridDesc& gf, const GridDesc& gc, int nt,
-                                     const Transfer1D& t, cudaStream_t s);
+                                     const Transfer1D& t, const T* copy_src, T* copy_dst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict_space(T* rc, const T* rf, const GridDesc& gf, const GridDesc& gc, int nt,
-                                  const Transfer1D& t, cudaStream_t s);
+                                  const Transfer1D& t, T* zero_dst, cudaStream_t s);
 struct TimeTransfer { int ntf, ntc; double P[kMaxNT][kMaxNT]; };
 template <typename T>
-cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const TimeTransfer& t, cudaStream_t s);
+cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const TimeTransfer& t, const T* copy_src,
+                                    T* copy_dst, cudaStream_t s);
 template <typename T>
-cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const TimeTransfer& t, cudaStream_t s);
+cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const TimeTransfer& t, T* zero_dst,
+                                 cudaStream_t s);
 
 // ---- vectors, reductions, coarse solve (vec.cu) ----
 template <typename Tin, typename Tout>

@@ -211,16 +211,18 @@ stmg_status op_residual(stmg_ctx* ctx, Level& L, const T* f, const T* u, T* r) {
   return STMG_OK;
 }
 
+// u += omega * ASM r ; optionally also copy_dst := copy_src (a fused side job for the V-cycle)
 template <typename T>
-stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega) {
+stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega, const T* copy_src = nullptr,
+                   T* copy_dst = nullptr) {
   ModeTab<T> mt = mt_of<T>(L);
   mt.omega = (T)omega;
   ctx->launches += 1;
   if (L.fd) {
-    CK(launch_fd_apply<T>(L.n, L.nt, r, u, rho_of<T>(L), L.g, fd_of<T>(L), mt, ctx->stream));
+    CK(launch_fd_apply<T>(L.n, L.nt, r, u, rho_of<T>(L), L.g, fd_of<T>(L), mt, copy_src, copy_dst, ctx->stream));
     return STMG_OK;
   }
-  CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, ctx->stream));
+  CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->stream));
   return STMG_OK;
 }
 
@@ -236,69 +238,93 @@ stmg_status op_smooth(stmg_ctx* ctx, int l, int sweeps, const T* f, T* u, T* r) 
 
 bool transfer_fused_host(int terms, int64_t n_out) { return terms <= 8 || (terms <= 27 && n_out < (int64_t)4 << 20); }
 
+// r_{l+1} = R r_l ; optionally also zero_dst := 0 over the coarse vector (V-cycle side job)
 template <typename T>
-stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc) {
+stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc, T* zero_dst = nullptr) {
   Level& F = ctx->levels[l];
   Level& C = ctx->levels[l + 1];
   ctx->launches += 1;
   if (F.tkind == 1) {
-    CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, ctx->stream));
+    CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, zero_dst, ctx->stream));
     const int R = F.tr.width_r;
     if (!transfer_fused_host(F.dim == 3 ? R * R * R : R * R, C.size())) ctx->launches += F.dim - 1;
   }
-  else CK(launch_restrict_time<T>(rc, rf, F.g, F.tt, ctx->stream));
+  else CK(launch_restrict_time<T>(rc, rf, F.g, F.tt, zero_dst, ctx->stream));
   return STMG_OK;
 }
 
+// u_l += P e_{l+1} ; optionally also copy_dst := copy_src over the fine vector (V-cycle side job)
 template <typename T>
-stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf) {
+stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf, const T* copy_src = nullptr,
+                              T* copy_dst = nullptr) {
   Level& F = ctx->levels[l];
   Level& C = ctx->levels[l + 1];
   ctx->launches += 1;
   if (F.tkind == 1) {
-    CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, ctx->stream));
+    CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, copy_src, copy_dst, ctx->stream));
     const int R = F.tr.width_p;
     if (!transfer_fused_host(F.dim == 3 ? R * R * R : R * R, F.size())) ctx->launches += F.dim - 1;
   }
-  else CK(launch_prolong_time_add<T>(uf, ec, F.g, F.tt, ctx->stream));
+  else CK(launch_prolong_time_add<T>(uf, ec, F.g, F.tt, copy_src, copy_dst, ctx->stream));
+  return STMG_OK;
+}
+
+// r += -S u on unconstrained rows, r already holding f (the V-cycle keeps u = 0 on constrained nodes,
+// so f - u = f there): the residual without its initialisation pass
+template <typename T>
+stmg_status op_residual_preset(stmg_ctx* ctx, Level& L, const T* u, T* r) {
+  OpTab<T> t = tab_of<T>(L);
+  t.sign = T(-1);
+  ctx->launches += 1;
+  CK(launch_apply<T>(L.dim, L.n, L.nt, u, r, geo_of<T>(L), L.g, t, 1, ctx->stream));
   return STMG_OK;
 }
 
 template <typename T>
-stmg_status coarse_solve(stmg_ctx* ctx, Level& L, const T* f, T* u) {
-  CK(cudaMemsetAsync(u, 0, sizeof(T) * L.size(), ctx->stream));
+stmg_status coarse_solve(stmg_ctx* ctx, Level& L, const T* f, T* u, bool u_zeroed = false) {
+  if (!u_zeroed) CK(cudaMemsetAsync(u, 0, sizeof(T) * L.size(), ctx->stream));
   CK(launch_coarse_solve<T>(f, u, cinv_of<T>(L), L.cmap, L.n_coarse, L.size(), ctx->stream));
   ctx->launches += 1;
   return STMG_OK;
 }
 
-// Algorithm stmg: V-cycle with zero initial guess on level l, f_l -> u_l
+// Algorithm stmg: V-cycle with zero initial guess on level l, f_l -> u_l.  Bookkeeping passes
+// are fused into the neighbouring kernels: the restriction into level l zeroes u_l, the first
+// smoothing kernel and the prolongation write r_l := f_l, so that the residuals need only the
+// operator kernel (u_l stays 0 on constrained nodes throughout).
 template <typename T>
 stmg_status vcycle_level(stmg_ctx* ctx, int l) {
   Level& L = ctx->levels[l];
   T* f = fv<T>(L);
   T* u = uv<T>(L);
   T* r = rv<T>(L);
-  if (l == (int)ctx->levels.size() - 1) return coarse_solve<T>(ctx, L, f, u);
-  CK(cudaMemsetAsync(u, 0, sizeof(T) * L.size(), ctx->stream));
-  for (int s = 0; s < ctx->opt.nu_pre; ++s) {
+  if (l == (int)ctx->levels.size() - 1) return coarse_solve<T>(ctx, L, f, u, l > 0);
+  if (l == 0) CK(cudaMemsetAsync(u, 0, sizeof(T) * L.size(), ctx->stream));
+  const int nu1 = ctx->opt.nu_pre, nu2 = ctx->opt.nu_post;
+  for (int s = 0; s < nu1; ++s) {
     if (s == 0) {
-      CKS(op_asm<T>(ctx, L, f, u, L.omega));  // zero guess: residual = f
+      // zero guess: residual = f; on the last pre-sweep also preset r := f for the residual below
+      CKS(op_asm<T>(ctx, L, f, u, L.omega, nu1 == 1 ? f : nullptr, nu1 == 1 ? r : nullptr));
     } else {
       CKS(op_residual<T>(ctx, L, f, u, r));
       CKS(op_asm<T>(ctx, L, r, u, L.omega));
+      if (s == nu1 - 1) CK(cudaMemcpyAsync(r, f, sizeof(T) * L.size(), cudaMemcpyDeviceToDevice, ctx->stream));
     }
   }
   const T* res = f;
-  if (ctx->opt.nu_pre > 0) {
-    CKS(op_residual<T>(ctx, L, f, u, r));
+  if (nu1 > 0) {
+    CKS(op_residual_preset<T>(ctx, L, u, r));
     res = r;
   }
   Level& Cl = ctx->levels[l + 1];
-  CKS(op_restrict<T>(ctx, l, res, fv<T>(Cl)));
+  CKS(op_restrict<T>(ctx, l, res, fv<T>(Cl), uv<T>(Cl)));
   CKS(vcycle_level<T>(ctx, l + 1));
-  CKS(op_prolongate_add<T>(ctx, l, uv<T>(Cl), u));
-  CKS(op_smooth<T>(ctx, l, ctx->opt.nu_post, f, u, r));
+  CKS(op_prolongate_add<T>(ctx, l, uv<T>(Cl), u, nu2 > 0 ? f : nullptr, nu2 > 0 ? r : nullptr));
+  for (int s = 0; s < nu2; ++s) {
+    if (s == 0) CKS(op_residual_preset<T>(ctx, L, u, r));
+    else CKS(op_residual<T>(ctx, L, f, u, r));
+    CKS(op_asm<T>(ctx, L, r, u, L.omega));
+  }
   return STMG_OK;
 }
 

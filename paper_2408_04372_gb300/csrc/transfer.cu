@@ -22,13 +22,26 @@ inline int grid_blocks(int64_t total) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
 }
 
+// Optional side job of a transfer's final pass over output entries e (V-cycle fusion):
+// copy_dst[e] = copy_src[e] and/or zero_dst[e] = 0.
+template <typename T>
+struct SideJob {
+  const T* copy_src = nullptr;
+  T* copy_dst = nullptr;
+  T* zero_dst = nullptr;
+  __device__ void run(int64_t e) const {
+    if (copy_dst) copy_dst[e] = copy_src[e];
+    if (zero_dst) zero_dst[e] = T(0);
+  }
+};
+
 // One 1D pass of a separable transfer along `axis` of a [nt][d2][d1][d0] array (d0 fastest):
 // out[..., i, ...] (+)= sum_r w[i][r] in[..., idx[i][r], ...], the axis length changing from
 // in_dims[axis] to n_out.
 template <typename T>
 __global__ void gather_axis_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2, int nt,
                                    int axis, int n_out, const int* __restrict__ idx, const double* __restrict__ w,
-                                   int R, int accumulate) {
+                                   int R, int accumulate, SideJob<T> side) {
   const int o0 = axis == 0 ? n_out : d0, o1 = axis == 1 ? n_out : d1, o2 = axis == 2 ? n_out : d2;
   const int64_t total = (int64_t)nt * o2 * o1 * o0;
   const int64_t sin_ = axis == 0 ? 1 : (axis == 1 ? d0 : (int64_t)d0 * d1);
@@ -48,6 +61,7 @@ __global__ void gather_axis_kernel(const T* __restrict__ in, T* __restrict__ out
     }
     if (accumulate) out[e] += acc;
     else out[e] = acc;
+    side.run(e);
   }
 }
 
@@ -61,7 +75,8 @@ __host__ __device__ inline bool transfer_fused(int terms, int64_t n_out) {
 // 1D lists directly (width^dim terms), one launch instead of dim.
 template <typename T>
 __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ out, int dim, int nt, int nin, int nout,
-                                    const int* __restrict__ idx, const double* __restrict__ w, int R, int accumulate) {
+                                    const int* __restrict__ idx, const double* __restrict__ w, int R, int accumulate,
+                                    SideJob<T> side) {
   const int64_t per = dim == 3 ? (int64_t)nout * nout * nout : (int64_t)nout * nout;
   const int64_t per_in = dim == 3 ? (int64_t)nin * nin * nin : (int64_t)nin * nin;
   const int64_t total = per * nt;
@@ -95,32 +110,34 @@ __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ ou
     }
     if (accumulate) out[e] += acc;
     else out[e] = acc;
+    side.run(e);
   }
 }
 
 template <typename T>
 cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, const int* idx, const double* w, int R,
-                      T* t1, T* t2, int accumulate, cudaStream_t s) {
+                      T* t1, T* t2, int accumulate, SideJob<T> side, cudaStream_t s) {
+  const SideJob<T> none{};
   // passes x, y(, z): dims go from nin^dim to nout^dim
   auto blocks = [](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); };
   const int terms = dim == 3 ? R * R * R : R * R;
   const int64_t nout_total = (int64_t)nt * (dim == 3 ? (int64_t)nout * nout * nout : (int64_t)nout * nout);
   if (transfer_fused(terms, nout_total)) {
-    gather_fused_kernel<T><<<blocks(nout_total), 256, 0, s>>>(in, out, dim, nt, nin, nout, idx, w, R, accumulate);
+    gather_fused_kernel<T><<<blocks(nout_total), 256, 0, s>>>(in, out, dim, nt, nin, nout, idx, w, R, accumulate, side);
     return cudaGetLastError();
   }
   if (dim == 2) {
     const int64_t n1 = (int64_t)nt * nin * nout;
-    gather_axis_kernel<T><<<blocks(n1), 256, 0, s>>>(in, t1, nin, nin, 1, nt, 0, nout, idx, w, R, 0);
+    gather_axis_kernel<T><<<blocks(n1), 256, 0, s>>>(in, t1, nin, nin, 1, nt, 0, nout, idx, w, R, 0, none);
     const int64_t n2 = (int64_t)nt * nout * nout;
-    gather_axis_kernel<T><<<blocks(n2), 256, 0, s>>>(t1, out, nout, nin, 1, nt, 1, nout, idx, w, R, accumulate);
+    gather_axis_kernel<T><<<blocks(n2), 256, 0, s>>>(t1, out, nout, nin, 1, nt, 1, nout, idx, w, R, accumulate, side);
   } else {
     const int64_t n1 = (int64_t)nt * nin * nin * nout;
-    gather_axis_kernel<T><<<blocks(n1), 256, 0, s>>>(in, t1, nin, nin, nin, nt, 0, nout, idx, w, R, 0);
+    gather_axis_kernel<T><<<blocks(n1), 256, 0, s>>>(in, t1, nin, nin, nin, nt, 0, nout, idx, w, R, 0, none);
     const int64_t n2 = (int64_t)nt * nin * nout * nout;
-    gather_axis_kernel<T><<<blocks(n2), 256, 0, s>>>(t1, t2, nout, nin, nin, nt, 1, nout, idx, w, R, 0);
+    gather_axis_kernel<T><<<blocks(n2), 256, 0, s>>>(t1, t2, nout, nin, nin, nt, 1, nout, idx, w, R, 0, none);
     const int64_t n3 = (int64_t)nt * nout * nout * nout;
-    gather_axis_kernel<T><<<blocks(n3), 256, 0, s>>>(t2, out, nout, nout, nin, nt, 2, nout, idx, w, R, accumulate);
+    gather_axis_kernel<T><<<blocks(n3), 256, 0, s>>>(t2, out, nout, nout, nin, nt, 2, nout, idx, w, R, accumulate, side);
   }
   return cudaGetLastError();
 }
@@ -134,9 +151,11 @@ __device__ inline bool node_on_boundary(int64_t node, const GridDesc& g) {
 }
 
 template <typename T>
-__global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict__ ec, GridDesc g, TimeTransfer tt) {
+__global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict__ ec, GridDesc g, TimeTransfer tt,
+                                       SideJob<T> side) {
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
        node += (int64_t)gridDim.x * blockDim.x) {
+    for (int i = 0; i < tt.ntf; ++i) side.run(i * g.n_nodes + node);
     if (node_on_boundary(node, g)) continue;
     T ev[kMaxNT];
     for (int j = 0; j < tt.ntc; ++j) ev[j] = ec[j * g.n_nodes + node];
@@ -149,9 +168,11 @@ __global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict_
 }
 
 template <typename T>
-__global__ void restrict_time_kernel(T* __restrict__ rc, const T* __restrict__ rf, GridDesc g, TimeTransfer tt) {
+__global__ void restrict_time_kernel(T* __restrict__ rc, const T* __restrict__ rf, GridDesc g, TimeTransfer tt,
+                                     SideJob<T> side) {
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
        node += (int64_t)gridDim.x * blockDim.x) {
+    for (int j = 0; j < tt.ntc; ++j) side.run(j * g.n_nodes + node);
     const bool bnd = node_on_boundary(node, g);
     T rv[kMaxNT];
     for (int i = 0; i < tt.ntf; ++i) rv[i] = bnd ? T(0) : rf[i * g.n_nodes + node];
@@ -167,34 +188,47 @@ __global__ void restrict_time_kernel(T* __restrict__ rc, const T* __restrict__ r
 
 template <typename T>
 cudaError_t launch_prolong_space_add(T* uf, const T* ec, const GridDesc& gf, const GridDesc& gc, int nt,
-                                     const Transfer1D& t, cudaStream_t s) {
+                                     const Transfer1D& t, const T* copy_src, T* copy_dst, cudaStream_t s) {
+  SideJob<T> side;
+  side.copy_src = copy_src;
+  side.copy_dst = copy_dst;
   return separable<T>(ec, uf, gf.dim, nt, gc.nn1, gf.nn1, t.p_idx, t.p_w, t.width_p, reinterpret_cast<T*>(t.tmp1),
-                      reinterpret_cast<T*>(t.tmp2), 1, s);
+                      reinterpret_cast<T*>(t.tmp2), 1, side, s);
 }
 template <typename T>
 cudaError_t launch_restrict_space(T* rc, const T* rf, const GridDesc& gf, const GridDesc& gc, int nt,
-                                  const Transfer1D& t, cudaStream_t s) {
+                                  const Transfer1D& t, T* zero_dst, cudaStream_t s) {
+  SideJob<T> side;
+  side.zero_dst = zero_dst;
   return separable<T>(rf, rc, gf.dim, nt, gf.nn1, gc.nn1, t.r_idx, t.r_w, t.width_r, reinterpret_cast<T*>(t.tmp1),
-                      reinterpret_cast<T*>(t.tmp2), 0, s);
+                      reinterpret_cast<T*>(t.tmp2), 0, side, s);
 }
 template <typename T>
-cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const TimeTransfer& t, cudaStream_t s) {
-  prolong_time_add_kernel<T><<<grid_blocks(g.n_nodes), 256, 0, s>>>(uf, ec, g, t);
+cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const TimeTransfer& t, const T* copy_src,
+                                    T* copy_dst, cudaStream_t s) {
+  SideJob<T> side;
+  side.copy_src = copy_src;
+  side.copy_dst = copy_dst;
+  prolong_time_add_kernel<T><<<grid_blocks(g.n_nodes), 256, 0, s>>>(uf, ec, g, t, side);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const TimeTransfer& t, cudaStream_t s) {
-  restrict_time_kernel<T><<<grid_blocks(g.n_nodes), 256, 0, s>>>(rc, rf, g, t);
+cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const TimeTransfer& t, T* zero_dst,
+                                 cudaStream_t s) {
+  SideJob<T> side;
+  side.zero_dst = zero_dst;
+  restrict_time_kernel<T><<<grid_blocks(g.n_nodes), 256, 0, s>>>(rc, rf, g, t, side);
   return cudaGetLastError();
 }
 
 #define STMG_TR_INST(T)                                                                                        \
   template cudaError_t launch_prolong_space_add<T>(T*, const T*, const GridDesc&, const GridDesc&, int,          \
-                                                   const Transfer1D&, cudaStream_t);                             \
+                                                   const Transfer1D&, const T*, T*, cudaStream_t);               \
   template cudaError_t launch_restrict_space<T>(T*, const T*, const GridDesc&, const GridDesc&, int,             \
-                                                const Transfer1D&, cudaStream_t);                                \
-  template cudaError_t launch_prolong_time_add<T>(T*, const T*, const GridDesc&, const TimeTransfer&, cudaStream_t); \
-  template cudaError_t launch_restrict_time<T>(T*, const T*, const GridDesc&, const TimeTransfer&, cudaStream_t);
+                                                const Transfer1D&, T*, cudaStream_t);                            \
+  template cudaError_t launch_prolong_time_add<T>(T*, const T*, const GridDesc&, const TimeTransfer&, const T*, T*, \
+                                                  cudaStream_t);                                                 \
+  template cudaError_t launch_restrict_time<T>(T*, const T*, const GridDesc&, const TimeTransfer&, T*, cudaStream_t);
 STMG_TR_INST(float)
 STMG_TR_INST(double)
 
