@@ -58,7 +58,9 @@ typedef enum {
 enum { STMG_HEAT = 0, STMG_WAVE = 1 };                 /* PDE, eqs. heat, wave */
 enum { STMG_DG = 0, STMG_CGP = 1 };                    /* time discretisation, Sections 2.1 / 2.2 */
 enum { STMG_COEFF_PER_CELL = 0, STMG_COEFF_PER_QPOINT = 1 };
-enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3 };   /* 0 in an option = default */
+/* STMG_DF32 = double-float: FP32 input vector, arithmetic on pairs of FP32 numbers (about 44
+ * significand bits), FP64 output; only for the finest-level operator (outer_apply, stmg_apply). */
+enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3, STMG_DF32 = 4 };   /* 0 in an option = default */
 enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2 };
 
 /* Structured grid of n_cells^dim cells.  vertices: HOST array of
@@ -102,6 +104,9 @@ typedef struct {
   int fgmres_restart;      /* [30] */
   double rtol;             /* relative residual target of stmg_solve [1e-8] */
   int max_it;              /* [200] */
+  int outer_apply;         /* arithmetic of the FGMRES operator apply on V-cycle outputs: STMG_FP64, or
+                              STMG_DF32 (FP32 V-cycle only; its outputs are exact in FP32) [DF32 with
+                              the FP32 V-cycle, else FP64].  Residuals b - S x always use FP64. */
 } stmg_options;
 
 typedef struct {
@@ -129,7 +134,8 @@ stmg_status stmg_node_coords(const stmg_ctx* ctx, int level, double* xyz);
 /* Physical Gauss-point coordinates of a level (HOST output, cells x (p+1)^dim x dim). */
 stmg_status stmg_qpoint_coords(const stmg_ctx* ctx, int level, double* xyz);
 
-/* y = S_l x on level l (matrix-free, sum factorisation, Section 3.1). */
+/* y = S_l x on level l (matrix-free, sum factorisation, Section 3.1).  precision STMG_DF32
+ * (level 0 of a context created with outer_apply = STMG_DF32): x is float*, y is double*. */
 stmg_status stmg_apply(stmg_ctx* ctx, int level, int precision, const void* x, void* y);
 /* r = f - S_l u. */
 stmg_status stmg_residual(stmg_ctx* ctx, int level, int precision, const void* f, const void* u, void* r);
@@ -181,6 +187,8 @@ stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f
 typedef struct stmg_net stmg_net;
 stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int* channels, const double* weights,
                             const double* biases, const double* scales);
+/* Frees the network.  Destroying its context first is allowed: the network is then detached,
+ * every later call on it returns STMG_ERR_INVALID_ARG, and stmg_net_destroy still frees it. */
 stmg_status stmg_net_destroy(stmg_net* net);
 /* u_guess = network guess for the slab after u_prev, from the slab's source f. */
 stmg_status stmg_net_predict(stmg_net* net, const double* u_prev, const double* f, double* u_guess);
@@ -235,7 +243,8 @@ stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count);
  * overwritten) and returns the mean duration from CUDA events recorded on that
  * stream.  kernel: STMG_KERNEL_APPLY (the operator kernel alone, no row
  * initialisation), STMG_KERNEL_ASM (one additive Schwarz application) or
- * STMG_KERNEL_VCYCLE (one whole V-cycle from level 0; level must be 0).  Synchronous. */
+ * STMG_KERNEL_VCYCLE (one whole V-cycle from level 0; level must be 0).  Synchronous.
+ * precision STMG_DF32 times the double-float level-0 apply (outer_apply = STMG_DF32). */
 enum { STMG_KERNEL_APPLY = 1, STMG_KERNEL_ASM = 2, STMG_KERNEL_VCYCLE = 3 };
 stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision, int reps, double* avg_ms);
 

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstmg.so")
@@ -16,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libstmg.so")
 HEAT, WAVE = 0, 1
 DG, CGP = 0, 1
 COEFF_PER_CELL, COEFF_PER_QPOINT = 0, 1
-FP64, FP32, BF16 = 1, 2, 3
+FP64, FP32, BF16, DF32 = 1, 2, 3, 4
 SMOOTHER_AUTO, SMOOTHER_DENSE, SMOOTHER_FD = 0, 1, 2
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
@@ -51,7 +52,7 @@ class Options(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("vcycle_precision", ctypes.c_int),
                 ("inverse_precision", ctypes.c_int), ("smoother_kind", ctypes.c_int),
                 ("omega", ctypes.POINTER(ctypes.c_double)), ("fgmres_restart", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("max_it", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("outer_apply", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -128,11 +129,13 @@ class Context:
 
     def __init__(self, dim, n_cells, p, k, tau, pde=HEAT, scheme=DG, vertices=None, coeff=None,
                  coeff_mode=COEFF_PER_CELL, nu_pre=1, nu_post=1, vcycle_precision=FP32, inverse_precision=0,
-                 omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO):
+                 omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO,
+                 outer_apply=0):
         import numpy as np
         import torch
         self.lib = load()
         self._keep = []
+        self._nets = weakref.WeakSet()
         v = None if vertices is None else np.ascontiguousarray(vertices, dtype=np.float64)
         c = None if coeff is None else np.ascontiguousarray(coeff, dtype=np.float64)
         om = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)
@@ -140,7 +143,7 @@ class Context:
         mesh = Mesh(dim, n_cells, _dptr(v))
         prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c))
         opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, smoother_kind, _dptr(om), restart, rtol,
-                       max_it)
+                       max_it, outer_apply)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -159,6 +162,8 @@ class Context:
         self.pde = pde
 
     def __del__(self):
+        for net in list(getattr(self, "_nets", ())):
+            net.close()
         if getattr(self, "h", None):
             self.lib.stmg_destroy(self.h)
             self.h = None
@@ -211,6 +216,14 @@ class Context:
     def apply(self, x, y, level=0):
         self._vec(x, level); self._vec(y, level)
         self._check(self.lib.stmg_apply(self.h, level, self._prec(x), _ptr(x), _ptr(y)))
+
+    def apply_df(self, x, y):
+        """y (FP64) = S x (FP32) on level 0 in double-float arithmetic (outer_apply = DF32)."""
+        import torch
+        self._vec(x, 0); self._vec(y, 0)
+        if x.dtype != torch.float32 or y.dtype != torch.float64:
+            raise TypeError("apply_df takes a float32 x and a float64 y")
+        self._check(self.lib.stmg_apply(self.h, 0, DF32, _ptr(x), _ptr(y)))
 
     def residual(self, f, u, r, level=0):
         for t in (f, u, r):
@@ -305,6 +318,7 @@ class Net:
         h = ctypes.c_void_p()
         ctx._check(self.lib.stmg_net_create(ctypes.byref(h), ctx.h, self.L, ch, _dptr(w), _dptr(b), _dptr(sc)))
         self.h = h
+        ctx._nets.add(self)
         self._nw, self._nb = w.size, b.size
 
     def close(self):

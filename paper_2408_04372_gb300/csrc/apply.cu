@@ -1,335 +1,17 @@
-// Matrix-free space-time operator y (+)= sign * (TA (x) A_h + TM (x) M_h) x   (Section 3.1).
-// TA must be diagonal: it is M_tau, diagonal for the Lagrange time bases at quadrature
-// nodes of dG(k) and cGP(k) (the host checks this at set-up).
-//
-// One group of n^(dim-1) threads per cell ("pencil" threads, one per (x,y) node
-// column in 3D, one per x node line in 2D), several cells per CTA.  Per cell and
-// time DoF the pencil threads do the sum-factorised interpolation to the Gauss
-// points (B), collocation derivatives there (D), the space-time mixing with the
-// two N_t x N_t time matrices and the metric (rho w |J| J^-1 J^-T) at each point,
-// then the transposed sweeps (D^T, B^T).  The last direction runs in registers,
-// the others through shared memory.  Results go to global memory with atomic
-// adds on unconstrained rows; the caller initialises the output (identity on
-// constrained rows, 0 or the right-hand side elsewhere).
-#include "common.cuh"
-#include "kernels.h"
+// Matrix-free space-time operator y (+)= sign * (TA (x) A_h + TM (x) M_h) x   (Section 3.1):
+// FP32 and FP64 instances of the kernels in apply_kernels.cuh, and the row initialisation.
+#include "apply_kernels.cuh"
 
 namespace stmg {
 
 namespace {
 
-template <int N> constexpr int cells_per_block(int dim) {
-  return dim == 3 ? (N == 2 ? 32 : N == 3 ? 14 : N == 4 ? 8 : 5) : (N == 2 ? 64 : N == 3 ? 42 : N == 4 ? 32 : 25);
-}
-
-template <int N, int NT, typename T, int CPB>
-__global__ void __launch_bounds__(CPB * N * N)
-apply3d_kernel(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ geo, GridDesc g,
-               OpTab<T> tab, int mask_input) {
-  constexpr int N2 = N * N, N3 = N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
-  const int slot = threadIdx.x / N2;
-  const int lid = threadIdx.x - slot * N2;
-  const int i = lid % N, j = lid / N;
-  const int64_t cell = (int64_t)blockIdx.x * CPB + slot;
-  const bool active = cell < g.n_cells;
-  T* s0 = smem + (size_t)slot * 3 * NT * N3;
-  T* s1 = s0 + NT * N3;
-  T* s2 = s1 + NT * N3;
-  auto I4 = [](int t, int c, int b, int a) { return ((t * N + c) * N + b) * N + a; };
-
-  const int64_t cc = active ? cell : 0;
-  const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N), cz = (int)(cc / ((int64_t)g.N * g.N));
-  const int gx = cx * g.p + i, gy = cy * g.p + j;
-  const bool bxy = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
-
-  // gather + interpolation in z (registers)
-  {
-    T xcol[NT][N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int gz = cz * g.p + k;
-      const bool bnd = bxy || on_boundary(gz, g.nn1);
-      const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
-#pragma unroll
-      for (int t = 0; t < NT; ++t)
-        xcol[t][k] = (active && !(mask_input && bnd)) ? x[t * g.n_nodes + node] : T(0);
-    }
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        T v = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) v += tab.B[q][k] * xcol[t][k];
-        s0[I4(t, q, j, i)] = v;
-      }
-  }
-  __syncthreads();
-  // interpolation in y: thread (i, qy = j)
-#pragma unroll
-  for (int t = 0; t < NT; ++t)
-#pragma unroll
-    for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
-#pragma unroll
-      for (int b = 0; b < N; ++b) v += tab.B[j][b] * s0[I4(t, qz, b, i)];
-      s1[I4(t, qz, j, i)] = v;
-    }
-  __syncthreads();
-  // interpolation in x: thread (qx = i, qy = j); values at the column of Gauss points in registers
-  T u[NT][N];
-#pragma unroll
-  for (int t = 0; t < NT; ++t)
-#pragma unroll
-    for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[i][a] * s1[I4(t, qz, j, a)];
-      u[t][qz] = v;
-      s0[I4(t, qz, j, i)] = v;
-    }
-  __syncthreads();
-  // derivatives, time mixing and metric at each Gauss point of the column
-  T fz[NT][N], val[NT][N];
-  const T* gc = geo + cc * 7 * N3;
-#pragma unroll
-  for (int qz = 0; qz < N; ++qz) {
-    T ux[NT], uy[NT], uz[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        a0 += tab.D[i][a] * s0[I4(t, qz, j, a)];
-        a1 += tab.D[j][a] * s0[I4(t, qz, a, i)];
-        a2 += tab.D[qz][a] * u[t][a];
-      }
-      ux[t] = a0; uy[t] = a1; uz[t] = a2;
-    }
-    const int q = i + N * (j + N * qz);
-    const T G00 = gc[0 * N3 + q], G01 = gc[1 * N3 + q], G02 = gc[2 * N3 + q];
-    const T G11 = gc[3 * N3 + q], G12 = gc[4 * N3 + q], G22 = gc[5 * N3 + q];
-    const T m = gc[6 * N3 + q];
-#pragma unroll
-    for (int it = 0; it < NT; ++it) {
-      // TA = M_tau is diagonal (Lagrange time basis at the quadrature nodes): no mixing of gradients
-      const T ta = tab.TA[it][it];
-      const T gx_ = ta * ux[it], gy_ = ta * uy[it], gz_ = ta * uz[it];
-      T v = 0;
-#pragma unroll
-      for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qz];
-      s1[I4(it, qz, j, i)] = G00 * gx_ + G01 * gy_ + G02 * gz_;
-      s2[I4(it, qz, j, i)] = G01 * gx_ + G11 * gy_ + G12 * gz_;
-      fz[it][qz] = G02 * gx_ + G12 * gy_ + G22 * gz_;
-      val[it][qz] = m * v;
-    }
-  }
-  __syncthreads();
-  // transposed derivatives: test-function contributions at each Gauss point
-#pragma unroll
-  for (int it = 0; it < NT; ++it)
-#pragma unroll
-    for (int qz = 0; qz < N; ++qz) {
-      T v = val[it][qz];
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        v += tab.D[a][i] * s1[I4(it, qz, j, a)];
-        v += tab.D[a][j] * s2[I4(it, qz, a, i)];
-        v += tab.D[a][qz] * fz[it][a];
-      }
-      u[it][qz] = v;
-    }
-  // s0 was last read before the previous barrier
-#pragma unroll
-  for (int it = 0; it < NT; ++it)
-#pragma unroll
-    for (int qz = 0; qz < N; ++qz) s0[I4(it, qz, j, i)] = u[it][qz];
-  __syncthreads();
-  // B^T in x: thread (node i, qy = j)
-#pragma unroll
-  for (int it = 0; it < NT; ++it)
-#pragma unroll
-    for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[a][i] * s0[I4(it, qz, j, a)];
-      s1[I4(it, qz, j, i)] = v;
-    }
-  __syncthreads();
-  // B^T in y and z, scatter
-#pragma unroll
-  for (int it = 0; it < NT; ++it) {
-    T r[N];
-#pragma unroll
-    for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
-#pragma unroll
-      for (int b = 0; b < N; ++b) v += tab.B[b][j] * s1[I4(it, qz, b, i)];
-      r[qz] = v;
-    }
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      T v = 0;
-#pragma unroll
-      for (int qz = 0; qz < N; ++qz) v += tab.B[qz][k] * r[qz];
-      const int gz = cz * g.p + k;
-      if (active && !bxy && !on_boundary(gz, g.nn1)) {
-        const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
-        atomicAdd(y + it * g.n_nodes + node, tab.sign * v);
-      }
-    }
-  }
-}
-
-template <int N, int NT, typename T, int CPB>
-__global__ void __launch_bounds__(CPB * N)
-apply2d_kernel(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ geo, GridDesc g,
-               OpTab<T> tab, int mask_input) {
-  constexpr int N2 = N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
-  const int slot = threadIdx.x / N;
-  const int i = threadIdx.x - slot * N;
-  const int64_t cell = (int64_t)blockIdx.x * CPB + slot;
-  const bool active = cell < g.n_cells;
-  T* s0 = smem + (size_t)slot * 2 * NT * N2;
-  T* s1 = s0 + NT * N2;
-  auto I3 = [](int t, int b, int a) { return (t * N + b) * N + a; };
-  const int64_t cc = active ? cell : 0;
-  const int cx = (int)(cc % g.N), cy = (int)(cc / g.N);
-  const int gx = cx * g.p + i;
-  const bool bx = on_boundary(gx, g.nn1);
-  {
-    T xcol[NT][N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int gy = cy * g.p + k;
-      const bool bnd = bx || on_boundary(gy, g.nn1);
-      const int64_t node = gx + (int64_t)g.nn1 * gy;
-#pragma unroll
-      for (int t = 0; t < NT; ++t)
-        xcol[t][k] = (active && !(mask_input && bnd)) ? x[t * g.n_nodes + node] : T(0);
-    }
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        T v = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) v += tab.B[q][k] * xcol[t][k];
-        s0[I3(t, q, i)] = v;
-      }
-  }
-  __syncthreads();
-  T u[NT][N];
-#pragma unroll
-  for (int t = 0; t < NT; ++t)
-#pragma unroll
-    for (int qy = 0; qy < N; ++qy) {
-      T v = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[i][a] * s0[I3(t, qy, a)];
-      u[t][qy] = v;
-      s1[I3(t, qy, i)] = v;
-    }
-  __syncthreads();
-  T fy[NT][N], val[NT][N];
-  const T* gc = geo + cc * 4 * N2;
-#pragma unroll
-  for (int qy = 0; qy < N; ++qy) {
-    T ux[NT], uy[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      T a0 = 0, a1 = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        a0 += tab.D[i][a] * s1[I3(t, qy, a)];
-        a1 += tab.D[qy][a] * u[t][a];
-      }
-      ux[t] = a0; uy[t] = a1;
-    }
-    const int q = i + N * qy;
-    const T G00 = gc[0 * N2 + q], G01 = gc[1 * N2 + q], G11 = gc[2 * N2 + q], m = gc[3 * N2 + q];
-#pragma unroll
-    for (int it = 0; it < NT; ++it) {
-      const T ta = tab.TA[it][it];
-      const T gx_ = ta * ux[it], gy_ = ta * uy[it];
-      T v = 0;
-#pragma unroll
-      for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qy];
-      s0[I3(it, qy, i)] = G00 * gx_ + G01 * gy_;
-      fy[it][qy] = G01 * gx_ + G11 * gy_;
-      val[it][qy] = m * v;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int it = 0; it < NT; ++it)
-#pragma unroll
-    for (int qy = 0; qy < N; ++qy) {
-      T v = val[it][qy];
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        v += tab.D[a][i] * s0[I3(it, qy, a)];
-        v += tab.D[a][qy] * fy[it][a];
-      }
-      u[it][qy] = v;
-    }
-#pragma unroll
-  for (int it = 0; it < NT; ++it)
-#pragma unroll
-    for (int qy = 0; qy < N; ++qy) s1[I3(it, qy, i)] = u[it][qy];
-  __syncthreads();
-#pragma unroll
-  for (int it = 0; it < NT; ++it) {
-    T r[N];
-#pragma unroll
-    for (int qy = 0; qy < N; ++qy) {
-      T v = 0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[a][i] * s1[I3(it, qy, a)];
-      r[qy] = v;
-    }
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      T v = 0;
-#pragma unroll
-      for (int qy = 0; qy < N; ++qy) v += tab.B[qy][k] * r[qy];
-      const int gy = cy * g.p + k;
-      if (active && !bx && !on_boundary(gy, g.nn1))
-        atomicAdd(y + it * g.n_nodes + gx + (int64_t)g.nn1 * gy, tab.sign * v);
-    }
-  }
-}
-
-template <int DIM, int N, int NT, typename T>
-cudaError_t launch_apply_t(const T* x, T* y, const T* geo, const GridDesc& g, const OpTab<T>& tab,
-                           int mask_input, cudaStream_t s) {
-  constexpr int CPB = cells_per_block<N>(DIM);
-  const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
-  if constexpr (DIM == 3) {
-    const size_t smem = (size_t)CPB * 3 * NT * N * N * N * sizeof(T);
-    auto k = apply3d_kernel<N, NT, T, CPB>;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
-    k<<<(unsigned)blocks, CPB * N * N, smem, s>>>(x, y, geo, g, tab, mask_input);
-  } else {
-    const size_t smem = (size_t)CPB * 2 * NT * N * N * sizeof(T);
-    auto k = apply2d_kernel<N, NT, T, CPB>;
-    k<<<(unsigned)blocks, CPB * N, smem, s>>>(x, y, geo, g, tab, mask_input);
-  }
-  return cudaGetLastError();
-}
+using apply_detail::launch_apply_t;
 
 // init_apply: y = 0 on unconstrained rows, y = x on constrained rows (identity).
 // init_residual: r = f on unconstrained rows, r = f - x on constrained rows.
-template <typename T>
-__global__ void init_rows_kernel(T* __restrict__ y, const T* __restrict__ f, const T* __restrict__ x,
+template <typename T, typename TX = T>
+__global__ void init_rows_kernel(T* __restrict__ y, const T* __restrict__ f, const TX* __restrict__ x,
                                  GridDesc g, int nt, int mode) {
   const int64_t total = g.n_nodes * nt;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -345,8 +27,8 @@ __global__ void init_rows_kernel(T* __restrict__ y, const T* __restrict__ f, con
       bnd = bnd || on_boundary((int)rest, g.nn1);
     }
     T v;
-    if (mode == 0) v = bnd ? x[idx] : T(0);
-    else if (mode == 1) v = bnd ? f[idx] - x[idx] : f[idx];
+    if (mode == 0) v = bnd ? (T)x[idx] : T(0);
+    else if (mode == 1) v = bnd ? f[idx] - (T)x[idx] : f[idx];
     else v = T(0);
     y[idx] = v;
   }
@@ -355,7 +37,7 @@ __global__ void init_rows_kernel(T* __restrict__ y, const T* __restrict__ f, con
 }  // namespace
 
 #define STMG_APPLY_CASE(DIM, N, NT)                                              \
-  if (dim == DIM && n == N && nt == NT) return launch_apply_t<DIM, N, NT, T>(x, y, geo, g, tab, mask_input, s);
+  if (dim == DIM && n == N && nt == NT) return launch_apply_t<DIM, N, NT>(x, y, geo, g, tab, mask_input, s);
 
 template <typename T>
 cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo, const GridDesc& g,
@@ -378,6 +60,15 @@ cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, in
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
   init_rows_kernel<T><<<blocks, 256, 0, s>>>(y, f, x, g, nt, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_rows_f2d(double* y, const float* x, const GridDesc& g, int nt, cudaStream_t s) {
+  const int64_t total = g.n_nodes * nt;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  init_rows_kernel<double, float><<<blocks, 256, 0, s>>>(y, nullptr, x, g, nt, 0);
   return cudaGetLastError();
 }
 

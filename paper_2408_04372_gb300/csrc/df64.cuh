@@ -1,0 +1,65 @@
+// Double-float arithmetic on the FP32 pipe: a value is the unevaluated sum hi + lo of two
+// floats (about 44 significand bits).  GB300 issues FP32 at 64x its FP64 rate, so the
+// FP64-accuracy operator apply of the outer Krylov method runs in this arithmetic.
+//
+// Building blocks are the error-free transformations of Knuth (TwoSum: a + b = s + e
+// exactly, six additions) and of the FMA (TwoProd: a * b = p + e exactly), with Dekker's
+// Fast2Sum (|s| >= |e|) to renormalise.  A product is left unnormalised (its low part is
+// at most about 2^-23 of its high part); every sum is renormalised.  Relative error per
+// operation is about 2^-44 of the operands' magnitudes.  All roundings are explicit
+// (__fadd_rn, __fmul_rn, __fmaf_rn): the compiler must not merge a product into a sum
+// here, which would break the exactness of TwoSum and TwoProd.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace stmg {
+
+struct __align__(8) df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr df64(float h) : hi(h), lo(0.0f) {}
+};
+
+// Nearest double-float to x (host, for tables and geometry).
+inline df64 df_split(double x) {
+  const float h = (float)x;
+  return df64(h, (float)(x - (double)h));
+}
+
+__device__ __forceinline__ df64 df_add(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return df64(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df64(p, e);
+}
+
+__device__ __forceinline__ df64 df_mul(df64 a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return df64(p, e);
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) { return df_add(a, b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ df64 operator*(df64 a, float b) { return df_mul(a, b); }
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) {
+  a = df_add(a, b);
+  return a;
+}
+
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace stmg

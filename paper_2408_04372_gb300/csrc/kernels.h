@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace stmg {
 
@@ -13,14 +14,21 @@ namespace stmg {
 template <typename T>
 cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo, const GridDesc& g,
                          const OpTab<T>& tab, int mask_input, cudaStream_t s);
+// Same operator in double-float arithmetic (df64.cuh) for an FP32 input vector, accumulated into
+// an FP64 output: the FGMRES apply on V-cycle outputs, which are exact in FP32.
+cudaError_t launch_apply_df(int dim, int n, int nt, const float* x, double* y, const df64* geo, const GridDesc& g,
+                            const OpTab<df64>& tab, int mask_input, cudaStream_t s);
+// y = constrained ? x : 0 for an FP32 x and FP64 y (initialisation for launch_apply_df)
+cudaError_t launch_init_rows_f2d(double* y, const float* x, const GridDesc& g, int nt, cudaStream_t s);
 // mode 0: y = constrained ? x : 0 ; mode 1: y = constrained ? f - x : f ; mode 2: y = 0
 template <typename T>
 cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, int nt, int mode, cudaStream_t s);
 
 // ---- geometry (setup.cu) ----
-// geo64 [cell][7 or 4][nq^dim]: rho w |J| J^-1 J^-T (upper triangle) and w |J|
+// geo64 [cell][7 or 4][nq^dim]: rho w |J| J^-1 J^-T (upper triangle) and w |J|; geo32 the same in
+// FP32, geodf (may be NULL) as double-float pairs
 cudaError_t launch_geometry(const GridDesc& g, const double* vertices, const double* rho_qp, const double* xq,
-                            const double* wq, double* geo64, float* geo32, cudaStream_t s);
+                            const double* wq, double* geo64, float* geo32, df64* geodf, cudaStream_t s);
 
 // ---- additive Schwarz (asm.cu) ----
 struct LocalTab {        // 1D tables of the nodal basis at Gauss points (setup in FP64)
@@ -78,10 +86,15 @@ template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s);
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64_t n, cudaStream_t s);
-// out[j] = V_j . w (j < nv, V_j = V0 + j * stride), plus out[nv] = w.w if with_norm; deterministic
-// two-stage reduction through `partial` (nblocks x (nv + 1) scratch)
-cudaError_t launch_multidot(const double* V0, int64_t stride, int nv, const double* w, int64_t n, int with_norm,
-                            double* partial, int nblocks, double* out, cudaStream_t s);
+// One classical Gram-Schmidt pass over V_0..V_{nv-1} (nv <= 64), single launch, bit-reproducible:
+// optionally w -= sum_j c[j] V_j, then s_j = V_j . w and/or s_nv = w . w; fin 0 writes s to out,
+// fin 1 the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = ||w||, out[nv+1] = 1/||w||.
+// partial: (K+1) x cgs_blocks() doubles; counter: one zero-initialised unsigned int per stream,
+// left at zero on return.
+cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
+                            int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
+                            double* out, cudaStream_t s);
+int cgs_blocks();
 // w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride)
 cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,
                               int64_t n, cudaStream_t s);
@@ -93,6 +106,5 @@ template <typename T>
 cudaError_t launch_coarse_solve(const T* f, T* u, const T* inv, const int64_t* map, int n, int64_t total,
                                 cudaStream_t s);
 cudaError_t launch_zero_constrained(double* y, const GridDesc& g, int nt, cudaStream_t s);
-int multidot_blocks();
 
 }  // namespace stmg

@@ -14,7 +14,7 @@ namespace {
 
 __global__ void geometry_kernel(GridDesc g, const double* __restrict__ vert, const double* __restrict__ rho_qp,
                                 const double* __restrict__ xq, const double* __restrict__ wq, int nq,
-                                double* __restrict__ geo64, float* __restrict__ geo32) {
+                                double* __restrict__ geo64, float* __restrict__ geo32, df64* __restrict__ geodf) {
   const int dim = g.dim;
   const int nqd = dim == 3 ? nq * nq * nq : nq * nq;
   const int ncomp = dim == 3 ? 7 : 4;
@@ -83,6 +83,10 @@ __global__ void geometry_kernel(GridDesc g, const double* __restrict__ vert, con
       const int64_t o = (cell * ncomp + c) * nqd + q;
       geo64[o] = out[c];
       geo32[o] = (float)out[c];
+      if (geodf) {
+        const float h = (float)out[c];
+        geodf[o] = df64(h, (float)(out[c] - (double)h));
+      }
     }
   }
 }
@@ -90,11 +94,11 @@ __global__ void geometry_kernel(GridDesc g, const double* __restrict__ vert, con
 }  // namespace
 
 cudaError_t launch_geometry(const GridDesc& g, const double* vertices, const double* rho_qp, const double* xq,
-                            const double* wq, double* geo64, float* geo32, cudaStream_t s) {
+                            const double* wq, double* geo64, float* geo32, df64* geodf, cudaStream_t s) {
   const int nq = g.p + 1;
   const int64_t total = g.n_cells * (g.dim == 3 ? nq * nq * nq : nq * nq);
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
-  geometry_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(g, vertices, rho_qp, xq, wq, nq, geo64, geo32);
+  geometry_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(g, vertices, rho_qp, xq, wq, nq, geo64, geo32, geodf);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@ struct Level {
   std::vector<double> rho_qp;     // host cells x (p+1)^dim
   double* geo64 = nullptr;
   float* geo32 = nullptr;
+  df64* geodf = nullptr;         // finest level only, when the outer apply runs in double-float
+  OpTab<df64> tabdf{};
   SlabCoeffs sc;
   OpTab<double> tab64{};
   OpTab<float> tab32{};
@@ -72,7 +74,8 @@ struct stmg_ctx {
   int nvec = 0;
   double* V = nullptr;   // (nvec) vectors
   double* Z = nullptr;   // (m) vectors
-  double* partial = nullptr;
+  double* partial = nullptr;        // per-block partial sums of the Gram-Schmidt passes
+  unsigned int* counter = nullptr;  // arrival counter of those passes (zero between launches)
   double* dsm = nullptr;  // device scalars [0..nvec+8) h1, [128..) h2, [256..) outputs
   double* hsm = nullptr;  // pinned host mirror
   double* tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -84,7 +87,15 @@ struct stmg_ctx {
   std::vector<int64_t> iter_graph_kernels;
   bool warmed32 = false, warmed64 = false;
   int64_t launches = 0;  // kernels issued by this context (graph replays count their kernel nodes)
+  std::vector<stmg_net*> nets;  // networks bound to this context; detached when it is destroyed
+  bool outer_df = false;        // FGMRES apply on V-cycle outputs in double-float (FP32 V-cycle only)
 };
+
+// A network outliving its context keeps only its own device memory; every later call on it
+// except stmg_net_destroy returns STMG_ERR_INVALID_ARG.
+extern "C" {
+static void net_detach(stmg_net* net);
+}
 
 namespace {
 
@@ -159,6 +170,13 @@ void fill_tables(Level& L) {
     for (int b = 0; b < kMaxNT; ++b) { f.TA[a][b] = (float)t.TA[a][b]; f.TM[a][b] = (float)t.TM[a][b]; }
   f.sign = 1.0f;
   L.tab32 = f;
+  OpTab<df64> d{};
+  for (int a = 0; a < kMaxN; ++a)
+    for (int b = 0; b < kMaxN; ++b) { d.B[a][b] = df_split(t.B[a][b]); d.D[a][b] = df_split(t.D[a][b]); }
+  for (int a = 0; a < kMaxNT; ++a)
+    for (int b = 0; b < kMaxNT; ++b) { d.TA[a][b] = df_split(t.TA[a][b]); d.TM[a][b] = df_split(t.TM[a][b]); }
+  d.sign = df64(1.0f);
+  L.tabdf = d;
 }
 
 template <typename T> OpTab<T>& tab_of(Level& L);
@@ -197,6 +215,17 @@ stmg_status op_apply(stmg_ctx* ctx, Level& L, const T* x, T* y) {
   OpTab<T> t = tab_of<T>(L);
   t.sign = T(1);
   CK(launch_apply<T>(L.dim, L.n, L.nt, x, y, geo_of<T>(L), L.g, t, 1, ctx->stream));
+  return STMG_OK;
+}
+
+// y = S x for an FP32 x, in double-float arithmetic, FP64 y (identity on constrained rows)
+stmg_status op_apply_df(stmg_ctx* ctx, Level& L, const float* x, double* y) {
+  if (!L.geodf) { ctx->err = "no double-float geometry on this level"; return STMG_ERR_UNSUPPORTED; }
+  CK(launch_init_rows_f2d(y, x, L.g, L.nt, ctx->stream));
+  ctx->launches += 2;
+  OpTab<df64> t = L.tabdf;
+  t.sign = df64(1.0f);
+  CK(launch_apply_df(L.dim, L.n, L.nt, x, y, L.geodf, L.g, t, 1, ctx->stream));
   return STMG_OK;
 }
 
@@ -387,35 +416,25 @@ bool node_constrained(const Level& L, int64_t node) {
   return rest == 0 || rest == nn1 - 1;
 }
 
-// device multi-dot helper: out[0..nv) = V_j . w (+ w.w at nv), V_j = V0 + j * n
-stmg_status dots(stmg_ctx* ctx, const double* V0, int nv, const double* w, int64_t n, int with_norm, double* out) {
-  CK(launch_multidot(V0, n, nv, w, n, with_norm, ctx->partial, multidot_blocks(), out, ctx->stream));
+// out[0] = x . x (device), one launch
+stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
+  CK(launch_cgs_pass(nullptr, n, 0, const_cast<double*>(x), n, nullptr, 0, 0, 1, nullptr, 0, ctx->partial,
+                     ctx->counter, out, ctx->stream));
+  ctx->launches += 1;
   return STMG_OK;
 }
 
-__global__ void finalize_arnoldi_kernel(const double* h1, const double* h2, int nv, const double* nrm2, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int j = 0; j < nv; ++j) out[j] = h1[j] + h2[j];
-    const double hn = sqrt(fmax(nrm2[0], 0.0));
-    out[nv] = hn;
-    out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-  }
-}
-
-// enqueue part: no host synchronisation (capturable)
+// enqueue part: no host synchronisation (capturable).  Classical Gram-Schmidt twice in three
+// fused passes over the basis: h1 = V^T w ; w -= V h1, h2 = V^T w ; w -= V h2, ||w|| and the
+// column h1 + h2 ; then w /= ||w||.
 stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int nv, double* w, int64_t n) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
-  double* d_n = ctx->dsm + 256;
   double* d_out = ctx->dsm + 384;
-  CKS(dots(ctx, V0, nv, w, n, 0, d_h1));
-  CK(launch_multi_axpy(w, V0, n, d_h1, nv, -1.0, n, ctx->stream));
-  CKS(dots(ctx, V0, nv, w, n, 0, d_h2));
-  CK(launch_multi_axpy(w, V0, n, d_h2, nv, -1.0, n, ctx->stream));
-  CKS(dots(ctx, nullptr, 0, w, n, 1, d_n));
-  finalize_arnoldi_kernel<<<1, 1, 0, ctx->stream>>>(d_h1, d_h2, nv, d_n, d_out);
-  ctx->launches += 10;
-  CK(cudaGetLastError());
+  CK(launch_cgs_pass(V0, n, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream));
+  CK(launch_cgs_pass(V0, n, nv, w, n, d_h1, 1, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream));
+  CK(launch_cgs_pass(V0, n, nv, w, n, d_h2, 1, 0, 1, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream));
+  ctx->launches += 4;
   CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream));
   CK(cudaMemcpyAsync(ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
   return STMG_OK;
@@ -711,6 +730,11 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (!(o.rtol > 0.0)) o.rtol = 1e-8;
   if (o.max_it <= 0) o.max_it = 200;
   if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
+  if (o.outer_apply == 0) o.outer_apply = o.vcycle_precision == STMG_FP32 ? STMG_DF32 : STMG_FP64;
+  if (o.outer_apply != STMG_FP64 && o.outer_apply != STMG_DF32) return invalid(ctx, "outer_apply must be FP64 or DF32");
+  if (o.outer_apply == STMG_DF32 && o.vcycle_precision != STMG_FP32)
+    return invalid(ctx, "the double-float outer apply needs the FP32 V-cycle");
+  ctx->outer_df = o.outer_apply == STMG_DF32;
   if (o.inverse_precision < STMG_FP64 || o.inverse_precision > STMG_BF16) return invalid(ctx, "inverse_precision out of range");
   const int inv_prec = o.inverse_precision == STMG_FP64 ? 0 : o.inverse_precision == STMG_FP32 ? 1 : 2;
   ctx->opt = o;
@@ -812,7 +836,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     const int ncomp = dim == 3 ? 7 : 4;
     CKS(dev_alloc(ctx, &L.geo64, (size_t)L.g.n_cells * ncomp * nqd));
     CKS(dev_alloc(ctx, &L.geo32, (size_t)L.g.n_cells * ncomp * nqd));
-    CK(launch_geometry(L.g, dvert, drho, dxq, dwq, L.geo64, L.geo32, ctx->stream));
+    if (li == 0 && ctx->outer_df) CKS(dev_alloc(ctx, &L.geodf, (size_t)L.g.n_cells * ncomp * nqd));
+    CK(launch_geometry(L.g, dvert, drho, dxq, dwq, L.geo64, L.geo32, L.geodf, ctx->stream));
     const int64_t sz = L.size();
     CKS(dev_alloc(ctx, &L.f64, sz)); CKS(dev_alloc(ctx, &L.u64, sz)); CKS(dev_alloc(ctx, &L.r64, sz));
     CKS(dev_alloc(ctx, &L.f32, sz)); CKS(dev_alloc(ctx, &L.u32, sz)); CKS(dev_alloc(ctx, &L.r32, sz));
@@ -827,7 +852,9 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   ctx->nvec = std::max(ctx->m, 20) + 1;
   CKS(dev_alloc(ctx, &ctx->V, (size_t)ctx->nvec * n0));
   CKS(dev_alloc(ctx, &ctx->Z, (size_t)std::max(ctx->m, 1) * n0));
-  CKS(dev_alloc(ctx, &ctx->partial, (size_t)multidot_blocks() * 80));
+  CKS(dev_alloc(ctx, &ctx->partial, (size_t)cgs_blocks() * 80));
+  CKS(dev_alloc(ctx, &ctx->counter, 1));
+  CK(cudaMemsetAsync(ctx->counter, 0, sizeof(unsigned int), ctx->stream));
   CKS(dev_alloc(ctx, &ctx->dsm, 512));
   for (int i = 0; i < 6; ++i) CKS(dev_alloc(ctx, &ctx->tmp[i], ctx->levels[0].g.n_nodes));
   CKS(dev_alloc(ctx, &ctx->rhs_buf, n0));
@@ -918,13 +945,16 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
     else CKS(run_vcycle<float>(ctx));
     CK(launch_convert<float, double>(L.u32, z, n, ctx->stream));
     ctx->launches += 2;
+    // z_j is exact in FP32: the double-float apply reads the V-cycle output itself
+    if (ctx->outer_df) CKS(op_apply_df(ctx, L, L.u32, w));
+    else CKS(op_apply<double>(ctx, L, z, w));
   } else {
     CK(cudaMemcpyAsync(L.f64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     if (in_capture) CKS(vcycle_level<double>(ctx, 0));
     else CKS(run_vcycle<double>(ctx));
     CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CKS(op_apply<double>(ctx, L, z, w));
   }
-  CKS(op_apply<double>(ctx, L, z, w));
   return orthogonalise_enqueue(ctx, ctx->V, j + 1, w, n);
 }
 
@@ -965,8 +995,7 @@ stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
 }
 
 stmg_status norm2(stmg_ctx* ctx, const double* x, int64_t n, double& out) {
-  CKS(dots(ctx, nullptr, 0, x, n, 1, ctx->dsm + 448));
-  ctx->launches += 2;
+  CKS(dot_self(ctx, x, n, ctx->dsm + 448));
   CK(cudaMemcpyAsync(ctx->hsm + 448, ctx->dsm + 448, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   out = std::sqrt(std::max(ctx->hsm[448], 0.0));
@@ -1207,6 +1236,7 @@ stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_proble
 stmg_status stmg_destroy(stmg_ctx* ctx) {
   if (!ctx) return STMG_OK;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (stmg_net* net : ctx->nets) net_detach(net);
   for (auto g : ctx->iter_graphs)
     if (g) cudaGraphExecDestroy(g);
   if (ctx->graph32) cudaGraphExecDestroy(ctx->graph32);
@@ -1294,6 +1324,11 @@ stmg_status stmg_qpoint_coords(const stmg_ctx* ctx, int level, double* xyz) {
 
 stmg_status stmg_apply(stmg_ctx* ctx, int level, int precision, const void* x, void* y) {
   StreamJoin join_(ctx);
+  if (ctx && precision == STMG_DF32) {
+    if (level != 0 || !ctx->levels[0].geodf)
+      return invalid(ctx, "DF32 applies exist on level 0 of a context with outer_apply = DF32");
+    return op_apply_df(ctx, ctx->levels[0], (const float*)x, (double*)y);
+  }
   CKS(check_level(ctx, level, precision));
   Level& L = ctx->levels[level];
   if (precision == STMG_FP64) return op_apply<double>(ctx, L, (const double*)x, (double*)y);
@@ -1423,11 +1458,13 @@ stmg_status stmg_smooth_noalloc(stmg_ctx* ctx, int level, int precision, int swe
 
 // ------------------------------------------------------------------ learned initial guess
 struct stmg_net {
-  stmg_ctx* ctx = nullptr;
+  stmg_ctx* ctx = nullptr;  // null once the context has been destroyed
   NetDev d;
   std::vector<void*> allocs;
   std::vector<int> ch;
 };
+
+static void net_detach(stmg_net* net) { net->ctx = nullptr; }
 
 static stmg_status net_alloc(stmg_net* net, void** p, size_t bytes) {
   stmg_ctx* ctx = net->ctx;
@@ -1442,7 +1479,11 @@ static stmg_status net_alloc(stmg_net* net, void** p, size_t bytes) {
 
 stmg_status stmg_net_destroy(stmg_net* net) {
   if (!net) return STMG_OK;
-  if (net->ctx && net->ctx->stream) cudaStreamSynchronize(net->ctx->stream);
+  if (net->ctx) {
+    auto& v = net->ctx->nets;
+    v.erase(std::remove(v.begin(), v.end(), net), v.end());
+    if (net->ctx->stream) cudaStreamSynchronize(net->ctx->stream);
+  }  // a detached network has no work in flight: its context synchronised when it was destroyed
   for (void* p : net->allocs) cudaFree(p);
   delete net;
   return STMG_OK;
@@ -1511,12 +1552,13 @@ stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int
   if ((st = net_alloc(net, (void**)&d.loss, 8)) != STMG_OK) return fail(st);
   if (net_refresh_bf16(d, ctx->stream) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
     return fail(STMG_ERR_CUDA);
+  ctx->nets.push_back(net);
   *out = net;
   return STMG_OK;
 }
 
 stmg_status stmg_net_predict(stmg_net* net, const double* u_prev, const double* f, double* u_guess) {
-  if (!net || !u_prev || !f || !u_guess) return STMG_ERR_INVALID_ARG;
+  if (!net || !net->ctx || !u_prev || !f || !u_guess) return STMG_ERR_INVALID_ARG;
   stmg_ctx* ctx = net->ctx;
   StreamJoin join_(ctx);
   CK(net_forward(net->d, u_prev, f, ctx->stream));
@@ -1538,7 +1580,7 @@ static stmg_status net_fb(stmg_net* net, const double* u_prev, const double* f, 
 
 stmg_status stmg_net_train_step(stmg_net* net, const double* u_prev, const double* f, const double* u_target, double lr,
                                 double* loss) {
-  if (!net || !u_prev || !f || !u_target) return STMG_ERR_INVALID_ARG;
+  if (!net || !net->ctx || !u_prev || !f || !u_target) return STMG_ERR_INVALID_ARG;
   stmg_ctx* ctx = net->ctx;
   StreamJoin join_(ctx);
   CKS(net_fb(net, u_prev, f, u_target, loss));
@@ -1550,7 +1592,7 @@ stmg_status stmg_net_train_step(stmg_net* net, const double* u_prev, const doubl
 
 stmg_status stmg_net_gradients(stmg_net* net, const double* u_prev, const double* f, const double* u_target,
                                double* loss, double* grad_w, double* grad_b, double* out_host) {
-  if (!net || !u_prev || !f || !u_target) return STMG_ERR_INVALID_ARG;
+  if (!net || !net->ctx || !u_prev || !f || !u_target) return STMG_ERR_INVALID_ARG;
   stmg_ctx* ctx = net->ctx;
   StreamJoin join_(ctx);
   CKS(net_fb(net, u_prev, f, u_target, loss));
@@ -1581,7 +1623,7 @@ stmg_status stmg_net_gradients(stmg_net* net, const double* u_prev, const double
 }
 
 stmg_status stmg_net_weights(stmg_net* net, double* w, double* b) {
-  if (!net) return STMG_ERR_INVALID_ARG;
+  if (!net || !net->ctx) return STMG_ERR_INVALID_ARG;
   stmg_ctx* ctx = net->ctx;
   StreamJoin join_(ctx);
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1624,6 +1666,7 @@ stmg_status stmg_select_guess(stmg_ctx* ctx, const double* rhs, const double* ca
 stmg_status stmg_solve_slab_host_learned(stmg_ctx* ctx, stmg_net* net, const double* f, const double* u_prev,
                                          double* u, int* chosen, stmg_solve_stats* stats) {
   if (!ctx || !net || !f || !u_prev || !u) return STMG_ERR_INVALID_ARG;
+  if (net->ctx != ctx) return invalid(ctx, "network is bound to another context");
   if (ctx->pde != STMG_HEAT || ctx->scheme != STMG_DG) return invalid(ctx, "learned slab step supports heat dG");
   StreamJoin join_(ctx);
   Level& L = ctx->levels[0];
@@ -1663,7 +1706,10 @@ stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {
 }
 
 stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision, int reps, double* avg_ms) {
-  CKS(check_level(ctx, level, precision));
+  const bool df = precision == STMG_DF32;
+  if (df && (!ctx || kernel != STMG_KERNEL_APPLY || level != 0 || !ctx->levels[0].geodf))
+    return invalid(ctx, "DF32 timing exists for the level-0 apply of a context with outer_apply = DF32");
+  CKS(check_level(ctx, level, df ? STMG_FP64 : precision));
   if (reps < 1 || !avg_ms) return invalid(ctx, "reps must be >= 1");
   if (kernel != STMG_KERNEL_APPLY && kernel != STMG_KERNEL_ASM && kernel != STMG_KERNEL_VCYCLE)
     return invalid(ctx, "unknown kernel id");
@@ -1678,7 +1724,10 @@ stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision
       return run_vcycle<float>(ctx);
     }
     if (kernel == STMG_KERNEL_APPLY) {
-      if (precision == STMG_FP64) {
+      if (df) {
+        OpTab<df64> t = L.tabdf;
+        CK(launch_apply_df(L.dim, L.n, L.nt, L.u32, L.r64, L.geodf, L.g, t, 1, ctx->stream));
+      } else if (precision == STMG_FP64) {
         OpTab<double> t = L.tab64;
         CK(launch_apply<double>(L.dim, L.n, L.nt, L.u64, L.r64, L.geo64, L.g, t, 1, ctx->stream));
       } else {

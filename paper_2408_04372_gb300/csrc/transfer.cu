@@ -71,42 +71,56 @@ __host__ __device__ inline bool transfer_fused(int terms, int64_t n_out) {
   return terms <= 8 || (terms <= 27 && n_out < (int64_t)4 << 20);
 }
 
-// Fused form for narrow 1D stencils: every output node sums the tensor product of its three
-// 1D lists directly (width^dim terms), one launch instead of dim.
-template <typename T>
-__global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ out, int dim, int nt, int nin, int nout,
-                                    const int* __restrict__ idx, const double* __restrict__ w, int R, int accumulate,
+// Fused form for narrow 1D stencils: every output node sums the tensor product of its 1D
+// lists directly (R^DIM terms), one launch instead of DIM.  The list width R is a template
+// parameter: each thread reads its three lists first (padding entries become weight 0 on
+// index 0) and then issues all R^DIM input loads at once.
+template <typename T, int R, int DIM>
+__global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ out, int nt, int nin, int nout,
+                                    const int* __restrict__ idx, const double* __restrict__ w, int accumulate,
                                     SideJob<T> side) {
-  const int64_t per = dim == 3 ? (int64_t)nout * nout * nout : (int64_t)nout * nout;
-  const int64_t per_in = dim == 3 ? (int64_t)nin * nin * nin : (int64_t)nin * nin;
+  const int64_t per = DIM == 3 ? (int64_t)nout * nout * nout : (int64_t)nout * nout;
+  const int64_t per_in = DIM == 3 ? (int64_t)nin * nin * nin : (int64_t)nin * nin;
   const int64_t total = per * nt;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int t = (int)(e / per);
     int64_t r = e - (int64_t)t * per;
     const int x = (int)(r % nout);
     r /= nout;
-    const int y = dim == 3 ? (int)(r % nout) : (int)r;
-    const int z = dim == 3 ? (int)(r / nout) : 0;
+    const int y = DIM == 3 ? (int)(r % nout) : (int)r;
+    const int z = DIM == 3 ? (int)(r / nout) : 0;
+    int jx[R], jy[R], jz[R];
+    T wx[R], wy[R], wz[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int ix = __ldg(idx + x * R + k), iy = __ldg(idx + y * R + k);
+      jx[k] = ix < 0 ? 0 : ix;
+      wx[k] = ix < 0 ? T(0) : (T)__ldg(w + x * R + k);
+      jy[k] = iy < 0 ? 0 : iy;
+      wy[k] = iy < 0 ? T(0) : (T)__ldg(w + y * R + k);
+      if (DIM == 3) {
+        const int iz = __ldg(idx + z * R + k);
+        jz[k] = iz < 0 ? 0 : iz;
+        wz[k] = iz < 0 ? T(0) : (T)__ldg(w + z * R + k);
+      } else {
+        jz[k] = 0;
+        wz[k] = k == 0 ? T(1) : T(0);
+      }
+    }
     const T* src = in + (int64_t)t * per_in;
     T acc = 0;
-    const int Rz = dim == 3 ? R : 1;
-    for (int kz = 0; kz < Rz; ++kz) {
-      const int jz = dim == 3 ? idx[z * R + kz] : 0;
-      if (jz < 0) break;
-      const T wz = dim == 3 ? (T)w[z * R + kz] : T(1);
+#pragma unroll
+    for (int kz = 0; kz < (DIM == 3 ? R : 1); ++kz) {
+      T sy = 0;
+#pragma unroll
       for (int ky = 0; ky < R; ++ky) {
-        const int jy = idx[y * R + ky];
-        if (jy < 0) break;
-        const T wy = (T)w[y * R + ky];
-        const T* row = src + ((int64_t)jz * nin + jy) * nin;
+        const T* row = src + ((int64_t)jz[kz] * nin + jy[ky]) * nin;
         T sx = 0;
-        for (int kx = 0; kx < R; ++kx) {
-          const int jx = idx[x * R + kx];
-          if (jx < 0) break;
-          sx += (T)w[x * R + kx] * row[jx];
-        }
-        acc += wz * wy * sx;
+#pragma unroll
+        for (int kx = 0; kx < R; ++kx) sx += wx[kx] * row[jx[kx]];
+        sy += wy[ky] * sx;
       }
+      acc += wz[kz] * sy;
     }
     if (accumulate) out[e] += acc;
     else out[e] = acc;
@@ -122,8 +136,17 @@ cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, c
   auto blocks = [](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); };
   const int terms = dim == 3 ? R * R * R : R * R;
   const int64_t nout_total = (int64_t)nt * (dim == 3 ? (int64_t)nout * nout * nout : (int64_t)nout * nout);
-  if (transfer_fused(terms, nout_total)) {
-    gather_fused_kernel<T><<<blocks(nout_total), 256, 0, s>>>(in, out, dim, nt, nin, nout, idx, w, R, accumulate, side);
+  if (transfer_fused(terms, nout_total)) {  // R <= 3 in 3D, R <= 5 in 2D
+    const int nb = blocks(nout_total);
+#define STMG_FUSED(RR, DD) \
+  gather_fused_kernel<T, RR, DD><<<nb, 256, 0, s>>>(in, out, nt, nin, nout, idx, w, accumulate, side)
+    if (dim == 3) {
+      if (R == 1) STMG_FUSED(1, 3); else if (R == 2) STMG_FUSED(2, 3); else STMG_FUSED(3, 3);
+    } else {
+      if (R == 1) STMG_FUSED(1, 2); else if (R == 2) STMG_FUSED(2, 2); else if (R == 3) STMG_FUSED(3, 2);
+      else if (R == 4) STMG_FUSED(4, 2); else STMG_FUSED(5, 2);
+    }
+#undef STMG_FUSED
     return cudaGetLastError();
   }
   if (dim == 2) {

@@ -1,7 +1,6 @@
-// Vector kernels of the FP64 outer FGMRES and small helpers: conversions,
-// deterministic multi-dot products (two-stage reduction in a fixed order: per-block
-// partial sums in a scratch buffer, then one block per product),
-// multi-AXPY, time-only mixing of nodal blocks, the dense coarsest-level solve.
+// Vector kernels of the FP64 outer FGMRES and small helpers: conversions, the fused
+// classical Gram-Schmidt passes (deterministic single-launch reductions), multi-AXPY,
+// time-only mixing of nodal blocks, the dense coarsest-level solve.
 #include <algorithm>
 
 #include "common.cuh"
@@ -12,9 +11,8 @@ namespace stmg {
 namespace {
 
 constexpr int kMaxVec = 72;
-constexpr int kDotBlocks = 152 * 4;
-constexpr int kDotThreads = 256;
-constexpr int kChunk = 8;
+constexpr int kCgsThreads = 256;
+constexpr int kCgsBlocks = 152 * 4;
 
 inline int grid_blocks(int64_t total) {
   int64_t b = (total + 255) / 256;
@@ -38,65 +36,98 @@ __global__ void scale_by_device_kernel(double* __restrict__ x, const double* __r
     x[i] *= s;
 }
 
-__device__ inline double block_sum(double v, double* red) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+// One pass of classical Gram-Schmidt against V_0..V_{nv-1} (V_j = V0 + j * stride):
+//   sub : w -= sum_j c[j] V_j             (c on the device)
+//   dot : s_j = V_j . w, j < nv            (after the subtraction)
+//   norm: s_nv = w . w                     (after the subtraction)
+// Every block reduces a fixed contiguous slice; the last block to arrive sums the per-block
+// partials in block order, so the results do not depend on scheduling.  It then writes
+//   fin 0: out[j] = s_j (j < nv) and out[nv] = s_nv when norm is set;
+//   fin 1: the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = sqrt(s_nv), out[nv+1] = 1/out[nv].
+// One thread keeps the K values V_j[i] of its element in registers between the subtraction and
+// the dot products, so every basis vector is read once per pass.
+template <int K>
+__global__ void __launch_bounds__(kCgsThreads)
+cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
+                const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev, int fin,
+                double* __restrict__ partial, unsigned int* __restrict__ counter, double* __restrict__ out) {
+  __shared__ double red[kCgsThreads / 32][K + 1];
+  __shared__ double cs[K];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (sub && j < nv) ? c[j] : 0.0;
   __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;  // valid in thread 0
-}
-
-// stage 1: partial[j * nblocks + b] = sum over block b's fixed slice of V_j . w ; j = nv holds w . w
-__global__ void __launch_bounds__(kDotThreads)
-multidot_stage1(const double* __restrict__ V0, int64_t stride, int nv, const double* __restrict__ w, int64_t n,
-                int with_norm, double* __restrict__ partial) {
-  __shared__ double red[kDotThreads / 32][kChunk];
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = blockIdx.x * per, hi = std::min<int64_t>(n, lo + per);
-  const int ntot = nv + (with_norm ? 1 : 0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j0 = 0; j0 < ntot; j0 += kChunk) {
-    double acc[kChunk];
+  const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  double acc[K + 1];
 #pragma unroll
-    for (int c = 0; c < kChunk; ++c) acc[c] = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double wi = w[i];
+  for (int j = 0; j <= K; ++j) acc[j] = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kCgsThreads) {
+    double v[K];
 #pragma unroll
-      for (int c = 0; c < kChunk; ++c) {
-        const int j = j0 + c;
-        if (j < nv) acc[c] += __ldg(V0 + j * stride + i) * wi;
-        else if (j == nv && with_norm) acc[c] += wi * wi;
-      }
-    }
+    for (int j = 0; j < K; ++j) v[j] = j < nv ? __ldg(V0 + j * stride + i) : 0.0;
+    double wi = w[i];
+    if (sub) {
+      double sv = 0.0;
 #pragma unroll
-    for (int c = 0; c < kChunk; ++c) {
-      double v = acc[c];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) red[warp][c] = v;
+      for (int j = 0; j < K; ++j) sv += cs[j] * v[j];
+      wi -= sv;
+      w[i] = wi;
     }
-    __syncthreads();
-    if (threadIdx.x < kChunk && j0 + (int)threadIdx.x < ntot) {
-      double s = 0.0;
-      for (int wv = 0; wv < kDotThreads / 32; ++wv) s += red[wv][threadIdx.x];
-      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    if (dot) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc[j] += v[j] * wi;
     }
-    __syncthreads();
+    acc[K] += wi * wi;
   }
-}
-
-// stage 2: block j sums partial[j][0..nblocks) by a fixed-order tree
-__global__ void __launch_bounds__(kDotThreads)
-multidot_stage2(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
-  __shared__ double red[kDotThreads / 32];
-  const double* p = partial + (int64_t)blockIdx.x * nblocks;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += p[b];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) out[blockIdx.x] = s;
+  // block partials: slot j < nv (dot), slot K (norm)
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = acc[j];
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) red[warp][j] = x;
+    }
+  }
+  __syncthreads();
+  const int nb = gridDim.x;
+  for (int j = threadIdx.x; j <= K; j += blockDim.x) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = 0.0;
+      for (int wv = 0; wv < kCgsThreads / 32; ++wv) x += red[wv][j];
+      partial[(int64_t)j * nb + blockIdx.x] = x;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // fixed-order sums over blocks: warp w takes slots w, w + 8, ...
+  __shared__ double tot[K + 1];
+  for (int j = warp; j <= K; j += kCgsThreads / 32) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = 0.0;
+      for (int b = lane; b < nb; b += 32) x += __ldcg(partial + (int64_t)j * nb + b);
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) tot[j] = x;
+    }
+  }
+  __syncthreads();
+  if (fin == 0) {
+    for (int j = threadIdx.x; j < nv; j += blockDim.x)
+      if (dot) out[j] = tot[j];
+    if (norm && threadIdx.x == 0) out[nv] = tot[K];
+  } else {
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) out[j] = h_prev[j] + cs[j];
+    if (threadIdx.x == 0) {
+      const double hn = sqrt(fmax(tot[K], 0.0));
+      out[nv] = hn;
+      out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 __global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V0, int64_t stride,
@@ -158,7 +189,6 @@ __global__ void zero_constrained_kernel(double* __restrict__ y, GridDesc g, int 
 
 }  // namespace
 
-int multidot_blocks() { return kDotBlocks; }
 
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s) {
@@ -179,12 +209,21 @@ cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_multidot(const double* V0, int64_t stride, int nv, const double* w, int64_t n, int with_norm,
-                            double* partial, int nblocks, double* out, cudaStream_t s) {
-  if (nv > kMaxVec || nblocks < 1) return cudaErrorInvalidValue;
-  const int ntot = nv + (with_norm ? 1 : 0);
-  multidot_stage1<<<nblocks, kDotThreads, 0, s>>>(V0, stride, nv, w, n, with_norm, partial);
-  multidot_stage2<<<ntot, kDotThreads, 0, s>>>(partial, nblocks, out);
+int cgs_blocks() { return kCgsBlocks; }
+
+cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
+                            int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
+                            double* out, cudaStream_t s) {
+  if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+  // one wave: blocks per SM as the register use of each width allows (4, 4, 2, 1, 1)
+#define STMG_CGS(KK, BPS) \
+  cgs_pass_kernel<KK><<<152 * (BPS), kCgsThreads, 0, s>>>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter, out)
+  if (nv <= 4) STMG_CGS(4, 4);
+  else if (nv <= 8) STMG_CGS(8, 4);
+  else if (nv <= 16) STMG_CGS(16, 2);
+  else if (nv <= 32) STMG_CGS(32, 1);
+  else STMG_CGS(64, 1);
+#undef STMG_CGS
   return cudaGetLastError();
 }
 

@@ -2,7 +2,8 @@
 
 Tolerances: FP64 kernels 1e-10 relative (max-norm over the vector, scaled by its
 largest entry), FP32 kernels 2e-5 relative (float rounding of O(100) terms),
-solutions 1e-8 relative L2 after FGMRES to rtol 1e-12.
+double-float kernels 1e-11 relative (about 44 significand bits: 6e-14 per operation
+over O(100) operations), solutions 1e-8 relative L2 after FGMRES to rtol 1e-12.
 """
 import numpy as np
 import pytest
@@ -14,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
 TOL32 = 2e-5
+TOLDF = 1e-11
 
 
 def _rand(n, seed, bmask=None):
@@ -49,6 +51,22 @@ def test_apply_every_level(env, case):
         rd = torch.empty_like(fd)
         ctx.residual(fd, ud, rd, level=li)
         assert rel_err(rd.cpu().numpy(), f - ref) < TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_double_float_apply_on_fp32_vectors(env, case):
+    """The FGMRES apply on V-cycle outputs: FP32 input, double-float arithmetic, FP64 output."""
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H)
+    prob = H.levels[0].prob
+    for seed in (300, 301):
+        x32 = _rand(prob.n, seed).astype(np.float32)   # constrained entries nonzero: identity rows
+        ref = prob.S @ x32.astype(np.float64)
+        y = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        ctx.apply_df(torch.from_numpy(x32).cuda(), y)
+        assert rel_err(y.cpu().numpy(), ref) < TOLDF, case.name
     ctx.close()
 
 
@@ -131,13 +149,14 @@ def test_solve_matches_direct_solution(env, case):
     prob = H.levels[0].prob
     b = _rand(prob.n, 700, prob.bmask_full)
     xd = prob.solve(b).reshape(-1)
-    for prec in (stmg.FP64, stmg.FP32):
-        ctx = make_context(stmg, case, H, vcycle_precision=prec, rtol=1e-12, max_it=300)
+    # plain FP64; mixed with the double-float outer apply (default); mixed with the FP64 outer apply
+    for prec, outer in ((stmg.FP64, 0), (stmg.FP32, 0), (stmg.FP32, stmg.FP64)):
+        ctx = make_context(stmg, case, H, vcycle_precision=prec, rtol=1e-12, max_it=300, outer_apply=outer)
         u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
         st = ctx.solve(torch.from_numpy(b).cuda(), u)
         assert st["converged"] and st["rel_residual"] <= 1e-12
         err = np.linalg.norm(u.cpu().numpy() - xd) / np.linalg.norm(xd)
-        assert err < 1e-8, (case.name, prec, err, st)
+        assert err < 1e-8, (case.name, prec, outer, err, st)
         ctx.close()
 
 
