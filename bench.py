@@ -165,10 +165,11 @@ def run_kernel_only(args):
     torch.cuda.set_device(0)
     wl = workload(args.n_cells)
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
-                       vcycle_precision=stmg.FP32, omega=[0.2] * 16)
+                       vcycle_precision=stmg.FP32, inverse_precision=stmg.BF16, omega=[0.2] * 16)
     kind, prec = {"apply64": (stmg.KERNEL_APPLY, stmg.FP64), "apply32": (stmg.KERNEL_APPLY, stmg.FP32),
+                  "applydf": (stmg.KERNEL_APPLY, stmg.DF32),
                   "asm32": (stmg.KERNEL_ASM, stmg.FP32), "asm64": (stmg.KERNEL_ASM, stmg.FP64),
-                  "vcycle32": (stmg.KERNEL_VCYCLE, stmg.FP32)}[args.only_kernel]
+                  "vcycle32": (stmg.KERNEL_VCYCLE, stmg.FP32), "vcycle64": (stmg.KERNEL_VCYCLE, stmg.FP64)}[args.only_kernel]
     ms = ctx.time_kernel(kind, 0, prec, reps=args.steps)
     print(json.dumps({"kernel": args.only_kernel, "avg_launch_ms": ms, "workload": wl["name"]}))
     ctx.close()
@@ -625,7 +626,7 @@ def main():
     ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64"],
                     help="storage of the Schwarz inverses in the mixed solver")
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "asm32", "asm64", "vcycle32"],
+    ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     args = ap.parse_args()
     if args.only_kernel:

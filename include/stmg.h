@@ -49,7 +49,7 @@ typedef enum {
   STMG_ERR_OOM = 3,           /* device allocation failed */
   STMG_ERR_NOT_CONVERGED = 4, /* FGMRES hit max_it before rtol */
   STMG_ERR_BREAKDOWN = 5,     /* Krylov breakdown before convergence */
-  STMG_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  STMG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (reported by stmg_solve); destroy the context */
   STMG_ERR_NONFINITE = 7,     /* NaN/Inf met in a residual or preconditioner output */
   STMG_ERR_INTERNAL = 8,
   STMG_ERR_UNSUPPORTED = 9    /* valid request outside the compiled kernel set */

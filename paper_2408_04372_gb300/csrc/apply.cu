@@ -53,6 +53,22 @@ cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo,
   return cudaErrorInvalidValue;
 }
 
+#define STMG_MASS_CASE(DIM, N, NT)                                              \
+  if (dim == DIM && n == N && nt == NT) return launch_apply_t<DIM, N, NT, double, double, double, true>(x, y, geo, g, tab, 0, s);
+
+cudaError_t launch_mass_apply(int dim, int n, int nt, const double* x, double* y, const double* geo, const GridDesc& g,
+                              const OpTab<double>& tab, cudaStream_t s) {
+  STMG_MASS_CASE(3, 2, 1) STMG_MASS_CASE(3, 2, 2) STMG_MASS_CASE(3, 2, 3) STMG_MASS_CASE(3, 2, 4)
+  STMG_MASS_CASE(3, 3, 1) STMG_MASS_CASE(3, 3, 2) STMG_MASS_CASE(3, 3, 3) STMG_MASS_CASE(3, 3, 4)
+  STMG_MASS_CASE(3, 4, 1) STMG_MASS_CASE(3, 4, 2) STMG_MASS_CASE(3, 4, 3) STMG_MASS_CASE(3, 4, 4)
+  STMG_MASS_CASE(3, 5, 1) STMG_MASS_CASE(3, 5, 2) STMG_MASS_CASE(3, 5, 3) STMG_MASS_CASE(3, 5, 4)
+  STMG_MASS_CASE(2, 2, 1) STMG_MASS_CASE(2, 2, 2) STMG_MASS_CASE(2, 2, 3) STMG_MASS_CASE(2, 2, 4)
+  STMG_MASS_CASE(2, 3, 1) STMG_MASS_CASE(2, 3, 2) STMG_MASS_CASE(2, 3, 3) STMG_MASS_CASE(2, 3, 4)
+  STMG_MASS_CASE(2, 4, 1) STMG_MASS_CASE(2, 4, 2) STMG_MASS_CASE(2, 4, 3) STMG_MASS_CASE(2, 4, 4)
+  STMG_MASS_CASE(2, 5, 1) STMG_MASS_CASE(2, 5, 2) STMG_MASS_CASE(2, 5, 3) STMG_MASS_CASE(2, 5, 4)
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, int nt, int mode, cudaStream_t s) {
   const int64_t total = g.n_nodes * nt;

@@ -30,10 +30,12 @@ __device__ __forceinline__ void add_out(double* p, double v) { atomicAdd(p, v); 
 __device__ __forceinline__ void add_out(double* p, df64 v) { atomicAdd(p, df_to_double(v)); }
 
 // T: arithmetic (float, double or double-float), TI: input vector type, TO: output vector type.
-template <int N, int NT, typename T, int CPB, typename TI, typename TO>
+// MASS: mass part only, y (+)= sign * (TM (x) M_h) x (no derivative sweeps, TA ignored).
+template <int N, int NT, typename T, int CPB, typename TI, typename TO, bool MASS = false>
 __global__ void __launch_bounds__(CPB * N * N)
 apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict__ geo, GridDesc g,
                OpTab<T> tab, int mask_input) {
+  using Acc = typename acc_of<T>::type;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
@@ -68,7 +70,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int t = 0; t < NT; ++t)
 #pragma unroll
       for (int q = 0; q < N; ++q) {
-        T v = 0;
+        Acc v = 0;
 #pragma unroll
         for (int k = 0; k < N; ++k) v += tab.B[q][k] * xcol[t][k];
         s0[I4(t, q, j, i)] = v;
@@ -80,7 +82,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   for (int t = 0; t < NT; ++t)
 #pragma unroll
     for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int b = 0; b < N; ++b) v += tab.B[j][b] * s0[I4(t, qz, b, i)];
       s1[I4(t, qz, j, i)] = v;
@@ -92,12 +94,32 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   for (int t = 0; t < NT; ++t)
 #pragma unroll
     for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) v += tab.B[i][a] * s1[I4(t, qz, j, a)];
-      u[t][qz] = v;
-      s0[I4(t, qz, j, i)] = v;
+      const T vt = v;
+      u[t][qz] = vt;
+      if constexpr (!MASS) s0[I4(t, qz, j, i)] = vt;
     }
+  if constexpr (MASS) {
+    // time mixing and mass weight at each Gauss point of the column; s0 is free (nobody reads it)
+    const T* gm = geo + cc * 7 * N3 + 6 * N3;
+#pragma unroll
+    for (int qz = 0; qz < N; ++qz) {
+      const T m = gm[i + N * (j + N * qz)];
+      T w[NT];
+#pragma unroll
+      for (int it = 0; it < NT; ++it) {
+        Acc v = 0;
+#pragma unroll
+        for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qz];
+        w[it] = m * v;
+      }
+#pragma unroll
+      for (int it = 0; it < NT; ++it) s0[I4(it, qz, j, i)] = w[it];
+    }
+    __syncthreads();
+  } else {
   __syncthreads();
   // derivatives, time mixing and metric at each Gauss point of the column
   T fz[NT][N], val[NT][N];
@@ -107,7 +129,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     T ux[NT], uy[NT], uz[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      T a0 = 0, a1 = 0, a2 = 0;
+      Acc a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         a0 += tab.D[i][a] * s0[I4(t, qz, j, a)];
@@ -125,7 +147,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       // TA = M_tau is diagonal (Lagrange time basis at the quadrature nodes): no mixing of gradients
       const T ta = tab.TA[it][it];
       const T gx_ = ta * ux[it], gy_ = ta * uy[it], gz_ = ta * uz[it];
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qz];
       s1[I4(it, qz, j, i)] = G00 * gx_ + G01 * gy_ + G02 * gz_;
@@ -140,7 +162,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   for (int it = 0; it < NT; ++it)
 #pragma unroll
     for (int qz = 0; qz < N; ++qz) {
-      T v = val[it][qz];
+      Acc v = val[it][qz];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         v += tab.D[a][i] * s1[I4(it, qz, j, a)];
@@ -155,12 +177,13 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
 #pragma unroll
     for (int qz = 0; qz < N; ++qz) s0[I4(it, qz, j, i)] = u[it][qz];
   __syncthreads();
+  }
   // B^T in x: thread (node i, qy = j)
 #pragma unroll
   for (int it = 0; it < NT; ++it)
 #pragma unroll
     for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) v += tab.B[a][i] * s0[I4(it, qz, j, a)];
       s1[I4(it, qz, j, i)] = v;
@@ -172,14 +195,14 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     T r[N];
 #pragma unroll
     for (int qz = 0; qz < N; ++qz) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int b = 0; b < N; ++b) v += tab.B[b][j] * s1[I4(it, qz, b, i)];
       r[qz] = v;
     }
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int qz = 0; qz < N; ++qz) v += tab.B[qz][k] * r[qz];
       const int gz = cz * g.p + k;
@@ -191,10 +214,11 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   }
 }
 
-template <int N, int NT, typename T, int CPB, typename TI, typename TO>
+template <int N, int NT, typename T, int CPB, typename TI, typename TO, bool MASS = false>
 __global__ void __launch_bounds__(CPB * N)
 apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict__ geo, GridDesc g,
                OpTab<T> tab, int mask_input) {
+  using Acc = typename acc_of<T>::type;
   constexpr int N2 = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
@@ -224,7 +248,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int t = 0; t < NT; ++t)
 #pragma unroll
       for (int q = 0; q < N; ++q) {
-        T v = 0;
+        Acc v = 0;
 #pragma unroll
         for (int k = 0; k < N; ++k) v += tab.B[q][k] * xcol[t][k];
         s0[I3(t, q, i)] = v;
@@ -236,12 +260,31 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   for (int t = 0; t < NT; ++t)
 #pragma unroll
     for (int qy = 0; qy < N; ++qy) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) v += tab.B[i][a] * s0[I3(t, qy, a)];
-      u[t][qy] = v;
-      s1[I3(t, qy, i)] = v;
+      const T vt = v;
+      u[t][qy] = vt;
+      if constexpr (!MASS) s1[I3(t, qy, i)] = vt;
     }
+  if constexpr (MASS) {
+    const T* gm = geo + cc * 4 * N2 + 3 * N2;
+#pragma unroll
+    for (int qy = 0; qy < N; ++qy) {
+      const T m = gm[i + N * qy];
+      T w[NT];
+#pragma unroll
+      for (int it = 0; it < NT; ++it) {
+        Acc v = 0;
+#pragma unroll
+        for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qy];
+        w[it] = m * v;
+      }
+#pragma unroll
+      for (int it = 0; it < NT; ++it) s1[I3(it, qy, i)] = w[it];
+    }
+    __syncthreads();
+  } else {
   __syncthreads();
   T fy[NT][N], val[NT][N];
   const T* gc = geo + cc * 4 * N2;
@@ -250,7 +293,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     T ux[NT], uy[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      T a0 = 0, a1 = 0;
+      Acc a0 = 0, a1 = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         a0 += tab.D[i][a] * s1[I3(t, qy, a)];
@@ -264,7 +307,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int it = 0; it < NT; ++it) {
       const T ta = tab.TA[it][it];
       const T gx_ = ta * ux[it], gy_ = ta * uy[it];
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int jt = 0; jt < NT; ++jt) v += tab.TM[it][jt] * u[jt][qy];
       s0[I3(it, qy, i)] = G00 * gx_ + G01 * gy_;
@@ -277,7 +320,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   for (int it = 0; it < NT; ++it)
 #pragma unroll
     for (int qy = 0; qy < N; ++qy) {
-      T v = val[it][qy];
+      Acc v = val[it][qy];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         v += tab.D[a][i] * s0[I3(it, qy, a)];
@@ -290,19 +333,20 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
 #pragma unroll
     for (int qy = 0; qy < N; ++qy) s1[I3(it, qy, i)] = u[it][qy];
   __syncthreads();
+  }
 #pragma unroll
   for (int it = 0; it < NT; ++it) {
     T r[N];
 #pragma unroll
     for (int qy = 0; qy < N; ++qy) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) v += tab.B[a][i] * s1[I3(it, qy, a)];
       r[qy] = v;
     }
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      T v = 0;
+      Acc v = 0;
 #pragma unroll
       for (int qy = 0; qy < N; ++qy) v += tab.B[qy][k] * r[qy];
       const int gy = cy * g.p + k;
@@ -312,14 +356,14 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   }
 }
 
-template <int DIM, int N, int NT, typename T, typename TI, typename TO>
+template <int DIM, int N, int NT, typename T, typename TI, typename TO, bool MASS = false>
 cudaError_t launch_apply_t(const TI* x, TO* y, const T* geo, const GridDesc& g, const OpTab<T>& tab,
                            int mask_input, cudaStream_t s) {
   constexpr int CPB = cells_per_block<N>(DIM);
   const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
   if constexpr (DIM == 3) {
     const size_t smem = (size_t)CPB * 3 * NT * N * N * N * sizeof(T);
-    auto k = apply3d_kernel<N, NT, T, CPB, TI, TO>;
+    auto k = apply3d_kernel<N, NT, T, CPB, TI, TO, MASS>;
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -328,7 +372,7 @@ cudaError_t launch_apply_t(const TI* x, TO* y, const T* geo, const GridDesc& g, 
     k<<<(unsigned)blocks, CPB * N * N, smem, s>>>(x, y, geo, g, tab, mask_input);
   } else {
     const size_t smem = (size_t)CPB * 2 * NT * N * N * sizeof(T);
-    auto k = apply2d_kernel<N, NT, T, CPB, TI, TO>;
+    auto k = apply2d_kernel<N, NT, T, CPB, TI, TO, MASS>;
     k<<<(unsigned)blocks, CPB * N, smem, s>>>(x, y, geo, g, tab, mask_input);
   }
   return cudaGetLastError();

@@ -18,6 +18,7 @@
 // (p+1)^(2 dim) numbers per cell), inverse transform; the additive sum over
 // overlapping cells uses atomic adds.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -31,9 +32,11 @@ struct Shape {
   static constexpr int NB = DIM == 3 ? N * N * N : N * N;
 };
 
-// Elements per cell in the inverse store: N_t planes of NB x NB, padded to a multiple
-// of 8 elements so that every cell block starts on a 16-byte boundary (FP32/BF16/FP64).
-__host__ __device__ constexpr int64_t cell_stride(int nb, int nt) { return ((int64_t)nt * nb * nb + 7) / 8 * 8; }
+// Inverse store: per cell N_t planes of NB rows x NBP columns, row-major, NBP = NB rounded up to a
+// multiple of 4 (zero padding), so that a row starts on an 8-byte boundary (BF16) and is read four
+// entries at a time; cell blocks padded to a multiple of 8 elements (16-byte boundaries).
+__host__ __device__ constexpr int nb_pad(int nb) { return (nb + 3) / 4 * 4; }
+__host__ __device__ constexpr int64_t cell_stride(int nb, int nt) { return ((int64_t)nt * nb * nb_pad(nb) + 7) / 8 * 8; }
 
 __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ inline double2 cinv(double2 a) {
@@ -177,13 +180,14 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
         }
       __syncthreads();
     }
-    // store column-major planes: element (a, b) at b * NB + a
+    // store row-major planes: element (a, b) at a * NBP + b, zero padding columns
+    constexpr int NBP = nb_pad(NB);
     const int nplanes = m < nreal ? 1 : 2;
     for (int pl = 0; pl < nplanes; ++pl) {
-      const int64_t base = (int64_t)cell * cell_stride(NB, nt) + (int64_t)(plane + pl) * NB * NB;
-      for (int pr = tid; pr < NB * NB; pr += blockDim.x) {
-        const int b = pr / NB, a = pr % NB;
-        const double2 v = C[a * NB + b];
+      const int64_t base = (int64_t)cell * cell_stride(NB, nt) + (int64_t)(plane + pl) * NB * NBP;
+      for (int pr = tid; pr < NB * NBP; pr += blockDim.x) {
+        const int a = pr / NBP, b = pr % NBP;
+        const double2 v = b < NB ? C[a * NB + b] : make_double2(0.0, 0.0);
         const double x = pl == 0 ? v.x : v.y;
         if (inv_prec == 0) reinterpret_cast<double*>(inv_out)[base + pr] = x;
         else if (inv_prec == 1) reinterpret_cast<float*>(inv_out)[base + pr] = (float)x;
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(AsmCfg<DIM, N, NT, TI>::CPB * AsmCfg<DIM, N, N
 asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g, ModeTab<T> mt,
                  const T* __restrict__ copy_src, T* __restrict__ copy_dst) {
   using C = AsmCfg<DIM, N, NT, TI>;
-  constexpr int NB = C::NB, TPC = C::TPC, CPB = C::CPB;
+  constexpr int NB = C::NB, TPC = C::TPC, CPB = C::CPB, NBP = nb_pad(NB);
   constexpr int64_t CS = C::CS;
   __shared__ T s_r[CPB][NT][NB];
   const int slot = threadIdx.x / TPC;
@@ -269,18 +273,18 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
     if (m < mt.nreal) {
-      const TI* pl = ic + m * NB * NB + a;
+      const TI* pl = ic + (m * NB + a) * NBP;
       T acc = 0;
 #pragma unroll
-      for (int b = 0; b < NB; ++b) acc += inv_val<T, TI>(ldg_inv(pl + b * NB)) * s_r[slot][m][b];
+      for (int b = 0; b < NB; ++b) acc += inv_val<T, TI>(ldg_inv(pl + b)) * s_r[slot][m][b];
       z[m] = acc;
     } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
-      const TI* pr_ = ic + m * NB * NB + a;
-      const TI* pi_ = pr_ + NB * NB;
+      const TI* pr_ = ic + (m * NB + a) * NBP;
+      const TI* pi_ = pr_ + NB * NBP;
       T zr = 0, zi = 0;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        const T ir = inv_val<T, TI>(ldg_inv(pr_ + b * NB)), ii = inv_val<T, TI>(ldg_inv(pi_ + b * NB));
+        const T ir = inv_val<T, TI>(ldg_inv(pr_ + b)), ii = inv_val<T, TI>(ldg_inv(pi_ + b));
         const T sre = s_r[slot][m][b], sim = s_r[slot][m + 1][b];
         zr += ir * sre - ii * sim;
         zi += ir * sim + ii * sre;
@@ -305,6 +309,232 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
   }
 }
 
+// ---- TMA-fed variant: bulk copies of whole cell groups into a ring of shared-memory stages ----
+//
+// The inverse store is contiguous over cells, so the planes of CPG consecutive cells are one
+// bulk copy (cp.async.bulk, completion counted on an mbarrier).  Each CTA walks its groups with
+// S stages in flight; while a group's copy lands, its threads form the modal residual of the
+// group's cells.  Every wait is bounded: on timeout the kernel records STMG_DEVICE_TIMEOUT in
+// *status, drains the copies it issued (bounded as well) and returns.
+template <int DIM, int N, int NT, typename TI>
+struct TmaCfg {
+  static constexpr int NB = Shape<DIM, N>::NB;
+  static constexpr int64_t CS = cell_stride(NB, NT);
+  static constexpr int CELL_BYTES = (int)(CS * sizeof(TI));
+  static constexpr int CPG0 = 128 / NB;
+  static constexpr int CPG_MEM = 20480 / CELL_BYTES;
+  static constexpr int CPG = CPG0 < CPG_MEM ? (CPG0 > 0 ? CPG0 : 1) : (CPG_MEM > 0 ? CPG_MEM : 1);
+  static constexpr int THREADS = (CPG * NB + 31) / 32 * 32;
+  static constexpr int STAGE_BYTES = CPG * CELL_BYTES;
+  static constexpr int S = STAGE_BYTES <= 16384 ? 4 : 3;
+  static constexpr size_t SMEM = (size_t)S * STAGE_BYTES;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Four consecutive entries of an inverse row in shared memory (8-byte aligned for BF16, 16 for FP32/FP64).
+__device__ __forceinline__ float4 inv4(const __nv_bfloat16* p) {
+  const uint2 w = *reinterpret_cast<const uint2*>(p);  // bf16 -> f32 places the 16 bits high
+  return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xffff0000u), __uint_as_float(w.y << 16),
+                     __uint_as_float(w.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 inv4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 inv4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+// sum_b row[b] s[b] over NBP entries (padding zero in both), two independent FP32x2 accumulators
+template <int NBP, typename TI>
+__device__ __forceinline__ float dot_row(const TI* row, const float* s) {
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < NBP; c += 4) {
+    const float4 w = inv4(row + c);
+    const float4 v = *reinterpret_cast<const float4*>(s + c);
+    a0 = __ffma2_rn(make_float2(w.x, w.y), make_float2(v.x, v.y), a0);
+    a1 = __ffma2_rn(make_float2(w.z, w.w), make_float2(v.z, v.w), a1);
+  }
+  return (a0.x + a0.y) + (a1.x + a1.y);
+}
+
+__device__ __forceinline__ void tma_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on phase `parity` of an mbarrier: false after kWaitNs nanoseconds, or as soon as
+// *status (if given) is nonzero because another CTA already gave up.
+constexpr uint64_t kWaitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* status) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    if (done) return true;
+    if ((it & 63) == 63) {
+      if (global_ns() - t0 > kWaitNs) return false;
+      if (status && *reinterpret_cast<const volatile int*>(status) != 0) return false;
+    }
+  }
+}
+
+template <int DIM, int N, int NT, typename T, typename TI>
+__global__ void __launch_bounds__(TmaCfg<DIM, N, NT, TI>::THREADS)
+asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g,
+                     ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst, int* status) {
+  using C = TmaCfg<DIM, N, NT, TI>;
+  constexpr int NB = C::NB, CPG = C::CPG, S = C::S;
+  constexpr int64_t CS = C::CS;
+  constexpr int NBP = nb_pad(NB);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[S];
+  __shared__ __align__(16) T s_r[CPG][NT][NBP];  // modal residual of the group's cells, zero padding
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  const int64_t ngroups = (g.n_cells + CPG - 1) / CPG;
+  auto group_bytes = [&](int64_t grp) -> uint32_t {
+    const int64_t c0 = grp * CPG;
+    const int64_t nc = g.n_cells - c0 < CPG ? g.n_cells - c0 : CPG;
+    return (uint32_t)(nc * C::CELL_BYTES);
+  };
+  if (tid == 0) s_fail = *reinterpret_cast<const volatile int*>(status);
+  for (int i = tid; i < CPG * NT * NBP; i += blockDim.x) (&s_r[0][0][0])[i] = T(0);
+  __syncthreads();
+  if (s_fail) return;  // an earlier wait gave up: issue nothing
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  // prologue: the first S groups of this CTA
+  int64_t issued = 0;  // groups issued by this CTA (thread 0's count; all threads track it alike)
+  if (tid == 0)
+    for (int s = 0; s < S; ++s) {
+      const int64_t grp = blockIdx.x + (int64_t)s * gridDim.x;
+      if (grp < ngroups)
+        tma_bulk_load(smem_raw + (size_t)s * C::STAGE_BYTES, inv + grp * CPG * CS, group_bytes(grp), &bar[s]);
+    }
+  for (int s = 0; s < S; ++s)
+    if (blockIdx.x + (int64_t)s * gridDim.x < ngroups) ++issued;
+  int64_t k = 0;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++k) {
+    const int stage = (int)(k % S);
+    const uint32_t parity = (uint32_t)((k / S) & 1);
+    // modal residual of this group's cells (independent of the copy in flight)
+    const int slot = tid / NB, a = tid - slot * NB;
+    const int64_t cell = grp * CPG + slot;
+    const bool active = slot < CPG && cell < g.n_cells;
+    int64_t node = 0;
+    bool live = false;
+    if (active) {
+      const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
+      const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+      const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
+      const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
+      bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+      if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
+      node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+      live = !bnd;
+      T rr[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
+      if (copy_dst) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) copy_dst[t * g.n_nodes + node] = copy_src[t * g.n_nodes + node];
+      }
+#pragma unroll
+      for (int m = 0; m < NT; ++m) {
+        const bool is_real = m < mt.nreal;
+        const int mode = is_real ? m : mt.nreal + (m - mt.nreal) / 2;
+        const bool im_part = !is_real && ((m - mt.nreal) & 1);
+        T v = 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[t];
+        s_r[slot][m][a] = v;
+      }
+    }
+    if (!mbar_wait(&bar[stage], parity, status)) {
+      atomicExch(status, STMG_DEVICE_TIMEOUT);
+      s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) break;
+    if (active && live) {
+      const TI* ic = reinterpret_cast<const TI*>(smem_raw + (size_t)stage * C::STAGE_BYTES) + slot * CS;
+      T z[NT];
+#pragma unroll
+      for (int m = 0; m < NT; ++m) z[m] = 0;
+#pragma unroll
+      for (int m = 0; m < NT; ++m) {
+        const TI* rr = ic + (m * NB + a) * NBP;  // row a of plane m
+        if (m < mt.nreal) {
+          if constexpr (std::is_same<T, float>::value) {
+            z[m] = dot_row<NBP>(rr, s_r[slot][m]);
+          } else {
+            T acc = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) acc += inv_val<T, TI>(rr[b]) * s_r[slot][m][b];
+            z[m] = acc;
+          }
+        } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+          const TI* ri = rr + NB * NBP;  // imaginary part: the next plane
+          if constexpr (std::is_same<T, float>::value) {
+            z[m] = dot_row<NBP>(rr, s_r[slot][m]) - dot_row<NBP>(ri, s_r[slot][m + 1]);
+            z[m + 1] = dot_row<NBP>(rr, s_r[slot][m + 1]) + dot_row<NBP>(ri, s_r[slot][m]);
+          } else {
+            T zr = 0, zi = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const T ir = inv_val<T, TI>(rr[b]), ii = inv_val<T, TI>(ri[b]);
+              const T sre = s_r[slot][m][b], sim = s_r[slot][m + 1][b];
+              zr += ir * sre - ii * sim;
+              zi += ir * sim + ii * sre;
+            }
+            z[m] = zr;
+            z[m + 1] = zi;
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        T o = 0;
+#pragma unroll
+        for (int m = 0; m < NT; ++m) {
+          if (m < mt.nreal) {
+            o += mt.Vr[t][m] * z[m];
+          } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+            const int mode = mt.nreal + (m - mt.nreal) / 2;
+            o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
+          }
+        }
+        atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
+      }
+    }
+    __syncthreads();  // stage and s_r free again
+    const int64_t next = grp + (int64_t)S * gridDim.x;
+    if (next < ngroups) {
+      if (tid == 0)
+        tma_bulk_load(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage]);
+      ++issued;
+    }
+  }
+  // after a timeout: wait (bounded) for the copies still in flight before the CTA exits
+  if (s_fail) {
+    for (int64_t q = k; q < issued; ++q) mbar_wait(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
+  }
+}
+
 template <int DIM, int N>
 cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, const double* lr, const double* li,
                     int nreal, int ncplx, void* inv, int inv_prec, cudaStream_t s) {
@@ -320,11 +550,32 @@ cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, 
 
 template <int DIM, int N, int NT, typename T, typename TI>
 cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd,
-                    cudaStream_t s) {
-  using C = AsmCfg<DIM, N, NT, TI>;
-  const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
-  asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, C::CPB * C::TPC, 0, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt,
-                                                                                 cs, cd);
+                    int* status, cudaStream_t s) {
+  // row-streaming kernel when there is no device status word to report a timeout to, or when
+  // S stages of one cell's planes exceed the shared memory of an SM (p = 3, N_t = 4, FP64)
+  if (!status || TmaCfg<DIM, N, NT, TI>::SMEM > (size_t)200 * 1024) {
+    using C = AsmCfg<DIM, N, NT, TI>;
+    const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
+    asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, C::CPB * C::TPC, 0, s>>>(
+        r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd);
+    return cudaGetLastError();
+  }
+  using C = TmaCfg<DIM, N, NT, TI>;
+  auto k = asm_apply_tma_kernel<DIM, N, NT, T, TI>;
+  static int per_sm = 0, sms = 0;  // one value per instantiation (same device for all contexts)
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
+  const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+  k<<<(unsigned)grid, C::THREADS, C::SMEM, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status);
   return cudaGetLastError();
 }
 
@@ -351,14 +602,15 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
 
 #define STMG_ASM_CASE(DIM, N, NT)                                                                  \
   if (dim == DIM && n == N && nt == NT) {                                                          \
-    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, s);         \
-    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, s);          \
-    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, s);                     \
+    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, status, s); \
+    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, status, s);  \
+    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, status, s);             \
   }
 
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
-                             const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd, cudaStream_t s) {
+                             const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd, int* status,
+                             cudaStream_t s) {
   STMG_ASM_CASE(3, 2, 1) STMG_ASM_CASE(3, 2, 2) STMG_ASM_CASE(3, 2, 3) STMG_ASM_CASE(3, 2, 4)
   STMG_ASM_CASE(3, 3, 1) STMG_ASM_CASE(3, 3, 2) STMG_ASM_CASE(3, 3, 3) STMG_ASM_CASE(3, 3, 4)
   STMG_ASM_CASE(3, 4, 1) STMG_ASM_CASE(3, 4, 2) STMG_ASM_CASE(3, 4, 3) STMG_ASM_CASE(3, 4, 4)
@@ -370,9 +622,9 @@ cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const voi
 }
 
 template cudaError_t launch_asm_apply<float>(int, int, int, const float*, float*, const void*, int, const GridDesc&,
-                                             const ModeTab<float>&, const float*, float*, cudaStream_t);
+                                             const ModeTab<float>&, const float*, float*, int*, cudaStream_t);
 template cudaError_t launch_asm_apply<double>(int, int, int, const double*, double*, const void*, int,
-                                              const GridDesc&, const ModeTab<double>&, const double*, double*,
+                                              const GridDesc&, const ModeTab<double>&, const double*, double*, int*,
                                               cudaStream_t);
 
 }  // namespace stmg

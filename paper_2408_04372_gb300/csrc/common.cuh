@@ -8,6 +8,7 @@
 namespace stmg {
 
 constexpr int kMaxN = 5;    // p <= 4
+constexpr int STMG_DEVICE_TIMEOUT = 1;  // device status word: a bounded wait gave up
 constexpr int kMaxNT = 4;   // time DoFs per slab
 
 // Tables of one operator evaluation, passed by value (constant bank).

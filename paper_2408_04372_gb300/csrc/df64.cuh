@@ -62,4 +62,32 @@ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) {
 
 __device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
 
+// Accumulator of a sum of double-float terms with the renormalisation deferred to the end:
+// each term costs TwoSum on the high parts (6 additions) plus 2 additions into the low part,
+// instead of a renormalised double-float sum (11 additions).  The low part collects the exact
+// TwoSum errors and the terms' low parts; its own rounding is of order 2^-24 of itself, i.e.
+// 2^-48 of the sum, which keeps the ~44-bit accuracy of the arithmetic.
+struct df_acc {
+  float hi, lo;
+  df_acc() = default;
+  __device__ constexpr df_acc(float h) : hi(h), lo(0.0f) {}
+  __device__ constexpr df_acc(df64 v) : hi(v.hi), lo(v.lo) {}
+  __device__ __forceinline__ operator df64() const {
+    const float h = __fadd_rn(hi, lo);
+    return df64(h, __fsub_rn(lo, __fsub_rn(h, hi)));
+  }
+};
+__device__ __forceinline__ df_acc& operator+=(df_acc& a, df64 t) {
+  const float s = __fadd_rn(a.hi, t.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(t.hi, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(t.lo, e));
+  return a;
+}
+
+// Accumulator type of a sum in arithmetic T (the type itself except for double-float).
+template <typename T> struct acc_of { using type = T; };
+template <> struct acc_of<df64> { using type = df_acc; };
+
 }  // namespace stmg

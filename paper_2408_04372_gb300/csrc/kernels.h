@@ -14,6 +14,9 @@ namespace stmg {
 template <typename T>
 cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo, const GridDesc& g,
                          const OpTab<T>& tab, int mask_input, cudaStream_t s);
+// Mass part only, y += (TM (x) M_h) x in FP64 (TA ignored, no input masking): right-hand sides.
+cudaError_t launch_mass_apply(int dim, int n, int nt, const double* x, double* y, const double* geo, const GridDesc& g,
+                              const OpTab<double>& tab, cudaStream_t s);
 // Same operator in double-float arithmetic (df64.cuh) for an FP32 input vector, accumulated into
 // an FP64 output: the FGMRES apply on V-cycle outputs, which are exact in FP32.
 cudaError_t launch_apply_df(int dim, int n, int nt, const float* x, double* y, const df64* geo, const GridDesc& g,
@@ -42,10 +45,13 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
                              int inv_prec, cudaStream_t s);
 // elements per cell in the inverse store (N_t planes, padded to a 16-byte multiple)
 int64_t asm_cell_stride(int dim, int n, int nt);
-// copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell
+// copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell.
+// status (device int, may be NULL): with it the inverses arrive by bulk copies (TMA) into shared memory and
+// a timed-out wait stores STMG_DEVICE_TIMEOUT there; without it each thread streams its rows itself.
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
-                             const GridDesc& g, const ModeTab<T>& mt, const T* copy_src, T* copy_dst, cudaStream_t s);
+                             const GridDesc& g, const ModeTab<T>& mt, const T* copy_src, T* copy_dst, int* status,
+                             cudaStream_t s);
 
 // ---- fast diagonalisation local solves (fd.cu), 3D Cartesian cells ----
 template <typename T>

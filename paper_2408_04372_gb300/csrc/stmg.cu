@@ -76,6 +76,7 @@ struct stmg_ctx {
   double* Z = nullptr;   // (m) vectors
   double* partial = nullptr;        // per-block partial sums of the Gram-Schmidt passes
   unsigned int* counter = nullptr;  // arrival counter of those passes (zero between launches)
+  int* status = nullptr;            // device status word: nonzero after a bounded device wait gave up
   double* dsm = nullptr;  // device scalars [0..nvec+8) h1, [128..) h2, [256..) outputs
   double* hsm = nullptr;  // pinned host mirror
   double* tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -251,7 +252,8 @@ stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega, cons
     CK(launch_fd_apply<T>(L.n, L.nt, r, u, rho_of<T>(L), L.g, fd_of<T>(L), mt, copy_src, copy_dst, ctx->stream));
     return STMG_OK;
   }
-  CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->stream));
+  CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->status,
+                         ctx->stream));
   return STMG_OK;
 }
 
@@ -713,6 +715,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (dim != 2 && dim != 3) return invalid(ctx, "dim must be 2 or 3");
   if (N < 2) return invalid(ctx, "n_cells must be >= 2");
   if (pr->p < 1 || pr->p > 4) return invalid(ctx, "p must be in 1..4");
+  CKS(dev_alloc(ctx, &ctx->status, 1));
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   if (pr->time_scheme != STMG_DG && pr->time_scheme != STMG_CGP) return invalid(ctx, "unknown time scheme");
   if (pr->pde != STMG_HEAT && pr->pde != STMG_WAVE) return invalid(ctx, "unknown pde");
   const int nt = pr->time_scheme == STMG_DG ? pr->k + 1 : pr->k;
@@ -994,6 +998,18 @@ stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
   return STMG_OK;
 }
 
+// Synchronises and reads the device status word (bounded waits that gave up set it).
+stmg_status check_device_status(stmg_ctx* ctx) {
+  int* h = reinterpret_cast<int*>(ctx->hsm + 510);
+  CK(cudaMemcpyAsync(h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (*h != 0) {
+    ctx->err = "a device wait for a bulk copy gave up (status word set); results of this call are invalid";
+    return STMG_ERR_TIMEOUT;
+  }
+  return STMG_OK;
+}
+
 stmg_status norm2(stmg_ctx* ctx, const double* x, int64_t n, double& out) {
   CKS(dot_self(ctx, x, n, ctx->dsm + 448));
   CK(cudaMemcpyAsync(ctx->hsm + 448, ctx->dsm + 448, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1080,7 +1096,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
   }
   s.iterations = its;
   if (st) *st = s;
-  CK(cudaStreamSynchronize(ctx->stream));
+  CKS(check_device_status(ctx));
   if (result != STMG_OK) ctx->err = "FGMRES did not reach rtol within max_it";
   return result;
 }
@@ -1098,7 +1114,7 @@ stmg_status rhs_impl(stmg_ctx* ctx, const double* f, const double* f0, const dou
       t.TM[i][j] = (i < nt && j < nt) ? L.sc.RM_f[i * nt + j] : 0.0;
     }
   t.sign = 1.0;
-  if (f) CK(launch_apply<double>(L.dim, L.n, nt, f, rhs, L.geo64, L.g, t, 0, ctx->stream));
+  if (f) CK(launch_mass_apply(L.dim, L.n, nt, f, rhs, L.geo64, L.g, t, ctx->stream));
   ctx->launches += 3;
   // single-block terms
   const double* srcs[4] = {f0, u0, u0, v0};
@@ -1118,7 +1134,8 @@ stmg_status rhs_impl(stmg_ctx* ctx, const double* f, const double* f0, const dou
       for (int j = 0; j < kMaxNT; ++j) { t1.TA[i][j] = 0.0; t1.TM[i][j] = 0.0; }
     if (stiff[term]) t1.TA[0][0] = 1.0; else t1.TM[0][0] = 1.0;
     t1.sign = 1.0;
-    CK(launch_apply<double>(L.dim, L.n, 1, srcs[term], out, L.geo64, L.g, t1, 0, ctx->stream));
+    if (stiff[term]) CK(launch_apply<double>(L.dim, L.n, 1, srcs[term], out, L.geo64, L.g, t1, 0, ctx->stream));
+    else CK(launch_mass_apply(L.dim, L.n, 1, srcs[term], out, L.geo64, L.g, t1, ctx->stream));
     ctx->launches += 1;
     xs.push_back(out);
     used.push_back(term);
