@@ -595,17 +595,25 @@ def read_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
-def read_traffic(key):
-    """DRAM bytes per launch from the committed ncu capture; None once the kernel source changed."""
+def source_sha(paths):
+    """First 16 hex digits of the SHA-256 over the given source files, in order."""
     import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(key):
+    """DRAM bytes per launch from the committed ncu capture; None once a source of the kernel changed."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(key)
     if d is None:
         return None
-    src = os.path.join(ROOT, d["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+    srcs = d["sources"] if "sources" in d else [d["source"]]
+    if source_sha(srcs) != d["source_sha"]:
         return None
     return d.get("bytes_per_launch")
 

@@ -107,6 +107,8 @@ typedef struct {
   int outer_apply;         /* arithmetic of the FGMRES operator apply on V-cycle outputs: STMG_FP64, or
                               STMG_DF32 (FP32 V-cycle only; its outputs are exact in FP32) [DF32 with
                               the FP32 V-cycle, else FP64].  Residuals b - S x always use FP64. */
+  double atol;             /* absolute residual target: stmg_solve stops at ||rhs - S u||_2 <=
+                              max(rtol ||rhs||_2, atol) [0: relative test only] */
 } stmg_options;
 
 typedef struct {
@@ -246,6 +248,12 @@ stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count);
  * STMG_KERNEL_VCYCLE (one whole V-cycle from level 0; level must be 0).  Synchronous.
  * precision STMG_DF32 times the double-float level-0 apply (outer_apply = STMG_DF32). */
 enum { STMG_KERNEL_APPLY = 1, STMG_KERNEL_ASM = 2, STMG_KERNEL_VCYCLE = 3 };
+/* Test hook for failure detection (no counterpart in the paper).  Runs one kernel whose bounded
+ * device wait cannot complete: it gives up after about one second and records the timeout in the
+ * context's device status word, exactly as a bulk copy that never lands would.  Nothing faults.
+ * Returns STMG_ERR_TIMEOUT; from then on the bulk-copy kernels of this context skip their work and
+ * stmg_solve returns STMG_ERR_TIMEOUT.  Destroy the context afterwards.  Synchronous. */
+stmg_status stmg_selftest_device_timeout(stmg_ctx* ctx);
 stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision, int reps, double* avg_ms);
 
 #ifdef __cplusplus

@@ -29,7 +29,7 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_wave_velocity", "stmg_guess_previous", "stmg_solve_slab_host", "stmg_launch_count",
            "stmg_time_kernel", "stmg_smooth_noalloc", "stmg_net_create", "stmg_net_destroy", "stmg_net_predict",
            "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights", "stmg_select_guess",
-           "stmg_solve_slab_host_learned"]
+           "stmg_solve_slab_host_learned", "stmg_selftest_device_timeout"]
 KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
 
 
@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("vcycle_precision", ctypes.c_int),
                 ("inverse_precision", ctypes.c_int), ("smoother_kind", ctypes.c_int),
                 ("omega", ctypes.POINTER(ctypes.c_double)), ("fgmres_restart", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("outer_apply", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("outer_apply", ctypes.c_int),
+                ("atol", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "stmg_guess_previous": [vp, vp, vp],
         "stmg_solve_slab_host": [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SolveStats)],
         "stmg_launch_count": [vp, ctypes.POINTER(i64)],
+        "stmg_selftest_device_timeout": [vp],
         "stmg_smooth_noalloc": [vp, i32, i32, i32, vp, vp],
         "stmg_net_create": [ctypes.POINTER(vp), vp, i32, ctypes.POINTER(i32), dp, dp, dp],
         "stmg_net_destroy": [vp],
@@ -130,7 +132,7 @@ class Context:
     def __init__(self, dim, n_cells, p, k, tau, pde=HEAT, scheme=DG, vertices=None, coeff=None,
                  coeff_mode=COEFF_PER_CELL, nu_pre=1, nu_post=1, vcycle_precision=FP32, inverse_precision=0,
                  omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO,
-                 outer_apply=0):
+                 outer_apply=0, atol=0.0):
         import numpy as np
         import torch
         self.lib = load()
@@ -143,7 +145,7 @@ class Context:
         mesh = Mesh(dim, n_cells, _dptr(v))
         prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c))
         opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, smoother_kind, _dptr(om), restart, rtol,
-                       max_it, outer_apply)
+                       max_it, outer_apply, float(atol))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -278,6 +280,10 @@ class Context:
         c = ctypes.c_int64()
         self._check(self.lib.stmg_launch_count(self.h, ctypes.byref(c)))
         return c.value
+
+    def selftest_device_timeout(self):
+        """Runs the bounded-wait test hook; returns the status code (STMG_ERR_TIMEOUT = 6 expected)."""
+        return self.lib.stmg_selftest_device_timeout(self.h)
 
     def time_kernel(self, kernel, level=0, precision=FP64, reps=20):
         """Mean duration in ms of one kernel, CUDA events on the context's own stream."""

@@ -13,6 +13,8 @@ using apply_detail::launch_apply_t;
 template <typename T, typename TX = T>
 __global__ void init_rows_kernel(T* __restrict__ y, const T* __restrict__ f, const TX* __restrict__ x,
                                  GridDesc g, int nt, int mode) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t total = g.n_nodes * nt;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -75,7 +77,7 @@ cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, in
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
-  init_rows_kernel<T><<<blocks, 256, 0, s>>>(y, f, x, g, nt, mode);
+  { const cudaError_t e_ = launch_k(init_rows_kernel<T>, dim3(blocks), dim3(256), 0, s, y, f, x, g, nt, mode); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -84,7 +86,7 @@ cudaError_t launch_init_rows_f2d(double* y, const float* x, const GridDesc& g, i
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) blocks = 1;
-  init_rows_kernel<double, float><<<blocks, 256, 0, s>>>(y, nullptr, x, g, nt, 0);
+  { const cudaError_t e_ = launch_k(init_rows_kernel<double, float>, dim3(blocks), dim3(256), 0, s, y, nullptr, x, g, nt, 0); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 

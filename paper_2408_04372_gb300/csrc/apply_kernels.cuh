@@ -35,6 +35,8 @@ template <int N, int NT, typename T, int CPB, typename TI, typename TO, bool MAS
 __global__ void __launch_bounds__(CPB * N * N)
 apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict__ geo, GridDesc g,
                OpTab<T> tab, int mask_input) {
+  pdl_wait();
+  pdl_trigger();
   using Acc = typename acc_of<T>::type;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -53,6 +55,17 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N), cz = (int)(cc / ((int64_t)g.N * g.N));
   const int gx = cx * g.p + i, gy = cy * g.p + j;
   const bool bxy = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+  // FP32: the metric of this thread's column of Gauss points is loaded first, so that its latency
+  // overlaps the gather and the interpolation sweeps (wider types keep their registers for arithmetic)
+  constexpr bool kPre = sizeof(T) == 4 && !MASS;
+  T gpre[kPre ? 7 : 1][kPre ? N : 1];
+  if constexpr (kPre) {
+    const T* gc0 = geo + cc * 7 * N3;
+#pragma unroll
+    for (int c = 0; c < 7; ++c)
+#pragma unroll
+      for (int qz = 0; qz < N; ++qz) gpre[c][qz] = gc0[c * N3 + i + N * (j + N * qz)];
+  }
 
   // gather + interpolation in z (registers)
   {
@@ -139,9 +152,14 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       ux[t] = a0; uy[t] = a1; uz[t] = a2;
     }
     const int q = i + N * (j + N * qz);
-    const T G00 = gc[0 * N3 + q], G01 = gc[1 * N3 + q], G02 = gc[2 * N3 + q];
-    const T G11 = gc[3 * N3 + q], G12 = gc[4 * N3 + q], G22 = gc[5 * N3 + q];
-    const T m = gc[6 * N3 + q];
+    T G00, G01, G02, G11, G12, G22, m;
+    if constexpr (kPre) {
+      G00 = gpre[0][qz]; G01 = gpre[1][qz]; G02 = gpre[2][qz];
+      G11 = gpre[3][qz]; G12 = gpre[4][qz]; G22 = gpre[5][qz]; m = gpre[6][qz];
+    } else {
+      G00 = gc[0 * N3 + q]; G01 = gc[1 * N3 + q]; G02 = gc[2 * N3 + q];
+      G11 = gc[3 * N3 + q]; G12 = gc[4 * N3 + q]; G22 = gc[5 * N3 + q]; m = gc[6 * N3 + q];
+    }
 #pragma unroll
     for (int it = 0; it < NT; ++it) {
       // TA = M_tau is diagonal (Lagrange time basis at the quadrature nodes): no mixing of gradients
@@ -218,6 +236,8 @@ template <int N, int NT, typename T, int CPB, typename TI, typename TO, bool MAS
 __global__ void __launch_bounds__(CPB * N)
 apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict__ geo, GridDesc g,
                OpTab<T> tab, int mask_input) {
+  pdl_wait();
+  pdl_trigger();
   using Acc = typename acc_of<T>::type;
   constexpr int N2 = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -369,11 +389,11 @@ cudaError_t launch_apply_t(const TI* x, TO* y, const T* geo, const GridDesc& g, 
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr = true;
     }
-    k<<<(unsigned)blocks, CPB * N * N, smem, s>>>(x, y, geo, g, tab, mask_input);
+    { const cudaError_t e_ = launch_k(k, dim3((unsigned)blocks), dim3(CPB * N * N), smem, s, x, y, geo, g, tab, mask_input); if (e_ != cudaSuccess) return e_; }
   } else {
     const size_t smem = (size_t)CPB * 2 * NT * N * N * sizeof(T);
     auto k = apply2d_kernel<N, NT, T, CPB, TI, TO, MASS>;
-    k<<<(unsigned)blocks, CPB * N, smem, s>>>(x, y, geo, g, tab, mask_input);
+    { const cudaError_t e_ = launch_k(k, dim3((unsigned)blocks), dim3(CPB * N), smem, s, x, y, geo, g, tab, mask_input); if (e_ != cudaSuccess) return e_; }
   }
   return cudaGetLastError();
 }

@@ -226,6 +226,8 @@ template <int DIM, int N, int NT, typename T, typename TI>
 __global__ void __launch_bounds__(AsmCfg<DIM, N, NT, TI>::CPB * AsmCfg<DIM, N, NT, TI>::TPC)
 asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g, ModeTab<T> mt,
                  const T* __restrict__ copy_src, T* __restrict__ copy_dst) {
+  pdl_wait();
+  pdl_trigger();
   using C = AsmCfg<DIM, N, NT, TI>;
   constexpr int NB = C::NB, TPC = C::TPC, CPB = C::CPB, NBP = nb_pad(NB);
   constexpr int64_t CS = C::CS;
@@ -387,10 +389,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
   }
 }
 
+// Test hook for the timeout path: one thread waits on an mbarrier that nothing will complete (no
+// copy is issued), gives up after the bounded wait and records the timeout.  Nothing faults.
+__global__ void wait_selftest_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+  if (!mbar_wait(&bar, 0u, nullptr)) atomicExch(status, STMG_DEVICE_TIMEOUT);
+}
+
 template <int DIM, int N, int NT, typename T, typename TI>
 __global__ void __launch_bounds__(TmaCfg<DIM, N, NT, TI>::THREADS)
 asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g,
                      ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst, int* status) {
+  pdl_wait();
+  pdl_trigger();
   using C = TmaCfg<DIM, N, NT, TI>;
   constexpr int NB = C::NB, CPG = C::CPG, S = C::S;
   constexpr int64_t CS = C::CS;
@@ -428,30 +441,44 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
   for (int s = 0; s < S; ++s)
     if (blockIdx.x + (int64_t)s * gridDim.x < ngroups) ++issued;
   int64_t k = 0;
+  // residual (and side-job source) of a group's node for this thread, loaded one group ahead so
+  // that their latency overlaps the previous group's work
+  const int slot = tid / NB, a = tid - slot * NB;
+  struct Pre { int64_t node; bool active, live; T rr[NT], cp[NT]; };
+  auto prefetch = [&](int64_t grp, Pre& P) {
+    const int64_t cell = grp * CPG + slot;
+    P.active = grp < ngroups && slot < CPG && cell < g.n_cells;
+    P.live = false;
+    P.node = 0;
+    if (!P.active) return;
+    const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
+    const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+    const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
+    const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
+    bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+    if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
+    P.node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+    P.live = !bnd;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) P.rr[t] = P.live ? r[t * g.n_nodes + P.node] : T(0);
+    if (copy_dst) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) P.cp[t] = copy_src[t * g.n_nodes + P.node];
+    }
+  };
+  Pre cur, nxt;
+  prefetch(blockIdx.x, cur);
   for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++k) {
     const int stage = (int)(k % S);
     const uint32_t parity = (uint32_t)((k / S) & 1);
+    prefetch(grp + gridDim.x, nxt);
+    const bool active = cur.active, live = cur.live;
+    const int64_t node = cur.node;
     // modal residual of this group's cells (independent of the copy in flight)
-    const int slot = tid / NB, a = tid - slot * NB;
-    const int64_t cell = grp * CPG + slot;
-    const bool active = slot < CPG && cell < g.n_cells;
-    int64_t node = 0;
-    bool live = false;
     if (active) {
-      const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
-      const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
-      const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
-      const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
-      bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
-      if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
-      node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
-      live = !bnd;
-      T rr[NT];
-#pragma unroll
-      for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
       if (copy_dst) {
 #pragma unroll
-        for (int t = 0; t < NT; ++t) copy_dst[t * g.n_nodes + node] = copy_src[t * g.n_nodes + node];
+        for (int t = 0; t < NT; ++t) copy_dst[t * g.n_nodes + node] = cur.cp[t];
       }
 #pragma unroll
       for (int m = 0; m < NT; ++m) {
@@ -460,7 +487,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
         const bool im_part = !is_real && ((m - mt.nreal) & 1);
         T v = 0;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[t];
+        for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * cur.rr[t];
         s_r[slot][m][a] = v;
       }
     }
@@ -528,6 +555,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
         tma_bulk_load(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage]);
       ++issued;
     }
+    cur = nxt;
   }
   // after a timeout: wait (bounded) for the copies still in flight before the CTA exits
   if (s_fail) {
@@ -556,8 +584,8 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
   if (!status || TmaCfg<DIM, N, NT, TI>::SMEM > (size_t)200 * 1024) {
     using C = AsmCfg<DIM, N, NT, TI>;
     const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
-    asm_apply_kernel<DIM, N, NT, T, TI><<<(unsigned)blocks, C::CPB * C::TPC, 0, s>>>(
-        r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd);
+    { const cudaError_t e_ = launch_k(asm_apply_kernel<DIM, N, NT, T, TI>, dim3((unsigned)blocks), dim3(C::CPB * C::TPC), 0, s, 
+        r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
   }
   using C = TmaCfg<DIM, N, NT, TI>;
@@ -575,11 +603,16 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
   }
   const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
   const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
-  k<<<(unsigned)grid, C::THREADS, C::SMEM, s>>>(r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status);
+  { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), C::SMEM, s, r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(int* status, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(status);
+  return cudaGetLastError();
+}
 
 int64_t asm_cell_stride(int dim, int n, int nt) { return cell_stride(dim == 3 ? n * n * n : n * n, nt); }
 

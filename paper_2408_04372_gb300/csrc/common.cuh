@@ -4,8 +4,34 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <utility>
 
 namespace stmg {
+
+// Programmatic dependent launch.  Kernels of the solve path start with pdl_wait(): launched with
+// the programmatic-serialisation attribute, a kernel may be scheduled while its predecessor drains,
+// and griddepcontrol.wait blocks until the predecessor grid has completed and its writes are
+// visible (without the attribute it returns at once).  pdl_trigger() lets the next kernel be
+// scheduled as soon as every CTA of this one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with programmatic stream serialisation (graph capture turns it into programmatic edges).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr int kMaxN = 5;    // p <= 4
 constexpr int STMG_DEVICE_TIMEOUT = 1;  // device status word: a bounded wait gave up

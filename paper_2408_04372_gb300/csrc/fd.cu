@@ -21,6 +21,8 @@ template <int N, int NT, typename T, int CPB>
 __global__ void __launch_bounds__(CPB * N * N)
 fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict__ rho_cell, GridDesc g, FDTab<T> fd,
                 ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
@@ -186,7 +188,7 @@ cudaError_t fd_t(const T* r, T* u, const T* rho, const GridDesc& g, const FDTab<
     attr = true;
   }
   const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
-  k<<<(unsigned)blocks, CPB * N * N, smem, s>>>(r, u, rho, g, fd, mt, cs, cd);
+  { const cudaError_t e_ = launch_k(k, dim3((unsigned)blocks), dim3(CPB * N * N), smem, s, r, u, rho, g, fd, mt, cs, cd); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 

@@ -53,6 +53,10 @@ cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const voi
                              const GridDesc& g, const ModeTab<T>& mt, const T* copy_src, T* copy_dst, int* status,
                              cudaStream_t s);
 
+// Test hook: a bounded device wait that cannot complete; about one second later *status holds
+// STMG_DEVICE_TIMEOUT.
+cudaError_t launch_wait_selftest(int* status, cudaStream_t s);
+
 // ---- fast diagonalisation local solves (fd.cu), 3D Cartesian cells ----
 template <typename T>
 cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho_cell, const GridDesc& g, const FDTab<T>& fd,
@@ -96,10 +100,11 @@ cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64
 // optionally w -= sum_j c[j] V_j, then s_j = V_j . w and/or s_nv = w . w; fin 0 writes s to out,
 // fin 1 the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = ||w||, out[nv+1] = 1/||w||.
 // partial: (K+1) x cgs_blocks() doubles; counter: one zero-initialised unsigned int per stream,
-// left at zero on return.
+// left at zero on return.  status (device int, may be NULL): with it, and 16-byte aligned w, V0 and
+// stride, the vectors arrive by bulk copies (TMA) and a timed-out wait is recorded there.
 cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                            double* out, cudaStream_t s);
+                            double* out, cudaStream_t s, int* status = nullptr);
 int cgs_blocks();
 // w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride)
 cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,

@@ -72,7 +72,8 @@ struct stmg_ctx {
   // FGMRES workspace
   int m = 30;
   int nvec = 0;
-  double* V = nullptr;   // (nvec) vectors
+  double* V = nullptr;   // (nvec) vectors, stride vld
+  int64_t vld = 0;       // stride of the Krylov basis: n0 rounded up to 32 (256-byte aligned vectors)
   double* Z = nullptr;   // (m) vectors
   double* partial = nullptr;        // per-block partial sums of the Gram-Schmidt passes
   unsigned int* counter = nullptr;  // arrival counter of those passes (zero between launches)
@@ -421,7 +422,7 @@ bool node_constrained(const Level& L, int64_t node) {
 // out[0] = x . x (device), one launch
 stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
   CK(launch_cgs_pass(nullptr, n, 0, const_cast<double*>(x), n, nullptr, 0, 0, 1, nullptr, 0, ctx->partial,
-                     ctx->counter, out, ctx->stream));
+                     ctx->counter, out, ctx->stream, ctx->status));
   ctx->launches += 1;
   return STMG_OK;
 }
@@ -429,13 +430,14 @@ stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
 // enqueue part: no host synchronisation (capturable).  Classical Gram-Schmidt twice in three
 // fused passes over the basis: h1 = V^T w ; w -= V h1, h2 = V^T w ; w -= V h2, ||w|| and the
 // column h1 + h2 ; then w /= ||w||.
-stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int nv, double* w, int64_t n) {
+stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, int nv, double* w, int64_t n) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
   double* d_out = ctx->dsm + 384;
-  CK(launch_cgs_pass(V0, n, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream));
-  CK(launch_cgs_pass(V0, n, nv, w, n, d_h1, 1, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream));
-  CK(launch_cgs_pass(V0, n, nv, w, n, d_h2, 1, 0, 1, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream));
+  int* st = ctx->status;
+  CK(launch_cgs_pass(V0, ld, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream, st));
+  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st));
+  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 1, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream, st));
   ctx->launches += 4;
   CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream));
   CK(cudaMemcpyAsync(ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
@@ -451,9 +453,9 @@ stmg_status orthogonalise_read(stmg_ctx* ctx, int nv, std::vector<double>& h, do
 
 // One Arnoldi/FGMRES orthogonalisation step (classical Gram-Schmidt, twice):
 // w <- w - V h, h = [V^T w]_1 + [V^T w]_2 ; hn = ||w|| ; w <- w / hn.  Host gets h (nv) and hn.
-stmg_status orthogonalise(stmg_ctx* ctx, const double* V0, int nv, double* w, int64_t n, std::vector<double>& h,
+stmg_status orthogonalise(stmg_ctx* ctx, const double* V0, int64_t ld, int nv, double* w, int64_t n, std::vector<double>& h,
                           double& hn) {
-  CKS(orthogonalise_enqueue(ctx, V0, nv, w, n));
+  CKS(orthogonalise_enqueue(ctx, V0, ld, nv, w, n));
   return orthogonalise_read(ctx, nv, h, hn);
 }
 
@@ -477,7 +479,8 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
   nr = std::sqrt(nr);
   for (auto& x : v0) x /= nr;
   std::vector<double*> V(steps + 1);
-  for (int j = 0; j <= steps; ++j) V[j] = ctx->V + (size_t)j * n;
+  const int64_t ld = (n + 31) / 32 * 32;  // 256-byte aligned basis vectors (bulk copies)
+  for (int j = 0; j <= steps; ++j) V[j] = ctx->V + (size_t)j * ld;
   CK(cudaMemcpyAsync(V[0], v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
   std::vector<double> H((steps + 1) * steps, 0.0);
   int m = steps;
@@ -488,7 +491,7 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
     CKS(op_apply<double>(ctx, L, z, V[j + 1]));
     std::vector<double> h;
     double hn = 0.0;
-    CKS(orthogonalise(ctx, V[0], j + 1, V[j + 1], n, h, hn));
+    CKS(orthogonalise(ctx, V[0], ld, j + 1, V[j + 1], n, h, hn));
     for (int i = 0; i <= j; ++i) H[i * steps + j] = h[i];
     H[(j + 1) * steps + j] = hn;
     if (hn <= 1e-14 * std::fabs(H[j * steps + j]) + 1e-300) { m = j + 1; break; }
@@ -510,6 +513,18 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
     return STMG_ERR_INTERNAL;
   }
   L.omega = 2.0 / (lmax + lmin);
+  return STMG_OK;
+}
+
+// Synchronises and reads the device status word (bounded waits that gave up set it).
+stmg_status check_device_status(stmg_ctx* ctx) {
+  int* h = reinterpret_cast<int*>(ctx->hsm + 510);
+  CK(cudaMemcpyAsync(h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (*h != 0) {
+    ctx->err = "a device wait for a bulk copy gave up (status word set); results of this call are invalid";
+    return STMG_ERR_TIMEOUT;
+  }
   return STMG_OK;
 }
 
@@ -732,6 +747,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (o.fgmres_restart <= 0) o.fgmres_restart = 30;
   if (o.fgmres_restart > 64) return invalid(ctx, "fgmres_restart must be <= 64");
   if (!(o.rtol > 0.0)) o.rtol = 1e-8;
+  if (!(o.atol >= 0.0)) return invalid(ctx, "atol must be >= 0");
   if (o.max_it <= 0) o.max_it = 200;
   if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
   if (o.outer_apply == 0) o.outer_apply = o.vcycle_precision == STMG_FP32 ? STMG_DF32 : STMG_FP64;
@@ -854,7 +870,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   const int64_t n0 = ctx->levels[0].size();
   ctx->m = o.fgmres_restart;
   ctx->nvec = std::max(ctx->m, 20) + 1;
-  CKS(dev_alloc(ctx, &ctx->V, (size_t)ctx->nvec * n0));
+  ctx->vld = (n0 + 31) / 32 * 32;
+  CKS(dev_alloc(ctx, &ctx->V, (size_t)ctx->nvec * ctx->vld));
   CKS(dev_alloc(ctx, &ctx->Z, (size_t)std::max(ctx->m, 1) * n0));
   CKS(dev_alloc(ctx, &ctx->partial, (size_t)cgs_blocks() * 80));
   CKS(dev_alloc(ctx, &ctx->counter, 1));
@@ -906,6 +923,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     if (o.omega) ctx->levels[li].omega = o.omega[li];
     else CKS(estimate_omega(ctx, (int)li));
   }
+  CKS(check_device_status(ctx));
   CK(cudaStreamSynchronize(ctx->stream));
   return STMG_OK;
 }
@@ -940,9 +958,9 @@ stmg_status precondition(stmg_ctx* ctx, const double* v, double* z) {
 stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
   Level& L = ctx->levels[0];
   const int64_t n = L.size();
-  double* v = ctx->V + (size_t)j * n;
+  double* v = ctx->V + (size_t)j * ctx->vld;
   double* z = ctx->Z + (size_t)j * n;
-  double* w = ctx->V + (size_t)(j + 1) * n;
+  double* w = ctx->V + (size_t)(j + 1) * ctx->vld;
   if (ctx->opt.vcycle_precision == STMG_FP32) {
     CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
     if (in_capture) CKS(vcycle_level<float>(ctx, 0));
@@ -959,7 +977,7 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
     CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     CKS(op_apply<double>(ctx, L, z, w));
   }
-  return orthogonalise_enqueue(ctx, ctx->V, j + 1, w, n);
+  return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n);
 }
 
 stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
@@ -998,18 +1016,6 @@ stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
   return STMG_OK;
 }
 
-// Synchronises and reads the device status word (bounded waits that gave up set it).
-stmg_status check_device_status(stmg_ctx* ctx) {
-  int* h = reinterpret_cast<int*>(ctx->hsm + 510);
-  CK(cudaMemcpyAsync(h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (*h != 0) {
-    ctx->err = "a device wait for a bulk copy gave up (status word set); results of this call are invalid";
-    return STMG_ERR_TIMEOUT;
-  }
-  return STMG_OK;
-}
-
 stmg_status norm2(stmg_ctx* ctx, const double* x, int64_t n, double& out) {
   CKS(dot_self(ctx, x, n, ctx->dsm + 448));
   CK(cudaMemcpyAsync(ctx->hsm + 448, ctx->dsm + 448, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1022,7 +1028,6 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
   Level& L = ctx->levels[0];
   const int64_t n = L.size();
   const int m = ctx->m;
-  const double rtol = ctx->opt.rtol;
   double bnorm = 0.0;
   CKS(norm2(ctx, b, n, bnorm));
   stmg_solve_stats s{};
@@ -1033,8 +1038,10 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     return STMG_OK;
   }
   if (!std::isfinite(bnorm)) { ctx->err = "right-hand side is not finite"; return STMG_ERR_NONFINITE; }
+  // stopping rule: ||b - S x|| <= max(rtol ||b||, atol) (the absolute part only when atol > 0)
+  const double target = std::max(ctx->opt.rtol * bnorm, ctx->opt.atol);
   std::vector<double*> V(m + 1), Z(m);
-  for (int j = 0; j <= m; ++j) V[j] = ctx->V + (size_t)j * n;
+  for (int j = 0; j <= m; ++j) V[j] = ctx->V + (size_t)j * ctx->vld;
   for (int j = 0; j < m; ++j) Z[j] = ctx->Z + (size_t)j * n;
   int its = 0;
   bool first = true;
@@ -1046,7 +1053,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     if (!std::isfinite(beta)) { ctx->err = "residual is not finite"; return STMG_ERR_NONFINITE; }
     if (first) { s.initial_rel_residual = beta / bnorm; first = false; }
     s.rel_residual = beta / bnorm;
-    if (beta <= rtol * bnorm) break;
+    if (beta <= target) break;
     if (its >= ctx->opt.max_it) { result = STMG_ERR_NOT_CONVERGED; break; }
     if (its > 0) s.restarts++;
     CK(launch_axpby(0.0, V[0], 1.0 / beta, V[0], n, ctx->stream));
@@ -1081,7 +1088,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
       ++its;
       jend = j + 1;
       if (hn == 0.0) { breakdown = true; break; }
-      if (std::fabs(g[j + 1]) <= rtol * bnorm || its >= ctx->opt.max_it) break;
+      if (std::fabs(g[j + 1]) <= target || its >= ctx->opt.max_it) break;
     }
     std::vector<double> y(jend, 0.0);
     for (int i = jend - 1; i >= 0; --i) {
@@ -1402,7 +1409,10 @@ stmg_status stmg_rhs(stmg_ctx* ctx, const double* f, const double* f0, const dou
 stmg_status stmg_solve(stmg_ctx* ctx, const double* rhs, double* u, stmg_solve_stats* stats) {
   StreamJoin join_(ctx);
   if (!ctx || !rhs || !u) return STMG_ERR_INVALID_ARG;
-  return solve_impl(ctx, rhs, u, stats);
+  const stmg_status s = solve_impl(ctx, rhs, u, stats);
+  // a bounded device wait that gave up invalidates every result of the call, whatever path it took
+  if (s != STMG_ERR_CUDA && check_device_status(ctx) == STMG_ERR_TIMEOUT) return STMG_ERR_TIMEOUT;
+  return s;
 }
 
 stmg_status stmg_wave_velocity(stmg_ctx* ctx, const double* u, const double* u0, const double* v0, double* v) {
@@ -1714,6 +1724,14 @@ stmg_status stmg_solve_slab_host_learned(stmg_ctx* ctx, stmg_net* net, const dou
   CK(cudaMemcpyAsync(u, d_u, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return s;
+}
+
+stmg_status stmg_selftest_device_timeout(stmg_ctx* ctx) {
+  if (!ctx) return STMG_ERR_INVALID_ARG;
+  StreamJoin join_(ctx);
+  CK(launch_wait_selftest(ctx->status, ctx->stream));
+  ctx->launches += 1;
+  return check_device_status(ctx);
 }
 
 stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {

@@ -42,6 +42,8 @@ template <typename T>
 __global__ void gather_axis_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2, int nt,
                                    int axis, int n_out, const int* __restrict__ idx, const double* __restrict__ w,
                                    int R, int accumulate, SideJob<T> side) {
+  pdl_wait();
+  pdl_trigger();
   const int o0 = axis == 0 ? n_out : d0, o1 = axis == 1 ? n_out : d1, o2 = axis == 2 ? n_out : d2;
   const int64_t total = (int64_t)nt * o2 * o1 * o0;
   const int64_t sin_ = axis == 0 ? 1 : (axis == 1 ? d0 : (int64_t)d0 * d1);
@@ -79,6 +81,8 @@ template <typename T, int R, int DIM>
 __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ out, int nt, int nin, int nout,
                                     const int* __restrict__ idx, const double* __restrict__ w, int accumulate,
                                     SideJob<T> side) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t per = DIM == 3 ? (int64_t)nout * nout * nout : (int64_t)nout * nout;
   const int64_t per_in = DIM == 3 ? (int64_t)nin * nin * nin : (int64_t)nin * nin;
   const int64_t total = per * nt;
@@ -139,7 +143,7 @@ cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, c
   if (transfer_fused(terms, nout_total)) {  // R <= 3 in 3D, R <= 5 in 2D
     const int nb = blocks(nout_total);
 #define STMG_FUSED(RR, DD) \
-  gather_fused_kernel<T, RR, DD><<<nb, 256, 0, s>>>(in, out, nt, nin, nout, idx, w, accumulate, side)
+  return launch_k(gather_fused_kernel<T, RR, DD>, dim3(nb), dim3(256), 0, s, in, out, nt, nin, nout, idx, w, accumulate, side)
     if (dim == 3) {
       if (R == 1) STMG_FUSED(1, 3); else if (R == 2) STMG_FUSED(2, 3); else STMG_FUSED(3, 3);
     } else {
@@ -151,16 +155,16 @@ cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, c
   }
   if (dim == 2) {
     const int64_t n1 = (int64_t)nt * nin * nout;
-    gather_axis_kernel<T><<<blocks(n1), 256, 0, s>>>(in, t1, nin, nin, 1, nt, 0, nout, idx, w, R, 0, none);
+    { const cudaError_t e_ = launch_k(gather_axis_kernel<T>, dim3(blocks(n1)), dim3(256), 0, s, in, t1, nin, nin, 1, nt, 0, nout, idx, w, R, 0, none); if (e_ != cudaSuccess) return e_; }
     const int64_t n2 = (int64_t)nt * nout * nout;
-    gather_axis_kernel<T><<<blocks(n2), 256, 0, s>>>(t1, out, nout, nin, 1, nt, 1, nout, idx, w, R, accumulate, side);
+    { const cudaError_t e_ = launch_k(gather_axis_kernel<T>, dim3(blocks(n2)), dim3(256), 0, s, t1, out, nout, nin, 1, nt, 1, nout, idx, w, R, accumulate, side); if (e_ != cudaSuccess) return e_; }
   } else {
     const int64_t n1 = (int64_t)nt * nin * nin * nout;
-    gather_axis_kernel<T><<<blocks(n1), 256, 0, s>>>(in, t1, nin, nin, nin, nt, 0, nout, idx, w, R, 0, none);
+    { const cudaError_t e_ = launch_k(gather_axis_kernel<T>, dim3(blocks(n1)), dim3(256), 0, s, in, t1, nin, nin, nin, nt, 0, nout, idx, w, R, 0, none); if (e_ != cudaSuccess) return e_; }
     const int64_t n2 = (int64_t)nt * nin * nout * nout;
-    gather_axis_kernel<T><<<blocks(n2), 256, 0, s>>>(t1, t2, nout, nin, nin, nt, 1, nout, idx, w, R, 0, none);
+    { const cudaError_t e_ = launch_k(gather_axis_kernel<T>, dim3(blocks(n2)), dim3(256), 0, s, t1, t2, nout, nin, nin, nt, 1, nout, idx, w, R, 0, none); if (e_ != cudaSuccess) return e_; }
     const int64_t n3 = (int64_t)nt * nout * nout * nout;
-    gather_axis_kernel<T><<<blocks(n3), 256, 0, s>>>(t2, out, nout, nout, nin, nt, 2, nout, idx, w, R, accumulate, side);
+    { const cudaError_t e_ = launch_k(gather_axis_kernel<T>, dim3(blocks(n3)), dim3(256), 0, s, t2, out, nout, nout, nin, nt, 2, nout, idx, w, R, accumulate, side); if (e_ != cudaSuccess) return e_; }
   }
   return cudaGetLastError();
 }
@@ -176,6 +180,8 @@ __device__ inline bool node_on_boundary(int64_t node, const GridDesc& g) {
 template <typename T>
 __global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict__ ec, GridDesc g, TimeTransfer tt,
                                        SideJob<T> side) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
        node += (int64_t)gridDim.x * blockDim.x) {
     for (int i = 0; i < tt.ntf; ++i) side.run(i * g.n_nodes + node);
@@ -193,6 +199,8 @@ __global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict_
 template <typename T>
 __global__ void restrict_time_kernel(T* __restrict__ rc, const T* __restrict__ rf, GridDesc g, TimeTransfer tt,
                                      SideJob<T> side) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
        node += (int64_t)gridDim.x * blockDim.x) {
     for (int j = 0; j < tt.ntc; ++j) side.run(j * g.n_nodes + node);
@@ -232,7 +240,7 @@ cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const
   SideJob<T> side;
   side.copy_src = copy_src;
   side.copy_dst = copy_dst;
-  prolong_time_add_kernel<T><<<grid_blocks(g.n_nodes), 256, 0, s>>>(uf, ec, g, t, side);
+  { const cudaError_t e_ = launch_k(prolong_time_add_kernel<T>, dim3(grid_blocks(g.n_nodes)), dim3(256), 0, s, uf, ec, g, t, side); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 template <typename T>
@@ -240,7 +248,7 @@ cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const Ti
                                  cudaStream_t s) {
   SideJob<T> side;
   side.zero_dst = zero_dst;
-  restrict_time_kernel<T><<<grid_blocks(g.n_nodes), 256, 0, s>>>(rc, rf, g, t, side);
+  { const cudaError_t e_ = launch_k(restrict_time_kernel<T>, dim3(grid_blocks(g.n_nodes)), dim3(256), 0, s, rc, rf, g, t, side); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 

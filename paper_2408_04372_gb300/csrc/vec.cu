@@ -21,16 +21,22 @@ inline int grid_blocks(int64_t total) {
 
 template <typename Tin, typename Tout>
 __global__ void convert_kernel(const Tin* __restrict__ x, Tout* __restrict__ y, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (Tout)x[i];
 }
 
 __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 
 __global__ void scale_by_device_kernel(double* __restrict__ x, const double* __restrict__ sc, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   const double s = sc[0];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= s;
@@ -51,6 +57,8 @@ __global__ void __launch_bounds__(kCgsThreads)
 cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
                 const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev, int fin,
                 double* __restrict__ partial, unsigned int* __restrict__ counter, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[kCgsThreads / 32][K + 1];
   __shared__ double cs[K];
   __shared__ bool last;
@@ -130,8 +138,197 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// ---- the same pass fed by bulk copies (TMA) ----
+// Each CTA walks chunks of E elements (chunk c, c + gridDim.x, ...); per chunk one bulk copy per
+// basis vector and one for w land in a shared-memory stage (S stages in flight, mbarrier
+// completion).  Only whole 16-byte units are copied; an odd last element is read directly, so no
+// copy runs past the end of a vector.  Waits are bounded: after kCgsWaitNs, or at once when
+// *status is already set, the CTA records STMG_DEVICE_TIMEOUT, drains its copies and leaves the
+// pass (the results are then invalid and the caller reports the status).
+constexpr uint64_t kCgsWaitNs = 1000000000ull;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, const int* status) {
+  const uint64_t t0 = now_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (done) return true;
+    if ((it & 63) == 63) {
+      if (now_ns() - t0 > kCgsWaitNs) return false;
+      if (status && *reinterpret_cast<const volatile int*>(status) != 0) return false;
+    }
+  }
+}
+
+template <int K> struct CgsTma;
+template <> struct CgsTma<4> { static constexpr int E = 512, S = 4, BPS = 2; };
+template <> struct CgsTma<8> { static constexpr int E = 512, S = 3, BPS = 2; };
+template <> struct CgsTma<16> { static constexpr int E = 512, S = 2, BPS = 1; };
+template <> struct CgsTma<32> { static constexpr int E = 128, S = 3, BPS = 1; };
+template <> struct CgsTma<64> { static constexpr int E = 64, S = 3, BPS = 1; };
+template <int K> constexpr size_t cgs_tma_smem() { return (size_t)CgsTma<K>::S * (K + 1) * CgsTma<K>::E * sizeof(double); }
+
+template <int K>
+__global__ void __launch_bounds__(kCgsThreads)
+cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
+                    const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev,
+                    int fin, double* __restrict__ partial, unsigned int* __restrict__ counter,
+                    double* __restrict__ out, int* status) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int E = CgsTma<K>::E, S = CgsTma<K>::S;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[S];
+  __shared__ double red[kCgsThreads / 32][K + 1];
+  __shared__ double cs[K];
+  __shared__ bool last;
+  __shared__ int fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t stage_bytes = (size_t)(K + 1) * E * sizeof(double);
+  const int64_t nch = (n + E - 1) / E;
+  for (int j = tid; j < K; j += blockDim.x) cs[j] = (sub && j < nv) ? c[j] : 0.0;
+  if (tid == 0) {
+    fail = *reinterpret_cast<const volatile int*>(status) != 0;
+    for (int st = 0; st < S; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[st])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto main_bytes = [&](int64_t ch) -> uint32_t {
+    const int64_t ne = n - ch * E < E ? n - ch * E : E;
+    return (uint32_t)((ne * (int64_t)sizeof(double)) / 16 * 16);
+  };
+  auto issue = [&](int64_t ch, int st) {  // thread 0
+    const uint32_t bytes = main_bytes(ch);
+    unsigned char* dst = smem_raw + (size_t)st * stage_bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(&bar[st])), "r"(bytes * (uint32_t)(nv + 1)) : "memory");
+    if (bytes == 0) return;
+    for (int j = 0; j <= nv; ++j) {
+      const double* src = (j < nv ? V0 + j * stride : w) + ch * E;
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   ::"r"(smem_addr(dst + (size_t)j * E * sizeof(double))), "l"(src), "r"(bytes),
+                   "r"(smem_addr(&bar[st])) : "memory");
+    }
+  };
+  double acc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) acc[j] = 0.0;
+  int64_t issued = 0, k = 0;
+  if (!fail) {
+    if (tid == 0)
+      for (int st = 0; st < S; ++st) {
+        const int64_t ch = blockIdx.x + (int64_t)st * gridDim.x;
+        if (ch < nch) issue(ch, st);
+      }
+    for (int st = 0; st < S; ++st)
+      if (blockIdx.x + (int64_t)st * gridDim.x < nch) ++issued;
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x, ++k) {
+      const int st = (int)(k % S);
+      if (!bar_wait(&bar[st], (uint32_t)((k / S) & 1), status)) {
+        atomicExch(status, STMG_DEVICE_TIMEOUT);
+        fail = 1;
+      }
+      __syncthreads();
+      if (fail) break;
+      const double* buf = reinterpret_cast<const double*>(smem_raw + (size_t)st * stage_bytes);
+      const int64_t e0 = ch * E;
+      const int ne = (int)(n - e0 < E ? n - e0 : E);
+      const int nin = (int)(main_bytes(ch) / sizeof(double));  // elements that came by bulk copy
+      for (int e = tid; e < ne; e += kCgsThreads) {
+        const bool in = e < nin;
+        // basis entries straight from the stage (read twice rather than kept in registers)
+        auto vj = [&](int j) { return in ? buf[j * E + e] : V0[j * stride + e0 + e]; };
+        double wi = in ? buf[nv * E + e] : w[e0 + e];
+        if (sub) {
+          double sv = 0.0;
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (j < nv) sv += cs[j] * vj(j);
+          wi -= sv;
+          w[e0 + e] = wi;
+        }
+        if (dot) {
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (j < nv) acc[j] += vj(j) * wi;
+        }
+        acc[K] += wi * wi;
+      }
+      __syncthreads();  // stage free again
+      const int64_t nx = ch + (int64_t)S * gridDim.x;
+      if (nx < nch) {
+        if (tid == 0) issue(nx, st);
+        ++issued;
+      }
+    }
+    if (fail) {  // drain the copies still in flight, then leave without a result
+      for (int64_t q = k; q < issued; ++q) bar_wait(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
+      return;
+    }
+  } else {
+    return;
+  }
+  // block partials, then the last block sums them in block order (as in cgs_pass_kernel)
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = acc[j];
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) red[warp][j] = x;
+    }
+  }
+  __syncthreads();
+  const int nb = gridDim.x;
+  for (int j = tid; j <= K; j += blockDim.x) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = 0.0;
+      for (int wv = 0; wv < kCgsThreads / 32; ++wv) x += red[wv][j];
+      partial[(int64_t)j * nb + blockIdx.x] = x;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double tot[K + 1];
+  for (int j = warp; j <= K; j += kCgsThreads / 32) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = 0.0;
+      for (int b = lane; b < nb; b += 32) x += __ldcg(partial + (int64_t)j * nb + b);
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) tot[j] = x;
+    }
+  }
+  __syncthreads();
+  if (fin == 0) {
+    for (int j = tid; j < nv; j += blockDim.x)
+      if (dot) out[j] = tot[j];
+    if (norm && tid == 0) out[nv] = tot[K];
+  } else {
+    for (int j = tid; j < nv; j += blockDim.x) out[j] = h_prev[j] + cs[j];
+    if (tid == 0) {
+      const double hn = sqrt(fmax(tot[K], 0.0));
+      out[nv] = hn;
+      out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    }
+  }
+  if (tid == 0) *counter = 0u;
+}
+
 __global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V0, int64_t stride,
                                   const double* __restrict__ h, int nv, double sign, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[kMaxVec];
   for (int j = threadIdx.x; j < nv; j += blockDim.x) sh[j] = h[j];
   __syncthreads();
@@ -143,6 +340,8 @@ __global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restri
 }
 
 __global__ void broadcast_time_kernel(const double* __restrict__ u0, double* __restrict__ u, int nt, int64_t nn) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = u0[i];
     for (int t = 0; t < nt; ++t) u[t * nn + i] = v;
@@ -152,6 +351,8 @@ __global__ void broadcast_time_kernel(const double* __restrict__ u0, double* __r
 struct MixTab { const double* x[8]; double C[kMaxNT][8]; };
 
 __global__ void time_mix_kernel(MixTab m, int nin, int nout, double* __restrict__ y, int64_t nn, int accumulate) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
     double xv[8];
     for (int j = 0; j < nin; ++j) xv[j] = m.x[j][i];
@@ -166,6 +367,8 @@ __global__ void time_mix_kernel(MixTab m, int nin, int nout, double* __restrict_
 template <typename T>
 __global__ void coarse_solve_kernel(const T* __restrict__ f, T* __restrict__ u, const T* __restrict__ inv,
                                     const int64_t* __restrict__ map, int n) {
+  pdl_wait();
+  pdl_trigger();
   // inv stored column-major: inv[j * n + i]
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     T s = 0;
@@ -175,6 +378,8 @@ __global__ void coarse_solve_kernel(const T* __restrict__ f, T* __restrict__ u, 
 }
 
 __global__ void zero_constrained_kernel(double* __restrict__ y, GridDesc g, int nt) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
        node += (int64_t)gridDim.x * blockDim.x) {
     const int gx = (int)(node % g.nn1);
@@ -192,7 +397,7 @@ __global__ void zero_constrained_kernel(double* __restrict__ y, GridDesc g, int 
 
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s) {
-  convert_kernel<Tin, Tout><<<grid_blocks(n), 256, 0, s>>>(x, y, n);
+  { const cudaError_t e_ = launch_k(convert_kernel<Tin, Tout>, dim3(grid_blocks(n)), dim3(256), 0, s, x, y, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
@@ -200,24 +405,53 @@ template cudaError_t launch_convert<float, double>(const float*, double*, int64_
 template cudaError_t launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
 
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s) {
-  axpby_kernel<<<grid_blocks(n), 256, 0, s>>>(a, x, b, y, n);
+  { const cudaError_t e_ = launch_k(axpby_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, a, x, b, y, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaStream_t s) {
-  scale_by_device_kernel<<<grid_blocks(n), 256, 0, s>>>(x, sc, n);
+  { const cudaError_t e_ = launch_k(scale_by_device_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, x, sc, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 int cgs_blocks() { return kCgsBlocks; }
 
+template <int K>
+cudaError_t launch_cgs_tma(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
+                           int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
+                           double* out, int* status, cudaStream_t s) {
+  static bool attr = false;
+  auto k = cgs_pass_tma_kernel<K>;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_tma_smem<K>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  { const cudaError_t e_ = launch_k(k, dim3(152 * CgsTma<K>::BPS), dim3(kCgsThreads), cgs_tma_smem<K>(), s, V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin,
+                                                                 partial, counter, out, status); if (e_ != cudaSuccess) return e_; }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                            double* out, cudaStream_t s) {
+                            double* out, cudaStream_t s, int* status) {
   if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+  // bulk copies need 16-byte aligned sources: w, V0 and the stride between basis vectors
+  const bool aligned = ((uintptr_t)w % 16 == 0) && (nv == 0 || (((uintptr_t)V0 % 16 == 0) && stride % 2 == 0));
+  if (status && aligned) {
+#define STMG_CGS_TMA(KK) \
+  return launch_cgs_tma<KK>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter, out, status, s)
+    if (nv <= 4) STMG_CGS_TMA(4);
+    if (nv <= 8) STMG_CGS_TMA(8);
+    if (nv <= 16) STMG_CGS_TMA(16);
+    if (nv <= 32) STMG_CGS_TMA(32);
+    STMG_CGS_TMA(64);
+#undef STMG_CGS_TMA
+  }
   // one wave: blocks per SM as the register use of each width allows (4, 4, 2, 1, 1)
 #define STMG_CGS(KK, BPS) \
-  cgs_pass_kernel<KK><<<152 * (BPS), kCgsThreads, 0, s>>>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter, out)
+  return launch_k(cgs_pass_kernel<KK>, dim3(152 * (BPS)), dim3(kCgsThreads), 0, s, V0, stride, nv, w, n, c, sub, dot, \
+                  norm, h_prev, fin, partial, counter, out)
   if (nv <= 4) STMG_CGS(4, 4);
   else if (nv <= 8) STMG_CGS(8, 4);
   else if (nv <= 16) STMG_CGS(16, 2);
@@ -230,12 +464,12 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
 cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,
                               int64_t n, cudaStream_t s) {
   if (nv > kMaxVec) return cudaErrorInvalidValue;
-  multi_axpy_kernel<<<grid_blocks(n), 256, 0, s>>>(w, V0, stride, h, nv, sign, n);
+  { const cudaError_t e_ = launch_k(multi_axpy_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, w, V0, stride, h, nv, sign, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_broadcast_time(const double* u0, double* u, int nt, int64_t nn, cudaStream_t s) {
-  broadcast_time_kernel<<<grid_blocks(nn), 256, 0, s>>>(u0, u, nt, nn);
+  { const cudaError_t e_ = launch_k(broadcast_time_kernel, dim3(grid_blocks(nn)), dim3(256), 0, s, u0, u, nt, nn); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -246,7 +480,7 @@ cudaError_t launch_time_mix(const double* const* xs, int nin, const double* C, i
   for (int j = 0; j < nin; ++j) m.x[j] = xs[j];
   for (int t = 0; t < nout; ++t)
     for (int j = 0; j < nin; ++j) m.C[t][j] = C[t * nin + j];
-  time_mix_kernel<<<grid_blocks(nn), 256, 0, s>>>(m, nin, nout, y, nn, accumulate);
+  { const cudaError_t e_ = launch_k(time_mix_kernel, dim3(grid_blocks(nn)), dim3(256), 0, s, m, nin, nout, y, nn, accumulate); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -254,7 +488,7 @@ template <typename T>
 cudaError_t launch_coarse_solve(const T* f, T* u, const T* inv, const int64_t* map, int n, int64_t total,
                                 cudaStream_t s) {
   (void)total;
-  coarse_solve_kernel<T><<<(n + 127) / 128, 128, 0, s>>>(f, u, inv, map, n);
+  { const cudaError_t e_ = launch_k(coarse_solve_kernel<T>, dim3((n + 127) / 128), dim3(128), 0, s, f, u, inv, map, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(const float*, float*, const float*, const int64_t*, int, int64_t,
@@ -263,7 +497,7 @@ template cudaError_t launch_coarse_solve<double>(const double*, double*, const d
                                                  cudaStream_t);
 
 cudaError_t launch_zero_constrained(double* y, const GridDesc& g, int nt, cudaStream_t s) {
-  zero_constrained_kernel<<<grid_blocks(g.n_nodes), 256, 0, s>>>(y, g, nt);
+  { const cudaError_t e_ = launch_k(zero_constrained_kernel, dim3(grid_blocks(g.n_nodes)), dim3(256), 0, s, y, g, nt); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
