@@ -170,8 +170,8 @@ def run_kernel_only(args):
                   "applydf": (stmg.KERNEL_APPLY, stmg.DF32),
                   "asm32": (stmg.KERNEL_ASM, stmg.FP32), "asm64": (stmg.KERNEL_ASM, stmg.FP64),
                   "vcycle32": (stmg.KERNEL_VCYCLE, stmg.FP32), "vcycle64": (stmg.KERNEL_VCYCLE, stmg.FP64)}[args.only_kernel]
-    ms = ctx.time_kernel(kind, 0, prec, reps=args.steps)
-    print(json.dumps({"kernel": args.only_kernel, "avg_launch_ms": ms, "workload": wl["name"]}))
+    ms = ctx.time_kernel(kind, args.level, prec, reps=args.steps)
+    print(json.dumps({"kernel": args.only_kernel, "level": args.level, "avg_launch_ms": ms, "workload": wl["name"]}))
     ctx.close()
     return 0
 
@@ -636,6 +636,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
+    ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")
     args = ap.parse_args()
     if args.only_kernel:
         return run_kernel_only(args)

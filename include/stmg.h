@@ -109,7 +109,12 @@ typedef struct {
                               the FP32 V-cycle, else FP64].  Residuals b - S x always use FP64. */
   double atol;             /* absolute residual target: stmg_solve stops at ||rhs - S u||_2 <=
                               max(rtol ||rhs||_2, atol) [0: relative test only] */
+  int space_coarsening;    /* spatial levels of the hierarchy: STMG_COARSEN_P_THEN_H lowers p one by one
+                              down to 1, then halves the cells; STMG_COARSEN_H keeps p and halves the
+                              cells; time coarsening (k) follows either way [P_THEN_H] */
 } stmg_options;
+
+enum { STMG_COARSEN_P_THEN_H = 0, STMG_COARSEN_H = 1 };
 
 typedef struct {
   int iterations;          /* FGMRES iterations (= V-cycles) */

@@ -47,10 +47,12 @@ class LevelSpec:
     k: int
 
 
-def level_sequence(p: int, N: int, k: int, scheme: str) -> list[LevelSpec]:
-    """Fine-to-coarse list of (p, N, k)."""
+def level_sequence(p: int, N: int, k: int, scheme: str, p_coarsening: bool = True) -> list[LevelSpec]:
+    """Fine-to-coarse list of (p, N, k): space first, then time (Algorithm mg-sequence).  With
+    p_coarsening the space levels lower p one by one down to 1 before halving the cells; without it
+    they keep p (h-multigrid only)."""
     seq = [LevelSpec(p, N, k)]
-    while seq[-1].p > 1:
+    while p_coarsening and seq[-1].p > 1:
         s = seq[-1]
         seq.append(LevelSpec(s.p - 1, s.N, s.k))
     while seq[-1].N % 2 == 0 and seq[-1].N // 2 >= 2:
@@ -190,8 +192,8 @@ class Hierarchy:
     """All levels of the STMG V-cycle for one slab problem (finest level first)."""
 
     def __init__(self, dim, N, p, k, pde, scheme, tau, vertices, rho_cell=None, rho_qp=None,
-                 omegas=None, estimate=True):
-        self.specs = level_sequence(p, N, k, scheme)
+                 omegas=None, estimate=True, p_coarsening=True):
+        self.specs = level_sequence(p, N, k, scheme, p_coarsening)
         self.pde, self.scheme = pde, scheme
         fine = Grid(N, dim, p, vertices)
         if rho_qp is None:

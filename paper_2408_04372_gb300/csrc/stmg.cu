@@ -138,9 +138,13 @@ stmg_status invalid(stmg_ctx* ctx, const std::string& msg) {
 
 struct Spec { int p, N, k; };
 
-std::vector<Spec> level_sequence(int p, int N, int k, int scheme) {
+// Coarsening in space first, then in time (Algorithm mg-sequence, Section 3.2).  p_coarsening: the
+// space levels first lower p one by one down to 1, then halve the cells; otherwise they keep p and
+// only halve the cells (h-multigrid).
+std::vector<Spec> level_sequence(int p, int N, int k, int scheme, bool p_coarsening) {
   std::vector<Spec> s{{p, N, k}};
-  while (s.back().p > 1) s.push_back({s.back().p - 1, s.back().N, s.back().k});
+  if (p_coarsening)
+    while (s.back().p > 1) s.push_back({s.back().p - 1, s.back().N, s.back().k});
   while (s.back().N % 2 == 0 && s.back().N / 2 >= 2) s.push_back({s.back().p, s.back().N / 2, s.back().k});
   const int kmin = scheme == STMG_DG ? 0 : 1;
   while (s.back().k > kmin) s.push_back({s.back().p, s.back().N, s.back().k - 1});
@@ -748,6 +752,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (o.fgmres_restart > 64) return invalid(ctx, "fgmres_restart must be <= 64");
   if (!(o.rtol > 0.0)) o.rtol = 1e-8;
   if (!(o.atol >= 0.0)) return invalid(ctx, "atol must be >= 0");
+  if (o.space_coarsening != STMG_COARSEN_P_THEN_H && o.space_coarsening != STMG_COARSEN_H)
+    return invalid(ctx, "space_coarsening out of range");
   if (o.max_it <= 0) o.max_it = 200;
   if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
   if (o.outer_apply == 0) o.outer_apply = o.vcycle_precision == STMG_FP32 ? STMG_DF32 : STMG_FP64;
@@ -790,7 +796,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     }
     for (double v : rho_f) if (!(v > 0.0) || !std::isfinite(v)) return invalid(ctx, "coefficient must be positive and finite");
   }
-  std::vector<Spec> seq = level_sequence(pr->p, N, pr->k, pr->time_scheme);
+  std::vector<Spec> seq = level_sequence(pr->p, N, pr->k, pr->time_scheme, o.space_coarsening == STMG_COARSEN_P_THEN_H);
   ctx->levels.resize(seq.size());
   for (size_t li = 0; li < seq.size(); ++li) {
     Level& L = ctx->levels[li];

@@ -142,6 +142,26 @@ def test_vcycle(env, case):
         ctx.close()
 
 
+@pytest.mark.parametrize("case", CASES[:3], ids=lambda c: c.name)
+def test_vcycle_with_h_coarsening_only(env, case):
+    """Algorithm mg-sequence with spatial levels that keep p (h-multigrid), then time levels."""
+    torch, stmg = env
+    from oracle import mg
+    H = mg.Hierarchy(case.dim, case.N, case.p, case.k, case.pde, case.scheme, case.tau, case.vertices(),
+                     rho_cell=case.rho_cell(), p_coarsening=False)
+    prob = H.levels[0].prob
+    r = _rand(prob.n, 610, prob.bmask_full)
+    ref = H.vcycle(r)
+    ctx = make_context(stmg, case, H, vcycle_precision=stmg.FP64, space_coarsening=stmg.COARSEN_H)
+    assert ctx.n_levels == len(H.levels)
+    for li, lev in enumerate(H.levels[:-1]):
+        assert ctx.level_info(li)["p"] == case.p
+    e = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.from_numpy(r).cuda(), e)
+    assert rel_err(e.cpu().numpy(), ref) < 1e-9, case.name
+    ctx.close()
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
 def test_solve_matches_direct_solution(env, case):
     torch, stmg = env

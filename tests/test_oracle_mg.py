@@ -12,6 +12,9 @@ def test_level_sequence_space_then_time():
     assert seq == [(2, 32, 2), (1, 32, 2), (1, 16, 2), (1, 8, 2), (1, 4, 2), (1, 2, 2), (1, 2, 1), (1, 2, 0)]
     seq = [(s.p, s.N, s.k) for s in mg.level_sequence(3, 24, 2, "cgp")]
     assert seq == [(3, 24, 2), (2, 24, 2), (1, 24, 2), (1, 12, 2), (1, 6, 2), (1, 3, 2), (1, 3, 1)]
+    # spatial levels that keep p (h-multigrid only), then time
+    seq = [(s.p, s.N, s.k) for s in mg.level_sequence(2, 32, 2, "dg", p_coarsening=False)]
+    assert seq == [(2, 32, 2), (2, 16, 2), (2, 8, 2), (2, 4, 2), (2, 2, 2), (2, 2, 1), (2, 2, 0)]
 
 
 @pytest.mark.parametrize("pf,Nf,pc,Nc", [(2, 4, 1, 4), (3, 3, 2, 3), (1, 8, 1, 4), (2, 4, 2, 2)])
