@@ -200,7 +200,8 @@ def run_ours(args):
     vprec = stmg.FP64 if args.plain else stmg.FP32
     inv_prec = {"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64}[args.inverse] if not args.plain else stmg.FP64
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
-                       vcycle_precision=vprec, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200)
+                       vcycle_precision=vprec, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
+                       coarse_max_dofs=args.coarse_max_dofs)
     nt, nn = ctx.nt, ctx.n_nodes
     n = nt * nn
     X = ctx.node_coords()
@@ -307,7 +308,8 @@ def run_ours(args):
             compare["mixed_previous_slab_guess"] = {"value": dofs_per_step * k2 / (t_m / 1e3), "unit": UNIT,
                                                     "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_m]))}
         ctx64 = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
-                             vcycle_precision=stmg.FP64, rtol=1e-8, restart=30, max_it=200)
+                             vcycle_precision=stmg.FP64, rtol=1e-8, restart=30, max_it=200,
+                             coarse_max_dofs=args.coarse_max_dofs)
         def plain(s):
             prev_end = sols[s][(nt - 1) * nn:]
             ctx64.rhs(F[s], rhs, u0=prev_end)
@@ -395,7 +397,10 @@ def run_ours(args):
                                      f"{args.inverse.upper()} Schwarz inverses",
                        "slabs_timed": f"{slab_of(args.warmup)}..{slab_of(args.warmup + args.steps - 1)} (held out)"
                        if use_net else "from slab 0",
-                       "parallelism": f"replicas{world}", "l2": "working set > L2 (inverses alone 0.29 GB)",
+                       "parallelism": f"replicas{world}", "l2": "working set > L2 (inverses alone 0.15 GB in BF16)",
+                       "levels": ctx.n_levels,
+                       "coarsest": (f"first level with <= {args.coarse_max_dofs} unknowns, dense inverse"
+                                    if args.coarse_max_dofs else "2^3 cells, lowest time degree, dense inverse"),
                        "fgmres_iterations_mean": float(np.mean(its)) if its else None,
                        "learned_guess_taken": int(sum(taken)) if use_net else None},
             "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
@@ -637,6 +642,8 @@ def main():
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")
+    ap.add_argument("--coarse-max-dofs", type=int, default=1500,
+                    help="hierarchy ends at the first coarser level with at most this many unknowns (0: full)")
     args = ap.parse_args()
     if args.only_kernel:
         return run_kernel_only(args)

@@ -112,6 +112,9 @@ typedef struct {
   int space_coarsening;    /* spatial levels of the hierarchy: STMG_COARSEN_P_THEN_H lowers p one by one
                               down to 1, then halves the cells; STMG_COARSEN_H keeps p and halves the
                               cells; time coarsening (k) follows either way [P_THEN_H] */
+  int coarse_max_dofs;     /* 1..4096: the hierarchy ends at the first coarser level with at most this many
+                              unknowns, solved exactly by its dense inverse; 0: the full sequence down to
+                              2^dim cells and the lowest time degree [0] */
 } stmg_options;
 
 enum { STMG_COARSEN_P_THEN_H = 0, STMG_COARSEN_H = 1 };

@@ -47,10 +47,18 @@ class LevelSpec:
     k: int
 
 
-def level_sequence(p: int, N: int, k: int, scheme: str, p_coarsening: bool = True) -> list[LevelSpec]:
+def level_unknowns(s: LevelSpec, dim: int, scheme: str) -> int:
+    """Unconstrained space-time DoFs of a level: N_t times the interior nodes."""
+    nt = s.k + 1 if scheme == timeint.DG else s.k
+    return nt * (s.p * s.N - 1) ** dim
+
+
+def level_sequence(p: int, N: int, k: int, scheme: str, p_coarsening: bool = True, coarse_max_dofs: int = 0,
+                   dim: int = 3) -> list[LevelSpec]:
     """Fine-to-coarse list of (p, N, k): space first, then time (Algorithm mg-sequence).  With
     p_coarsening the space levels lower p one by one down to 1 before halving the cells; without it
-    they keep p (h-multigrid only)."""
+    they keep p (h-multigrid only).  coarse_max_dofs > 0 ends the list at the first coarser level
+    with at most that many unknowns (the coarsest level is solved exactly)."""
     seq = [LevelSpec(p, N, k)]
     while p_coarsening and seq[-1].p > 1:
         s = seq[-1]
@@ -62,6 +70,10 @@ def level_sequence(p: int, N: int, k: int, scheme: str, p_coarsening: bool = Tru
     while seq[-1].k > kmin:
         s = seq[-1]
         seq.append(LevelSpec(s.p, s.N, s.k - 1))
+    if coarse_max_dofs > 0:
+        for i in range(1, len(seq)):
+            if level_unknowns(seq[i], dim, scheme) <= coarse_max_dofs:
+                return seq[:i + 1]
     return seq
 
 
@@ -192,8 +204,8 @@ class Hierarchy:
     """All levels of the STMG V-cycle for one slab problem (finest level first)."""
 
     def __init__(self, dim, N, p, k, pde, scheme, tau, vertices, rho_cell=None, rho_qp=None,
-                 omegas=None, estimate=True, p_coarsening=True):
-        self.specs = level_sequence(p, N, k, scheme, p_coarsening)
+                 omegas=None, estimate=True, p_coarsening=True, coarse_max_dofs=0):
+        self.specs = level_sequence(p, N, k, scheme, p_coarsening, coarse_max_dofs, dim)
         self.pde, self.scheme = pde, scheme
         fine = Grid(N, dim, p, vertices)
         if rho_qp is None:

@@ -328,7 +328,7 @@ struct TmaCfg {
   static constexpr int CPG = CPG0 < CPG_MEM ? (CPG0 > 0 ? CPG0 : 1) : (CPG_MEM > 0 ? CPG_MEM : 1);
   static constexpr int THREADS = (CPG * NB + 31) / 32 * 32;
   static constexpr int STAGE_BYTES = CPG * CELL_BYTES;
-  static constexpr int S = STAGE_BYTES <= 16384 ? 4 : 3;
+  static constexpr int S = 2;  // measured on GB300: two stages (more CTAs per SM) beat three or four
   static constexpr size_t SMEM = (size_t)S * STAGE_BYTES;
 };
 

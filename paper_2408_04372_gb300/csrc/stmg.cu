@@ -141,6 +141,11 @@ struct Spec { int p, N, k; };
 // Coarsening in space first, then in time (Algorithm mg-sequence, Section 3.2).  p_coarsening: the
 // space levels first lower p one by one down to 1, then halve the cells; otherwise they keep p and
 // only halve the cells (h-multigrid).
+int64_t level_unknowns(const Spec& sp, int dim, int scheme) {
+  const int64_t in1 = (int64_t)sp.p * sp.N - 1;
+  return (int64_t)(scheme == STMG_DG ? sp.k + 1 : sp.k) * (dim == 3 ? in1 * in1 * in1 : in1 * in1);
+}
+
 std::vector<Spec> level_sequence(int p, int N, int k, int scheme, bool p_coarsening) {
   std::vector<Spec> s{{p, N, k}};
   if (p_coarsening)
@@ -715,10 +720,10 @@ stmg_status setup_coarse(stmg_ctx* ctx, Level& L) {
     for (int i = 0; i < n; ++i) S[(size_t)i * n + j] = col[map[i]];
   }
   if (!invert(n, S)) { ctx->err = "coarsest operator singular"; return STMG_ERR_INTERNAL; }
+  // row-major inverse (the coarse kernel reads one row per warp)
   std::vector<double> cm((size_t)n * n);
   std::vector<float> cmf((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) { cm[(size_t)j * n + i] = S[(size_t)i * n + j]; cmf[(size_t)j * n + i] = (float)S[(size_t)i * n + j]; }
+  for (size_t e = 0; e < (size_t)n * n; ++e) { cm[e] = S[e]; cmf[e] = (float)S[e]; }
   CKS(dev_alloc(ctx, &L.cmap, n));
   CKS(dev_alloc(ctx, &L.cinv64, (size_t)n * n));
   CKS(dev_alloc(ctx, &L.cinv32, (size_t)n * n));
@@ -754,6 +759,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (!(o.atol >= 0.0)) return invalid(ctx, "atol must be >= 0");
   if (o.space_coarsening != STMG_COARSEN_P_THEN_H && o.space_coarsening != STMG_COARSEN_H)
     return invalid(ctx, "space_coarsening out of range");
+  if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096) return invalid(ctx, "coarse_max_dofs must be in 0..4096");
   if (o.max_it <= 0) o.max_it = 200;
   if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
   if (o.outer_apply == 0) o.outer_apply = o.vcycle_precision == STMG_FP32 ? STMG_DF32 : STMG_FP64;
@@ -797,6 +803,10 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     for (double v : rho_f) if (!(v > 0.0) || !std::isfinite(v)) return invalid(ctx, "coefficient must be positive and finite");
   }
   std::vector<Spec> seq = level_sequence(pr->p, N, pr->k, pr->time_scheme, o.space_coarsening == STMG_COARSEN_P_THEN_H);
+  // a shallower hierarchy: the first coarser level with at most coarse_max_dofs unknowns is the coarsest
+  if (o.coarse_max_dofs > 0)
+    for (size_t li = 1; li < seq.size(); ++li)
+      if (level_unknowns(seq[li], dim, pr->time_scheme) <= o.coarse_max_dofs) { seq.resize(li + 1); break; }
   ctx->levels.resize(seq.size());
   for (size_t li = 0; li < seq.size(); ++li) {
     Level& L = ctx->levels[li];

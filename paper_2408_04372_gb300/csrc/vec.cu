@@ -364,16 +364,25 @@ __global__ void time_mix_kernel(MixTab m, int nin, int nout, double* __restrict_
   }
 }
 
+// Coarsest-level solve u[map[i]] = sum_j inv[i][j] f[map[j]] with the inverse stored row-major: each
+// block gathers the n right-hand-side entries into shared memory, each warp takes one row and reduces
+// its coalesced dot product with shuffles in a fixed order (deterministic).
 template <typename T>
 __global__ void coarse_solve_kernel(const T* __restrict__ f, T* __restrict__ u, const T* __restrict__ inv,
                                     const int64_t* __restrict__ map, int n) {
   pdl_wait();
   pdl_trigger();
-  // inv stored column-major: inv[j * n + i]
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  extern __shared__ __align__(16) unsigned char cs_raw[];
+  T* fc = reinterpret_cast<T*>(cs_raw);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) fc[j] = f[map[j]];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n; i += gridDim.x * warps) {
+    const T* row = inv + (int64_t)i * n;
     T s = 0;
-    for (int j = 0; j < n; ++j) s += inv[(int64_t)j * n + i] * f[map[j]];
-    u[map[i]] = s;
+    for (int j = lane; j < n; j += 32) s += row[j] * fc[j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) u[map[i]] = s;
   }
 }
 
@@ -488,7 +497,9 @@ template <typename T>
 cudaError_t launch_coarse_solve(const T* f, T* u, const T* inv, const int64_t* map, int n, int64_t total,
                                 cudaStream_t s) {
   (void)total;
-  { const cudaError_t e_ = launch_k(coarse_solve_kernel<T>, dim3((n + 127) / 128), dim3(128), 0, s, f, u, inv, map, n); if (e_ != cudaSuccess) return e_; }
+  const size_t smem = (size_t)n * sizeof(T);  // n <= 4096 unknowns: at most 32 KB
+  const int blocks = std::max(1, std::min((n + 7) / 8, 152 * 4));
+  { const cudaError_t e_ = launch_k(coarse_solve_kernel<T>, dim3(blocks), dim3(256), smem, s, f, u, inv, map, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(const float*, float*, const float*, const int64_t*, int, int64_t,

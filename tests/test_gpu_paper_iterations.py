@@ -3,8 +3,9 @@ p = k) against the table the paper prints (tests/golden/iter_heat_dg_cartesian.t
 
 The absolute counts depend on details the paper leaves to cited work (the eigenvalue estimator
 behind eq. relaxation, the GMRES variant), so parity is not claimed for them. What is checked:
-the counts do not grow under refinement (the paper's grid independence), and they stay within a
-factor 2 of the printed values (measured on GB300: about 1.5-1.7 times the printed counts)."""
+the counts do not grow under refinement (the paper's grid independence), they stay within a
+factor 2 of the printed values (measured on GB300: about 1.5-1.7 times the printed counts), and
+the error converges at least at the order k + 1 the paper reports."""
 import os
 
 import numpy as np
@@ -56,18 +57,23 @@ def _mean_iterations(torch, stmg, k, r):
         assert st["converged"]
         its.append(st["iterations"])
         uprev = u[(nt - 1) * nn:].clone()
-    # the discrete solution approximates u at t = 1 (sin(2 pi f) = 0): small nodal values
-    assert float(uprev.abs().max()) < 1e-3
+    # the exact solution vanishes at t = 1 (sin(2 pi f) = 0): the nodal values there are the error
+    err = float(uprev.abs().max())
+    assert err < 1e-3
     ctx.close()
-    return float(np.mean(its))
+    return float(np.mean(its)), err
 
 
 @pytest.mark.parametrize("k", [2, 3])
 def test_iterations_grid_independent_and_near_the_paper(env, k):
     torch, stmg = env
     table = _table()
-    its = {r: _mean_iterations(torch, stmg, k, r) for r in (2, 3)}
+    res = {r: _mean_iterations(torch, stmg, k, r) for r in (2, 3)}
+    its = {r: v[0] for r, v in res.items()}
     for r, v in its.items():
         assert v <= 2.0 * table[k][r], (k, r, v, table[k][r])
         assert v >= 0.5 * table[k][r], (k, r, v, table[k][r])
     assert its[3] <= its[2] + 1.0, its
+    # convergence under refinement of h and tau together: at least the order k + 1 the paper reports
+    # (Figure conv-heat); measured on GB300 the nodal error at t = 1 falls by about 14 (k = 2) and 31 (k = 3)
+    assert res[2][1] / res[3][1] >= 0.8 * 2 ** (k + 1), res

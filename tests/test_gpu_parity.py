@@ -162,6 +162,35 @@ def test_vcycle_with_h_coarsening_only(env, case):
     ctx.close()
 
 
+@pytest.mark.parametrize("case,max_dofs", [(CASES[0], 5), (CASES[1], 10), (CASES[2], 20), (CASES[5], 30)],
+                         ids=lambda v: v.name if hasattr(v, "name") else str(v))
+def test_shallow_hierarchy_vcycle_and_solve(env, case, max_dofs):
+    """Hierarchy ending at the first coarser level with at most max_dofs unknowns (dense coarse solve)."""
+    torch, stmg = env
+    from oracle import mg
+    H = mg.Hierarchy(case.dim, case.N, case.p, case.k, case.pde, case.scheme, case.tau, case.vertices(),
+                     rho_cell=case.rho_cell(), coarse_max_dofs=max_dofs)
+    full = mg.level_sequence(case.p, case.N, case.k, case.scheme, dim=case.dim)
+    assert 2 <= len(H.levels) < len(full)
+    prob = H.levels[0].prob
+    r = _rand(prob.n, 620, prob.bmask_full)
+    ref = H.vcycle(r)
+    for prec, dt, tol in ((stmg.FP64, torch.float64, 1e-9), (stmg.FP32, torch.float32, 2e-4)):
+        ctx = make_context(stmg, case, H, vcycle_precision=prec, coarse_max_dofs=max_dofs, rtol=1e-12, max_it=300)
+        assert ctx.n_levels == len(H.levels)
+        for _ in range(3):
+            e = torch.empty(prob.n, dtype=dt, device="cuda")
+            ctx.vcycle(torch.from_numpy(r).to("cuda", dt), e)
+            assert rel_err(e.cpu().numpy(), ref) < tol, (case.name, prec)
+        b = _rand(prob.n, 630, prob.bmask_full)
+        u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        st = ctx.solve(torch.from_numpy(b).cuda(), u)
+        assert st["converged"]
+        xd = prob.solve(b).reshape(-1)
+        assert np.linalg.norm(u.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-8
+        ctx.close()
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
 def test_solve_matches_direct_solution(env, case):
     torch, stmg = env

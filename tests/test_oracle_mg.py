@@ -15,6 +15,13 @@ def test_level_sequence_space_then_time():
     # spatial levels that keep p (h-multigrid only), then time
     seq = [(s.p, s.N, s.k) for s in mg.level_sequence(2, 32, 2, "dg", p_coarsening=False)]
     assert seq == [(2, 32, 2), (2, 16, 2), (2, 8, 2), (2, 4, 2), (2, 2, 2), (2, 2, 1), (2, 2, 0)]
+    # shallower hierarchy: ends at the first coarser level with <= 1500 unknowns (Q1 8^3 dG(2): 3 * 7^3)
+    seq = [(s.p, s.N, s.k) for s in mg.level_sequence(2, 32, 2, "dg", coarse_max_dofs=1500)]
+    assert seq == [(2, 32, 2), (1, 32, 2), (1, 16, 2), (1, 8, 2)]
+    assert mg.level_unknowns(mg.LevelSpec(1, 8, 2), 3, "dg") == 1029
+    # the finest level never becomes the coarsest
+    seq = [(s.p, s.N, s.k) for s in mg.level_sequence(1, 4, 0, "dg", coarse_max_dofs=4096)]
+    assert seq == [(1, 4, 0), (1, 2, 0)]
 
 
 @pytest.mark.parametrize("pf,Nf,pc,Nc", [(2, 4, 1, 4), (3, 3, 2, 3), (1, 8, 1, 4), (2, 4, 2, 2)])
