@@ -374,9 +374,11 @@ def run_ours(args):
                                    "multiply-add, in FP64-equivalent flop/s (derived)",
                     "avg_launch_ms": df_ms}
             extra["apply_fp64_finest"] = roof_fp64
-        asm_bytes = cells * nt * (nq ** 3) ** 2 * inv_bytes + 2 * 4 * n
+        nb = nq ** 3
+        asm_bytes = cells * nt * nb * ((nb + 3) // 4 * 4) * inv_bytes + 2 * 4 * n  # rows padded to 4
         extra["asm_finest_fp32_arith"] = {"inverse_storage": args.inverse, "avg_launch_ms": asm_ms,
                                           "algorithmic_bytes": asm_bytes,
+                                          "traffic": read_traffic("asm_bf16") if args.inverse == "bf16" else None,
                                     "achieved_GBs": asm_bytes / (asm_ms * 1e-3) / 1e9,
                                     "frac_of_measured_hbm": asm_bytes / (asm_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
         extra["vcycle_ms"] = vc_ms
