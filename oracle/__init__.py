@@ -13,6 +13,8 @@ Every function is a direct, slow, readable restatement of the paper:
   slab      -- slab operator, right-hand side, direct solve, velocity update
   mg        -- transfers (Section 3.2), cell-wise additive Schwarz (eqs. vanka0, vanka),
                V-cycle (Algorithm stmg), relaxation (eq. relaxation), FGMRES
+  atonce    -- several heat dG(k) slabs in one system (eq. heat-cg-dg-at-once) and tau-multigrid
+               (Algorithm mg-sequence, mgType tau)
   conv      -- direct 3D convolution network used for the learned initial guess
 
 Parity status per function is stated in each module header.
