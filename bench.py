@@ -321,6 +321,8 @@ def run_ours(args):
         compare["plain_fp64_previous_slab_guess"] = {"value": dofs_per_step * k3 / (t_p / 1e3), "unit": UNIT,
                                                      "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_p]))}
         ctx64.close()
+        if args.atonce_slabs > 1:
+            compare["at_once"] = at_once_arm(args, stmg, wl, F, sols, dofs_per_step, nt, nn, inv_prec, dev)
 
     # end to end through the C ABI from pinned host buffers (H2D of f and the previous slab, D2H of u)
     Fh = torch.empty((n_slabs, n), dtype=torch.float64).pin_memory()
@@ -415,6 +417,45 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def at_once_arm(args, stmg, wl, F, sols, dofs_per_step, nt, nn, inv_prec, dev):
+    """The first n_c slabs as one system (eq. heat-cg-dg-at-once) with tau-levels in the hierarchy:
+    right-hand side, previous-slab guess and one FGMRES solve to 1e-8 relative residual of the whole
+    system, repeated; the solution is compared with the slab-by-slab one of the main arm."""
+    import torch
+    nc = args.atonce_slabs
+    n = nt * nn
+    ctxb = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
+                        vcycle_precision=stmg.FP32, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
+                        n_slabs=nc)
+    rb = torch.empty(nc * n, dtype=torch.float64, device=dev)
+    ub = torch.empty_like(rb)
+    prev_end = sols[0][(nt - 1) * nn:]
+
+    def once():
+        ctxb.rhs(F[:nc].reshape(-1), rb, u0=prev_end)
+        ctxb.guess_previous(prev_end, ub)
+        return ctxb.solve(rb, ub)
+    once()
+    reps = 3
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sts = [once() for _ in range(reps)]
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    seq = sols[1:nc + 1].reshape(-1)
+    diff = float((ub - seq).norm() / seq.norm())
+    asm_ms = ctxb.time_kernel(stmg.KERNEL_ASM, 0, stmg.FP32, reps=20)
+    levels = [ctxb.level_info(l) for l in range(ctxb.n_levels)]
+    out = {"slabs_per_system": nc, "value": nc * dofs_per_step / (ms / 1e3), "unit": UNIT, "ms_per_system": ms,
+           "fgmres_iterations": sts[-1]["iterations"], "rel_diff_to_slab_by_slab": diff,
+           "levels": [f"Q{l['p']} {l['n_cells']}^3 dG({l['k']}) x{l['n_slabs']}" for l in levels],
+           "asm_finest_ms_all_slabs": asm_ms, "asm_finest_ms_per_slab": asm_ms / nc}
+    ctxb.close()
+    return out
 
 
 def run_learned_c5(args):
@@ -644,6 +685,8 @@ def main():
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")
+    ap.add_argument("--atonce-slabs", type=int, default=8,
+                    help="comparison arm: the first n slabs as one system with tau-multigrid (0 = off)")
     ap.add_argument("--coarse-max-dofs", type=int, default=1500,
                     help="hierarchy ends at the first coarser level with at most this many unknowns (0: full)")
     args = ap.parse_args()

@@ -75,6 +75,12 @@ typedef struct {
 
 /* The slab problem (Section 2).  p: spatial degree 1..4; k: time degree
  * (dG: 0..3, N_t = k+1; cGP: 1..4, N_t = k); tau: slab length.
+ * n_slabs (0 = 1): consecutive slabs solved as one system, heat equation with dG
+ * only (eq. heat-cg-dg-at-once: the slab operator S on the block diagonal, the
+ * coupling -B = -1 (x) alpha (x) M_h to the previous slab's last time DoF below it).
+ * Vectors of such a system are [slab][N_t][n_nodes]; the hierarchy adds
+ * tau-levels (pairs of slabs merged, tau -> 2 tau, while their number is even)
+ * between the space and the k levels (Algorithm mg-sequence).  1..64.
  * coeff (HOST, copied at create): rho of eq. space-matrices, either one value
  * per finest cell (PER_CELL) or one per finest-level Gauss point
  * ([cell][(p+1)^dim points, x fastest], PER_QPOINT); NULL means rho = 1.
@@ -88,6 +94,7 @@ typedef struct {
   double tau;
   int coeff_mode;
   const double* coeff;
+  int n_slabs;
 } stmg_problem;
 
 /* Solver options.  Zero-initialised fields take the defaults in brackets.
@@ -136,7 +143,9 @@ const char* stmg_last_error(const stmg_ctx* ctx);
 
 /* Sizes of the finest level and number of levels (level 0 = finest). */
 stmg_status stmg_sizes(const stmg_ctx* ctx, int64_t* n_nodes, int* n_t, int* n_levels);
-/* Per-level data: degree p, cells per direction, time degree k, nodes, N_t, omega. */
+/* Slabs in the system of a level and their length (tau-levels halve the one, double the other). */
+stmg_status stmg_level_slabs(const stmg_ctx* ctx, int level, int* n_slabs, double* tau);
+/* Per-level data: degree p, cells per direction, time degree k, nodes, N_t (per slab), omega. */
 stmg_status stmg_level_info(const stmg_ctx* ctx, int level, int* p, int* n_cells, int* k,
                             int64_t* n_nodes, int* n_t, double* omega);
 /* Physical node coordinates of a level (HOST output, n_nodes x dim).  Synchronous. */
@@ -162,7 +171,8 @@ stmg_status stmg_vcycle(stmg_ctx* ctx, int precision, const void* r, void* e);
  * eqs. heat-cg-dg / heat-cg-cg / wave-cg-dg / wave-cg-cg]; f: nodal source
  * values [N_t][n_nodes] at the free time nodes of the slab; f0: source at the
  * slab start (cGP only, else ignored, may be NULL); u0, v0: end values of the
- * previous slab (v0 wave only).  Rows of boundary nodes are set to 0. */
+ * previous slab (v0 wave only).  Rows of boundary nodes are set to 0.  With
+ * n_slabs > 1, f is [slab][N_t][n_nodes] and u0 enters the first slab only. */
 stmg_status stmg_rhs(stmg_ctx* ctx, const double* f, const double* f0, const double* u0,
                      const double* v0, double* rhs);
 /* FGMRES (right preconditioned, one V-cycle per iteration) on the finest level
@@ -173,13 +183,14 @@ stmg_status stmg_solve(stmg_ctx* ctx, const double* rhs, double* u, stmg_solve_s
  * v = M_tau^-1 (A_tau u + alpha u0 - beta v0) (cGP) / M_tau^-1 (A_tau u - alpha u0) (dG). */
 stmg_status stmg_wave_velocity(stmg_ctx* ctx, const double* u, const double* u0, const double* v0,
                                double* v);
-/* Broadcast of the previous slab's end value to all time DoFs (the plain initial guess). */
+/* Broadcast of the previous slab's end value to all time DoFs (of every slab of the system):
+ * the plain initial guess. */
 stmg_status stmg_guess_previous(stmg_ctx* ctx, const double* u0, double* u);
 
 /* End-to-end slab step from HOST buffers: uploads f [N_t][n], f0, u0, v0 (may be
  * NULL as above), builds the right-hand side, solves from the previous-slab
  * guess and downloads u [N_t][n] (and v for the wave equation, may be NULL).
- * Synchronous. */
+ * With n_slabs > 1, f and u are [slab][N_t][n].  Synchronous. */
 stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f0, const double* u0,
                                  const double* v0, double* u, double* v, stmg_solve_stats* stats);
 

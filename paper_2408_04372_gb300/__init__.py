@@ -30,7 +30,7 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_wave_velocity", "stmg_guess_previous", "stmg_solve_slab_host", "stmg_launch_count",
            "stmg_time_kernel", "stmg_smooth_noalloc", "stmg_net_create", "stmg_net_destroy", "stmg_net_predict",
            "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights", "stmg_select_guess",
-           "stmg_solve_slab_host_learned", "stmg_selftest_device_timeout"]
+           "stmg_solve_slab_host_learned", "stmg_selftest_device_timeout", "stmg_level_slabs"]
 KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
 
 
@@ -46,7 +46,8 @@ class Mesh(ctypes.Structure):
 
 class Problem(ctypes.Structure):
     _fields_ = [("pde", ctypes.c_int), ("time_scheme", ctypes.c_int), ("p", ctypes.c_int), ("k", ctypes.c_int),
-                ("tau", ctypes.c_double), ("coeff_mode", ctypes.c_int), ("coeff", ctypes.POINTER(ctypes.c_double))]
+                ("tau", ctypes.c_double), ("coeff_mode", ctypes.c_int), ("coeff", ctypes.POINTER(ctypes.c_double)),
+                ("n_slabs", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "stmg_sizes": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "stmg_level_info": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                             ctypes.POINTER(i64), ctypes.POINTER(i32), dp],
+        "stmg_level_slabs": [vp, i32, ctypes.POINTER(i32), dp],
         "stmg_node_coords": [vp, i32, vp],
         "stmg_qpoint_coords": [vp, i32, vp],
         "stmg_apply": [vp, i32, i32, vp, vp],
@@ -133,7 +135,7 @@ class Context:
     def __init__(self, dim, n_cells, p, k, tau, pde=HEAT, scheme=DG, vertices=None, coeff=None,
                  coeff_mode=COEFF_PER_CELL, nu_pre=1, nu_post=1, vcycle_precision=FP32, inverse_precision=0,
                  omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO,
-                 outer_apply=0, atol=0.0, space_coarsening=0, coarse_max_dofs=0):
+                 outer_apply=0, atol=0.0, space_coarsening=0, coarse_max_dofs=0, n_slabs=1):
         import numpy as np
         import torch
         self.lib = load()
@@ -144,7 +146,7 @@ class Context:
         om = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)
         self._keep += [v, c, om]
         mesh = Mesh(dim, n_cells, _dptr(v))
-        prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c))
+        prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c), int(n_slabs))
         opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, smoother_kind, _dptr(om), restart, rtol,
                        max_it, outer_apply, float(atol), space_coarsening, coarse_max_dofs)
         if stream is None:
@@ -163,6 +165,8 @@ class Context:
         self._check(self.lib.stmg_sizes(h, ctypes.byref(n_nodes), ctypes.byref(nt), ctypes.byref(nl)))
         self.n_nodes, self.nt, self.n_levels, self.dim = n_nodes.value, nt.value, nl.value, dim
         self.pde = pde
+        self.n_slabs = int(n_slabs)
+        self.size = self.n_slabs * self.nt * self.n_nodes  # finest-level vector length, [slab][N_t][node]
 
     def __del__(self):
         for net in list(getattr(self, "_nets", ())):
@@ -183,7 +187,10 @@ class Context:
         nn, om = ctypes.c_int64(), ctypes.c_double()
         self._check(self.lib.stmg_level_info(self.h, level, ctypes.byref(p), ctypes.byref(N), ctypes.byref(k),
                                              ctypes.byref(nn), ctypes.byref(nt), ctypes.byref(om)))
-        return dict(p=p.value, n_cells=N.value, k=k.value, n_nodes=nn.value, nt=nt.value, omega=om.value)
+        nc, tau = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.stmg_level_slabs(self.h, level, ctypes.byref(nc), ctypes.byref(tau)))
+        return dict(p=p.value, n_cells=N.value, k=k.value, n_nodes=nn.value, nt=nt.value, omega=om.value,
+                    n_slabs=nc.value, tau=tau.value)
 
     def node_coords(self, level=0):
         import numpy as np
@@ -213,8 +220,8 @@ class Context:
         if t is None:
             return
         info = self.level_info(level)
-        if not t.is_cuda or not t.is_contiguous() or t.numel() != info["n_nodes"] * info["nt"]:
-            raise ValueError("expected a contiguous CUDA tensor of N_t * n_nodes values")
+        if not t.is_cuda or not t.is_contiguous() or t.numel() != info["n_slabs"] * info["nt"] * info["n_nodes"]:
+            raise ValueError("expected a contiguous CUDA tensor of n_slabs * N_t * n_nodes values")
 
     def apply(self, x, y, level=0):
         self._vec(x, level); self._vec(y, level)

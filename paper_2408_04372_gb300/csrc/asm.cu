@@ -316,8 +316,11 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
 // The inverse store is contiguous over cells, so the planes of CPG consecutive cells are one
 // bulk copy (cp.async.bulk, completion counted on an mbarrier).  Each CTA walks its groups with
 // S stages in flight; while a group's copy lands, its threads form the modal residual of the
-// group's cells.  Every wait is bounded: on timeout the kernel records STMG_DEVICE_TIMEOUT in
-// *status, drains the copies it issued (bounded as well) and returns.
+// group's cells.  With several slabs in one system (nslab > 1, vectors nslab blocks of
+// slab_stride entries) every slab has the same local inverses, so a landed group serves all
+// slabs before its stage is reused: the inverse stream, which bounds the kernel, is read once
+// per sweep instead of once per slab.  Every wait is bounded: on timeout the kernel records
+// STMG_DEVICE_TIMEOUT in *status, drains the copies it issued (bounded as well) and returns.
 template <int DIM, int N, int NT, typename TI>
 struct TmaCfg {
   static constexpr int NB = Shape<DIM, N>::NB;
@@ -401,7 +404,8 @@ __global__ void wait_selftest_kernel(int* status) {
 template <int DIM, int N, int NT, typename T, typename TI>
 __global__ void __launch_bounds__(TmaCfg<DIM, N, NT, TI>::THREADS)
 asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g,
-                     ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst, int* status) {
+                     ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst, int* status,
+                     int nslab, int64_t slab_stride) {
   pdl_wait();
   pdl_trigger();
   using C = TmaCfg<DIM, N, NT, TI>;
@@ -445,12 +449,14 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
   // that their latency overlaps the previous group's work
   const int slot = tid / NB, a = tid - slot * NB;
   struct Pre { int64_t node; bool active, live; T rr[NT], cp[NT]; };
-  auto prefetch = [&](int64_t grp, Pre& P) {
+  // work item (group grp, slab sl): the node of this thread and slab sl's residual there
+  auto prefetch = [&](int64_t grp, int sl, Pre& P) {
     const int64_t cell = grp * CPG + slot;
     P.active = grp < ngroups && slot < CPG && cell < g.n_cells;
     P.live = false;
     P.node = 0;
     if (!P.active) return;
+    const int64_t so = (int64_t)sl * slab_stride;
     const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
     const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
     const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
@@ -460,20 +466,23 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     P.node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
     P.live = !bnd;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) P.rr[t] = P.live ? r[t * g.n_nodes + P.node] : T(0);
+    for (int t = 0; t < NT; ++t) P.rr[t] = P.live ? r[so + t * g.n_nodes + P.node] : T(0);
     if (copy_dst) {
 #pragma unroll
-      for (int t = 0; t < NT; ++t) P.cp[t] = copy_src[t * g.n_nodes + P.node];
+      for (int t = 0; t < NT; ++t) P.cp[t] = copy_src[so + t * g.n_nodes + P.node];
     }
   };
   Pre cur, nxt;
-  prefetch(blockIdx.x, cur);
+  prefetch(blockIdx.x, 0, cur);
   for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++k) {
     const int stage = (int)(k % S);
     const uint32_t parity = (uint32_t)((k / S) & 1);
-    prefetch(grp + gridDim.x, nxt);
+   for (int sl = 0; sl < nslab; ++sl) {
+    const int64_t so = (int64_t)sl * slab_stride;
+    if (sl + 1 < nslab) prefetch(grp, sl + 1, nxt);
+    else prefetch(grp + gridDim.x, 0, nxt);
     const bool active = cur.active, live = cur.live;
-    const int64_t node = cur.node;
+    const int64_t node = so + cur.node;
     // modal residual of this group's cells (independent of the copy in flight)
     if (active) {
       if (copy_dst) {
@@ -491,7 +500,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
         s_r[slot][m][a] = v;
       }
     }
-    if (!mbar_wait(&bar[stage], parity, status)) {
+    if (sl == 0 && !mbar_wait(&bar[stage], parity, status)) {
       atomicExch(status, STMG_DEVICE_TIMEOUT);
       s_fail = 1;
     }
@@ -548,14 +557,16 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
         atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
       }
     }
-    __syncthreads();  // stage and s_r free again
+    __syncthreads();  // s_r free again (and, after the last slab, the stage)
+    cur = nxt;
+   }
+    if (s_fail) break;
     const int64_t next = grp + (int64_t)S * gridDim.x;
     if (next < ngroups) {
       if (tid == 0)
         tma_bulk_load(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage]);
       ++issued;
     }
-    cur = nxt;
   }
   // after a timeout: wait (bounded) for the copies still in flight before the CTA exits
   if (s_fail) {
@@ -578,14 +589,20 @@ cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, 
 
 template <int DIM, int N, int NT, typename T, typename TI>
 cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd,
-                    int* status, cudaStream_t s) {
-  // row-streaming kernel when there is no device status word to report a timeout to, or when
-  // S stages of one cell's planes exceed the shared memory of an SM (p = 3, N_t = 4, FP64)
+                    int* status, int nslab, int64_t ss, cudaStream_t s) {
+  // row-streaming kernel (one launch per slab) when there is no device status word to report a
+  // timeout to, or when S stages of one cell's planes exceed the shared memory of an SM (p = 3,
+  // N_t = 4, FP64)
   if (!status || TmaCfg<DIM, N, NT, TI>::SMEM > (size_t)200 * 1024) {
     using C = AsmCfg<DIM, N, NT, TI>;
     const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
-    { const cudaError_t e_ = launch_k(asm_apply_kernel<DIM, N, NT, T, TI>, dim3((unsigned)blocks), dim3(C::CPB * C::TPC), 0, s, 
-        r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd); if (e_ != cudaSuccess) return e_; }
+    for (int sl = 0; sl < nslab; ++sl) {
+      const int64_t o = sl * ss;
+      const cudaError_t e_ = launch_k(asm_apply_kernel<DIM, N, NT, T, TI>, dim3((unsigned)blocks), dim3(C::CPB * C::TPC),
+                                      0, s, r + o, u + o, reinterpret_cast<const TI*>(inv), g, mt, cs ? cs + o : nullptr,
+                                      cd ? cd + o : nullptr);
+      if (e_ != cudaSuccess) return e_;
+    }
     return cudaGetLastError();
   }
   using C = TmaCfg<DIM, N, NT, TI>;
@@ -603,7 +620,7 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
   }
   const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
   const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
-  { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), C::SMEM, s, r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), C::SMEM, s, r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status, nslab, ss); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -635,15 +652,15 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
 
 #define STMG_ASM_CASE(DIM, N, NT)                                                                  \
   if (dim == DIM && n == N && nt == NT) {                                                          \
-    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, status, s); \
-    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, status, s);  \
-    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, status, s);             \
+    if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s); \
+    if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);  \
+    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);             \
   }
 
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
                              const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd, int* status,
-                             cudaStream_t s) {
+                             int nslab, int64_t ss, cudaStream_t s) {
   STMG_ASM_CASE(3, 2, 1) STMG_ASM_CASE(3, 2, 2) STMG_ASM_CASE(3, 2, 3) STMG_ASM_CASE(3, 2, 4)
   STMG_ASM_CASE(3, 3, 1) STMG_ASM_CASE(3, 3, 2) STMG_ASM_CASE(3, 3, 3) STMG_ASM_CASE(3, 3, 4)
   STMG_ASM_CASE(3, 4, 1) STMG_ASM_CASE(3, 4, 2) STMG_ASM_CASE(3, 4, 3) STMG_ASM_CASE(3, 4, 4)
@@ -655,9 +672,10 @@ cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const voi
 }
 
 template cudaError_t launch_asm_apply<float>(int, int, int, const float*, float*, const void*, int, const GridDesc&,
-                                             const ModeTab<float>&, const float*, float*, int*, cudaStream_t);
+                                             const ModeTab<float>&, const float*, float*, int*, int, int64_t,
+                                             cudaStream_t);
 template cudaError_t launch_asm_apply<double>(int, int, int, const double*, double*, const void*, int,
                                               const GridDesc&, const ModeTab<double>&, const double*, double*, int*,
-                                              cudaStream_t);
+                                              int, int64_t, cudaStream_t);
 
 }  // namespace stmg

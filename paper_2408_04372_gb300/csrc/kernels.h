@@ -17,6 +17,13 @@ cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo,
 // Mass part only, y += (TM (x) M_h) x in FP64 (TA ignored, no input masking): right-hand sides.
 cudaError_t launch_mass_apply(int dim, int n, int nt, const double* x, double* y, const double* geo, const GridDesc& g,
                               const OpTab<double>& tab, cudaStream_t s);
+// Mass part with constrained input nodes read as 0, y += (TM (x) M_h) x in arithmetic T from TI to TO:
+// the coupling -B u_{i-1} between consecutive slabs of eq. heat-cg-dg-at-once (TM holds the column
+// of the previous slab's last time DoF).  Instances <float,float,float>, <double,double,double>,
+// <double,float,double>.
+template <typename T, typename TI, typename TO>
+cudaError_t launch_mass_couple(int dim, int n, int nt, const TI* x, TO* y, const T* geo, const GridDesc& g,
+                               const OpTab<T>& tab, cudaStream_t s);
 // Same operator in double-float arithmetic (df64.cuh) for an FP32 input vector, accumulated into
 // an FP64 output: the FGMRES apply on V-cycle outputs, which are exact in FP32.
 cudaError_t launch_apply_df(int dim, int n, int nt, const float* x, double* y, const df64* geo, const GridDesc& g,
@@ -48,10 +55,11 @@ int64_t asm_cell_stride(int dim, int n, int nt);
 // copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell.
 // status (device int, may be NULL): with it the inverses arrive by bulk copies (TMA) into shared memory and
 // a timed-out wait stores STMG_DEVICE_TIMEOUT there; without it each thread streams its rows itself.
+// nslab slabs of slab_stride entries each share the inverses (one bulk copy serves all of them).
 template <typename T>
 cudaError_t launch_asm_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int inv_prec,
                              const GridDesc& g, const ModeTab<T>& mt, const T* copy_src, T* copy_dst, int* status,
-                             cudaStream_t s);
+                             int nslab, int64_t slab_stride, cudaStream_t s);
 
 // Test hook: a bounded device wait that cannot complete; about one second later *status holds
 // STMG_DEVICE_TIMEOUT.
@@ -83,7 +91,11 @@ cudaError_t launch_prolong_space_add(T* uf, const T* ec, const GridDesc& gf, con
 template <typename T>
 cudaError_t launch_restrict_space(T* rc, const T* rf, const GridDesc& gf, const GridDesc& gc, int nt,
                                   const Transfer1D& t, T* zero_dst, cudaStream_t s);
-struct TimeTransfer { int ntf, ntc; double P[kMaxNT][kMaxNT]; };
+// Time transfers act on nb blocks of consecutive time components, the fine block b being components
+// [b ntf, (b+1) ntf) and the coarse one [b ntc, (b+1) ntc) of a [component][node] vector.  k-levels:
+// P_k per slab (ntf, ntc = N_t of the two levels, nb = slabs).  tau-levels: two consecutive fine slabs
+// form one fine block (ntf = 2 N_t) under one coarse slab of twice the length (ntc = N_t, nb = coarse slabs).
+struct TimeTransfer { int ntf, ntc, nb; double P[2 * kMaxNT][kMaxNT]; };
 template <typename T>
 cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const TimeTransfer& t, const T* copy_src,
                                     T* copy_dst, cudaStream_t s);

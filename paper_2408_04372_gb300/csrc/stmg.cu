@@ -19,6 +19,8 @@ namespace {
 
 struct Level {
   int dim = 3, p = 1, n = 2, N = 2, k = 0, nt = 1;
+  int nc = 1;          // slabs in the level's system (eq. heat-cg-dg-at-once), vectors [slab][N_t][node]
+  double tau = 1.0;    // slab length on this level (doubles on tau-levels)
   GridDesc g{};
   std::vector<double> vertices;   // host (N+1)^dim x dim
   std::vector<double> rho_qp;     // host cells x (p+1)^dim
@@ -29,6 +31,9 @@ struct Level {
   SlabCoeffs sc;
   OpTab<double> tab64{};
   OpTab<float> tab32{};
+  // coupling -B of slab i to the last time DoF of slab i-1 (TM column N_t - 1 = -alpha), nc > 1
+  OpTab<double> cpl64{};
+  OpTab<float> cpl32{};
   LocalTab lt{};
   // smoother
   int nreal = 0, ncplx = 0;
@@ -45,7 +50,7 @@ struct Level {
   // work vectors
   double *f64 = nullptr, *u64 = nullptr, *r64 = nullptr;
   float *f32 = nullptr, *u32 = nullptr, *r32 = nullptr;
-  // transfer into this level from levels[l+1] (tkind 1 space, 2 time, 0 none)
+  // transfer into this level from levels[l+1] (tkind 1 space, 2 time degree, 3 slab length, 0 none)
   int tkind = 0;
   Transfer1D tr{};
   TimeTransfer tt{};
@@ -54,7 +59,8 @@ struct Level {
   int64_t* cmap = nullptr;
   double* cinv64 = nullptr;
   float* cinv32 = nullptr;
-  int64_t size() const { return (int64_t)nt * g.n_nodes; }
+  int64_t slab_size() const { return (int64_t)nt * g.n_nodes; }
+  int64_t size() const { return (int64_t)nc * slab_size(); }
 };
 
 }  // namespace
@@ -136,23 +142,29 @@ stmg_status invalid(stmg_ctx* ctx, const std::string& msg) {
 
 // ---------------------------------------------------------------- level setup
 
-struct Spec { int p, N, k; };
+struct Spec { int p, N, k, nc; double tau; };
 
 // Coarsening in space first, then in time (Algorithm mg-sequence, Section 3.2).  p_coarsening: the
 // space levels first lower p one by one down to 1, then halve the cells; otherwise they keep p and
-// only halve the cells (h-multigrid).
+// only halve the cells (h-multigrid).  With several slabs in one system (nc > 1), tau-levels merge
+// pairs of slabs (tau -> 2 tau) while their number is even, before the k-levels.
 int64_t level_unknowns(const Spec& sp, int dim, int scheme) {
   const int64_t in1 = (int64_t)sp.p * sp.N - 1;
-  return (int64_t)(scheme == STMG_DG ? sp.k + 1 : sp.k) * (dim == 3 ? in1 * in1 * in1 : in1 * in1);
+  return (int64_t)sp.nc * (scheme == STMG_DG ? sp.k + 1 : sp.k) * (dim == 3 ? in1 * in1 * in1 : in1 * in1);
 }
 
-std::vector<Spec> level_sequence(int p, int N, int k, int scheme, bool p_coarsening) {
-  std::vector<Spec> s{{p, N, k}};
+std::vector<Spec> level_sequence(int p, int N, int k, int scheme, bool p_coarsening, int nc, double tau) {
+  std::vector<Spec> s{{p, N, k, nc, tau}};
+  auto next = [&](int dp, int hN, int dk, int hc) {
+    const Spec b = s.back();
+    s.push_back({b.p - dp, b.N / hN, b.k - dk, b.nc / hc, b.tau * hc});
+  };
   if (p_coarsening)
-    while (s.back().p > 1) s.push_back({s.back().p - 1, s.back().N, s.back().k});
-  while (s.back().N % 2 == 0 && s.back().N / 2 >= 2) s.push_back({s.back().p, s.back().N / 2, s.back().k});
+    while (s.back().p > 1) next(1, 1, 0, 1);
+  while (s.back().N % 2 == 0 && s.back().N / 2 >= 2) next(0, 2, 0, 1);
+  while (s.back().nc % 2 == 0) next(0, 1, 0, 2);
   const int kmin = scheme == STMG_DG ? 0 : 1;
-  while (s.back().k > kmin) s.push_back({s.back().p, s.back().N, s.back().k - 1});
+  while (s.back().k > kmin) next(0, 1, 1, 1);
   return s;
 }
 
@@ -218,37 +230,61 @@ template <typename T> const T* cinv_of(const Level& L);
 template <> const double* cinv_of<double>(const Level& L) { return L.cinv64; }
 template <> const float* cinv_of<float>(const Level& L) { return L.cinv32; }
 
-// y = S x (identity on constrained rows)
+template <typename T> const OpTab<T>& cpl_of(const Level& L);
+template <> const OpTab<double>& cpl_of<double>(const Level& L) { return L.cpl64; }
+template <> const OpTab<float>& cpl_of<float>(const Level& L) { return L.cpl32; }
+
+// y (+)= sign S x on unconstrained rows, slab by slab: the slab operator on the diagonal and the
+// coupling -B to the previous slab's last time DoF below it (eq. heat-cg-dg-at-once)
 template <typename T>
-stmg_status op_apply(stmg_ctx* ctx, Level& L, const T* x, T* y) {
-  CK(launch_init_rows<T>(y, nullptr, x, L.g, L.nt, 0, ctx->stream));
-  ctx->launches += 2;
+stmg_status apply_slabs(stmg_ctx* ctx, Level& L, const T* x, T* y, T sign) {
   OpTab<T> t = tab_of<T>(L);
-  t.sign = T(1);
-  CK(launch_apply<T>(L.dim, L.n, L.nt, x, y, geo_of<T>(L), L.g, t, 1, ctx->stream));
+  t.sign = sign;
+  OpTab<T> c = cpl_of<T>(L);
+  if (sign != T(1))
+    for (int i = 0; i < kMaxNT; ++i) c.TM[i][L.nt - 1] *= sign;
+  const int64_t ss = L.slab_size();
+  for (int i = 0; i < L.nc; ++i) {
+    CK(launch_apply<T>(L.dim, L.n, L.nt, x + i * ss, y + i * ss, geo_of<T>(L), L.g, t, 1, ctx->stream));
+    if (i > 0) CK(launch_mass_couple<T, T, T>(L.dim, L.n, L.nt, x + (i - 1) * ss, y + i * ss, geo_of<T>(L), L.g, c,
+                                              ctx->stream));
+  }
+  ctx->launches += 2 * L.nc - 1;
   return STMG_OK;
 }
 
+// y = S x (identity on constrained rows)
+template <typename T>
+stmg_status op_apply(stmg_ctx* ctx, Level& L, const T* x, T* y) {
+  CK(launch_init_rows<T>(y, nullptr, x, L.g, L.nt * L.nc, 0, ctx->stream));
+  ctx->launches += 1;
+  return apply_slabs<T>(ctx, L, x, y, T(1));
+}
+
 // y = S x for an FP32 x, in double-float arithmetic, FP64 y (identity on constrained rows)
+// (slab blocks in double-float; the coupling between slabs in FP64 from the FP32 input)
 stmg_status op_apply_df(stmg_ctx* ctx, Level& L, const float* x, double* y) {
   if (!L.geodf) { ctx->err = "no double-float geometry on this level"; return STMG_ERR_UNSUPPORTED; }
-  CK(launch_init_rows_f2d(y, x, L.g, L.nt, ctx->stream));
-  ctx->launches += 2;
+  CK(launch_init_rows_f2d(y, x, L.g, L.nt * L.nc, ctx->stream));
+  ctx->launches += 2 * L.nc;
   OpTab<df64> t = L.tabdf;
   t.sign = df64(1.0f);
-  CK(launch_apply_df(L.dim, L.n, L.nt, x, y, L.geodf, L.g, t, 1, ctx->stream));
+  const int64_t ss = L.slab_size();
+  for (int i = 0; i < L.nc; ++i) {
+    CK(launch_apply_df(L.dim, L.n, L.nt, x + i * ss, y + i * ss, L.geodf, L.g, t, 1, ctx->stream));
+    if (i > 0)
+      CK(launch_mass_couple<double, float, double>(L.dim, L.n, L.nt, x + (i - 1) * ss, y + i * ss, L.geo64, L.g,
+                                                   L.cpl64, ctx->stream));
+  }
   return STMG_OK;
 }
 
 // r = f - S u
 template <typename T>
 stmg_status op_residual(stmg_ctx* ctx, Level& L, const T* f, const T* u, T* r) {
-  CK(launch_init_rows<T>(r, f, u, L.g, L.nt, 1, ctx->stream));
-  ctx->launches += 2;
-  OpTab<T> t = tab_of<T>(L);
-  t.sign = T(-1);
-  CK(launch_apply<T>(L.dim, L.n, L.nt, u, r, geo_of<T>(L), L.g, t, 1, ctx->stream));
-  return STMG_OK;
+  CK(launch_init_rows<T>(r, f, u, L.g, L.nt * L.nc, 1, ctx->stream));
+  ctx->launches += 1;
+  return apply_slabs<T>(ctx, L, u, r, T(-1));
 }
 
 // u += omega * ASM r ; optionally also copy_dst := copy_src (a fused side job for the V-cycle)
@@ -257,13 +293,20 @@ stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega, cons
                    T* copy_dst = nullptr) {
   ModeTab<T> mt = mt_of<T>(L);
   mt.omega = (T)omega;
-  ctx->launches += 1;
-  if (L.fd) {
-    CK(launch_fd_apply<T>(L.n, L.nt, r, u, rho_of<T>(L), L.g, fd_of<T>(L), mt, copy_src, copy_dst, ctx->stream));
+  // block diagonal over the slabs: every space-time cell lies in one slab (same local inverses)
+  const int64_t ss = L.slab_size();
+  if (!L.fd) {
+    ctx->launches += 1;
+    CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->status, L.nc,
+                           ss, ctx->stream));
     return STMG_OK;
   }
-  CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->status,
-                         ctx->stream));
+  ctx->launches += L.nc;
+  for (int i = 0; i < L.nc; ++i) {
+    const int64_t o = i * ss;
+    CK(launch_fd_apply<T>(L.n, L.nt, r + o, u + o, rho_of<T>(L), L.g, fd_of<T>(L), mt, copy_src ? copy_src + o : nullptr,
+                          copy_dst ? copy_dst + o : nullptr, ctx->stream));
+  }
   return STMG_OK;
 }
 
@@ -286,7 +329,7 @@ stmg_status op_restrict(stmg_ctx* ctx, int l, const T* rf, T* rc, T* zero_dst = 
   Level& C = ctx->levels[l + 1];
   ctx->launches += 1;
   if (F.tkind == 1) {
-    CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt, F.tr, zero_dst, ctx->stream));
+    CK(launch_restrict_space<T>(rc, rf, F.g, C.g, F.nt * F.nc, F.tr, zero_dst, ctx->stream));
     const int R = F.tr.width_r;
     if (!transfer_fused_host(F.dim == 3 ? R * R * R : R * R, C.size())) ctx->launches += F.dim - 1;
   }
@@ -302,7 +345,7 @@ stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf, const T*
   Level& C = ctx->levels[l + 1];
   ctx->launches += 1;
   if (F.tkind == 1) {
-    CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt, F.tr, copy_src, copy_dst, ctx->stream));
+    CK(launch_prolong_space_add<T>(uf, ec, F.g, C.g, F.nt * F.nc, F.tr, copy_src, copy_dst, ctx->stream));
     const int R = F.tr.width_p;
     if (!transfer_fused_host(F.dim == 3 ? R * R * R : R * R, F.size())) ctx->launches += F.dim - 1;
   }
@@ -314,11 +357,7 @@ stmg_status op_prolongate_add(stmg_ctx* ctx, int l, const T* ec, T* uf, const T*
 // so f - u = f there): the residual without its initialisation pass
 template <typename T>
 stmg_status op_residual_preset(stmg_ctx* ctx, Level& L, const T* u, T* r) {
-  OpTab<T> t = tab_of<T>(L);
-  t.sign = T(-1);
-  ctx->launches += 1;
-  CK(launch_apply<T>(L.dim, L.n, L.nt, u, r, geo_of<T>(L), L.g, t, 1, ctx->stream));
-  return STMG_OK;
+  return apply_slabs<T>(ctx, L, u, r, T(-1));
 }
 
 template <typename T>
@@ -473,7 +512,7 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
   const int64_t n = L.size();
   int64_t n_free = 0;
   for (int64_t node = 0; node < L.g.n_nodes; ++node) n_free += node_constrained(L, node) ? 0 : 1;
-  n_free *= L.nt;
+  n_free *= (int64_t)L.nt * L.nc;
   // the Krylov space lives on the unconstrained DoFs: at most that many steps
   const int steps = (int)std::min<int64_t>(20, n_free);
   std::vector<double> v0(n);
@@ -641,10 +680,18 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
 }
 
 stmg_status setup_transfer(stmg_ctx* ctx, Level& F, const Level& C) {
+  if (F.nc != C.nc) {  // tau-level: fine slabs 2j, 2j+1 under coarse slab j (contiguous in memory)
+    F.tkind = 3;
+    std::vector<double> P = tau_prolongation(F.k);
+    F.tt.ntf = 2 * F.nt; F.tt.ntc = C.nt; F.tt.nb = C.nc;
+    for (int i = 0; i < 2 * F.nt; ++i)
+      for (int j = 0; j < C.nt; ++j) F.tt.P[i][j] = P[i * C.nt + j];
+    return STMG_OK;
+  }
   if (F.k != C.k) {
     F.tkind = 2;
     std::vector<double> P = time_prolongation(ctx->scheme, F.k, C.k);
-    F.tt.ntf = F.nt; F.tt.ntc = C.nt;
+    F.tt.ntf = F.nt; F.tt.ntc = C.nt; F.tt.nb = F.nc;
     for (int i = 0; i < F.nt; ++i)
       for (int j = 0; j < C.nt; ++j) F.tt.P[i][j] = P[i * C.nt + j];
     return STMG_OK;
@@ -687,7 +734,7 @@ stmg_status setup_transfer(stmg_ctx* ctx, Level& F, const Level& C) {
   F.tr.p_w = pw;
   F.tr.r_idx = ri;
   F.tr.r_w = rw;
-  const size_t tmp = (size_t)F.nt * nf * (size_t)(F.dim == 3 ? nf : 1) * nc;
+  const size_t tmp = (size_t)F.nt * F.nc * nf * (size_t)(F.dim == 3 ? nf : 1) * nc;
   double *t1 = nullptr, *t2 = nullptr;
   CKS(dev_alloc(ctx, &t1, tmp));
   CKS(dev_alloc(ctx, &t2, tmp));
@@ -698,7 +745,7 @@ stmg_status setup_transfer(stmg_ctx* ctx, Level& F, const Level& C) {
 
 stmg_status setup_coarse(stmg_ctx* ctx, Level& L) {
   std::vector<int64_t> map;
-  for (int t = 0; t < L.nt; ++t)
+  for (int t = 0; t < L.nt * L.nc; ++t)
     for (int64_t node = 0; node < L.g.n_nodes; ++node)
       if (!node_constrained(L, node)) map.push_back((int64_t)t * L.g.n_nodes + node);
   const int n = (int)map.size();
@@ -746,6 +793,10 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   const int nt = pr->time_scheme == STMG_DG ? pr->k + 1 : pr->k;
   if (nt < 1 || nt > kMaxNT || (pr->time_scheme == STMG_CGP && pr->k < 1)) return invalid(ctx, "time degree out of range");
   if (!(pr->tau > 0.0)) return invalid(ctx, "tau must be positive");
+  const int nslabs = pr->n_slabs == 0 ? 1 : pr->n_slabs;
+  if (nslabs < 1 || nslabs > 64) return invalid(ctx, "n_slabs must be in 1..64");
+  if (nslabs > 1 && (pr->pde != STMG_HEAT || pr->time_scheme != STMG_DG))
+    return invalid(ctx, "several slabs in one system: heat equation with dG in time only");
   ctx->dim = dim; ctx->pde = pr->pde; ctx->scheme = pr->time_scheme; ctx->tau = pr->tau;
   stmg_options o{};
   if (op) o = *op;
@@ -802,7 +853,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     }
     for (double v : rho_f) if (!(v > 0.0) || !std::isfinite(v)) return invalid(ctx, "coefficient must be positive and finite");
   }
-  std::vector<Spec> seq = level_sequence(pr->p, N, pr->k, pr->time_scheme, o.space_coarsening == STMG_COARSEN_P_THEN_H);
+  std::vector<Spec> seq = level_sequence(pr->p, N, pr->k, pr->time_scheme, o.space_coarsening == STMG_COARSEN_P_THEN_H,
+                                         nslabs, pr->tau);
   // a shallower hierarchy: the first coarser level with at most coarse_max_dofs unknowns is the coarsest
   if (o.coarse_max_dofs > 0)
     for (size_t li = 1; li < seq.size(); ++li)
@@ -811,11 +863,12 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   for (size_t li = 0; li < seq.size(); ++li) {
     Level& L = ctx->levels[li];
     L.dim = dim; L.p = seq[li].p; L.n = L.p + 1; L.N = seq[li].N; L.k = seq[li].k;
+    L.nc = seq[li].nc; L.tau = seq[li].tau;
     L.nt = pr->time_scheme == STMG_DG ? L.k + 1 : L.k;
     L.g.dim = dim; L.g.N = L.N; L.g.p = L.p; L.g.nn1 = L.p * L.N + 1;
     L.g.n_nodes = dim == 3 ? (int64_t)L.g.nn1 * L.g.nn1 * L.g.nn1 : (int64_t)L.g.nn1 * L.g.nn1;
     L.g.n_cells = dim == 3 ? (int64_t)L.N * L.N * L.N : (int64_t)L.N * L.N;
-    L.sc = slab_coeffs(pr->pde, pr->time_scheme, L.k, pr->tau);
+    L.sc = slab_coeffs(pr->pde, pr->time_scheme, L.k, L.tau);
     for (int i = 0; i < L.nt; ++i)
       for (int j = 0; j < L.nt; ++j)
         if (i != j && std::fabs(L.sc.TA[i * L.nt + j]) > 1e-13 * std::fabs(L.sc.TA[i * L.nt + i])) {
@@ -823,6 +876,16 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
           return STMG_ERR_INTERNAL;
         }
     fill_tables(L);
+    // coupling to the previous slab (heat dG: the coefficient of M_h u_0 in the slab's right-hand side)
+    L.cpl64 = L.tab64;
+    for (int i = 0; i < kMaxNT; ++i)
+      for (int j = 0; j < kMaxNT; ++j) { L.cpl64.TA[i][j] = 0.0; L.cpl64.TM[i][j] = 0.0; }
+    for (int i = 0; i < L.nt; ++i) L.cpl64.TM[i][L.nt - 1] = -L.sc.RM_u0[i];
+    L.cpl64.sign = 1.0;
+    L.cpl32 = L.tab32;
+    for (int i = 0; i < kMaxNT; ++i)
+      for (int j = 0; j < kMaxNT; ++j) { L.cpl32.TA[i][j] = 0.0f; L.cpl32.TM[i][j] = (float)L.cpl64.TM[i][j]; }
+    L.cpl32.sign = 1.0f;
     // vertices: every (N/N_l)-th fine vertex
     const int r = N / L.N;
     const int64_t lv1 = L.N + 1;
@@ -1124,12 +1187,12 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
   return result;
 }
 
-// rhs = RM_f (x) M f + RM_f0 M f0 + RA_u0 A u0 + RM_u0 M u0 + RM_v0 M v0, constrained rows 0
-stmg_status rhs_impl(stmg_ctx* ctx, const double* f, const double* f0, const double* u0, const double* v0, double* rhs) {
+// One slab: rhs = RM_f (x) M f + RM_f0 M f0 + RA_u0 A u0 + RM_u0 M u0 + RM_v0 M v0, constrained rows 0
+stmg_status rhs_slab(stmg_ctx* ctx, const double* f, const double* f0, const double* u0, const double* v0, double* rhs) {
   Level& L = ctx->levels[0];
   const int nt = L.nt;
   const int64_t nn = L.g.n_nodes;
-  CK(cudaMemsetAsync(rhs, 0, sizeof(double) * L.size(), ctx->stream));
+  CK(cudaMemsetAsync(rhs, 0, sizeof(double) * L.slab_size(), ctx->stream));
   OpTab<double> t = L.tab64;
   for (int i = 0; i < kMaxNT; ++i)
     for (int j = 0; j < kMaxNT; ++j) {
@@ -1172,6 +1235,17 @@ stmg_status rhs_impl(stmg_ctx* ctx, const double* f, const double* f0, const dou
     ctx->launches += 1;
   }
   CK(launch_zero_constrained(rhs, L.g, nt, ctx->stream));
+  return STMG_OK;
+}
+
+// Several slabs in one system (eq. heat-cg-dg-at-once): every slab gets its source term, only the
+// first the previous end value u0 (the later ones take it from the coupling block).
+stmg_status rhs_impl(stmg_ctx* ctx, const double* f, const double* f0, const double* u0, const double* v0, double* rhs) {
+  const Level& L = ctx->levels[0];
+  const int64_t ss = L.slab_size();
+  for (int i = 0; i < L.nc; ++i)
+    CKS(rhs_slab(ctx, f ? f + i * ss : nullptr, i == 0 ? f0 : nullptr, i == 0 ? u0 : nullptr, i == 0 ? v0 : nullptr,
+                 rhs + i * ss));
   return STMG_OK;
 }
 
@@ -1297,6 +1371,13 @@ stmg_status stmg_sizes(const stmg_ctx* ctx, int64_t* n_nodes, int* n_t, int* n_l
   if (n_nodes) *n_nodes = ctx->levels[0].g.n_nodes;
   if (n_t) *n_t = ctx->levels[0].nt;
   if (n_levels) *n_levels = (int)ctx->levels.size();
+  return STMG_OK;
+}
+
+stmg_status stmg_level_slabs(const stmg_ctx* ctx, int level, int* n_slabs, double* tau) {
+  if (!ctx || level < 0 || level >= (int)ctx->levels.size()) return STMG_ERR_INVALID_ARG;
+  if (n_slabs) *n_slabs = ctx->levels[level].nc;
+  if (tau) *tau = ctx->levels[level].tau;
   return STMG_OK;
 }
 
@@ -1442,7 +1523,7 @@ stmg_status stmg_guess_previous(stmg_ctx* ctx, const double* u0, double* u) {
   StreamJoin join_(ctx);
   if (!ctx || !u0 || !u) return STMG_ERR_INVALID_ARG;
   Level& L = ctx->levels[0];
-  CK(launch_broadcast_time(u0, u, L.nt, L.g.n_nodes, ctx->stream));
+  CK(launch_broadcast_time(u0, u, L.nt * L.nc, L.g.n_nodes, ctx->stream));
   ctx->launches += 1;
   return STMG_OK;
 }
@@ -1464,7 +1545,7 @@ stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f
   if (f0) CK(cudaMemcpyAsync(d_f0, f0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
   if (v0) CK(cudaMemcpyAsync(d_v0, v0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
   CKS(rhs_impl(ctx, d_f, f0 ? d_f0 : nullptr, d_u0, v0 ? d_v0 : nullptr, ctx->rhs_buf));
-  CK(launch_broadcast_time(d_u0, d_u, L.nt, nn, ctx->stream));
+  CK(launch_broadcast_time(d_u0, d_u, L.nt * L.nc, nn, ctx->stream));
   ctx->launches += 1;
   stmg_status s = solve_impl(ctx, ctx->rhs_buf, d_u, stats);
   if (s != STMG_OK && s != STMG_ERR_NOT_CONVERGED) return s;
@@ -1537,6 +1618,7 @@ stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int
   if (!out || !ctx || !channels || !weights || !biases || !scales) return STMG_ERR_INVALID_ARG;
   *out = nullptr;
   Level& L0 = ctx->levels[0];
+  if (L0.nc != 1) return invalid(ctx, "the learned guess needs one slab per system");
   if (layers < 1 || layers > kNetMaxLayers) return invalid(ctx, "layers must be in 1..8");
   if (channels[0] != 2 * L0.nt || channels[layers] != L0.nt)
     return invalid(ctx, "network must map 2 N_t input channels to N_t output channels");
@@ -1710,7 +1792,8 @@ stmg_status stmg_solve_slab_host_learned(stmg_ctx* ctx, stmg_net* net, const dou
                                          double* u, int* chosen, stmg_solve_stats* stats) {
   if (!ctx || !net || !f || !u_prev || !u) return STMG_ERR_INVALID_ARG;
   if (net->ctx != ctx) return invalid(ctx, "network is bound to another context");
-  if (ctx->pde != STMG_HEAT || ctx->scheme != STMG_DG) return invalid(ctx, "learned slab step supports heat dG");
+  if (ctx->pde != STMG_HEAT || ctx->scheme != STMG_DG || ctx->levels[0].nc != 1)
+    return invalid(ctx, "learned slab step supports heat dG with one slab per system");
   StreamJoin join_(ctx);
   Level& L = ctx->levels[0];
   const int64_t nn = L.g.n_nodes, n = L.size();

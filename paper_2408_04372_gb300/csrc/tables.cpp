@@ -451,6 +451,17 @@ std::vector<double> time_prolongation(int scheme, int kf, int kc) {
   return P;
 }
 
+std::vector<double> tau_prolongation(int k) {
+  std::vector<double> t, w;
+  gauss_radau_right(k + 1, t, w);
+  const int n = k + 1;
+  std::vector<double> P(2 * n * n, 0.0);
+  for (int h = 0; h < 2; ++h)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) P[(h * n + i) * n + j] = lagrange(t, j, 0.5 * (h + t[i]));
+  return P;
+}
+
 void jacobi_eigen(int n, std::vector<double> a, std::vector<double>& w, std::vector<double>& V) {
   V.assign(n * n, 0.0);
   for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;

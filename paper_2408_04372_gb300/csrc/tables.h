@@ -54,6 +54,9 @@ bool invert_complex(int n, std::vector<cplx>& a);
 void prolongation_1d(int pf, int Nf, int pc, int Nc, std::vector<int>& start, std::vector<double>& w);
 // Time prolongation P_tau (nt_f x nt_c, row-major).
 std::vector<double> time_prolongation(int scheme, int kf, int kc);
+// dG(k) prolongation from one slab of length 2 tau to its two halves of length tau:
+// (2 (k+1)) x (k+1) row-major, row h (k+1) + t = coarse basis functions at fine Radau node t of half h.
+std::vector<double> tau_prolongation(int k);
 
 // Fast diagonalisation tables of one direction of a uniform Cartesian grid (N cells of size h):
 // for cell type t (0: first cell, left node constrained; 1: interior; 2: last cell, right node

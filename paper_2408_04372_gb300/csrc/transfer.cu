@@ -3,7 +3,9 @@
 // Prolongation = embedding of the coarse space in the fine one, taken in the
 // reference coordinates of the structured grid: a Kronecker product of one 1D
 // matrix per direction (space levels, p- or h-coarsening) or the N_t x N_t
-// matrix P_tau on the time blocks (k-levels).  Restriction = transpose.
+// matrix P_tau on the time blocks (k-levels), or, between slabs of length tau and 2 tau
+// (tau-levels), the coarse dG(k) basis evaluated at the Radau nodes of the two fine halves.
+// Restriction = transpose.
 // Space transfers run as separable 1D passes (x, y, z), each in gather form -- every
 // output entry sums its own inputs by index arithmetic on the structured grid -- so no
 // colouring and no atomics are needed, results are deterministic, and a coarse node
@@ -182,16 +184,19 @@ __global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict_
                                        SideJob<T> side) {
   pdl_wait();
   pdl_trigger();
-  for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
-       node += (int64_t)gridDim.x * blockDim.x) {
-    for (int i = 0; i < tt.ntf; ++i) side.run(i * g.n_nodes + node);
+  const int64_t nn = g.n_nodes;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn * tt.nb; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / nn, node = e - b * nn;
+    T* ub = uf + b * tt.ntf * nn;
+    const T* eb = ec + b * tt.ntc * nn;
+    for (int i = 0; i < tt.ntf; ++i) side.run(b * tt.ntf * nn + i * nn + node);
     if (node_on_boundary(node, g)) continue;
     T ev[kMaxNT];
-    for (int j = 0; j < tt.ntc; ++j) ev[j] = ec[j * g.n_nodes + node];
+    for (int j = 0; j < tt.ntc; ++j) ev[j] = eb[j * nn + node];
     for (int i = 0; i < tt.ntf; ++i) {
       T s = 0;
       for (int j = 0; j < tt.ntc; ++j) s += (T)tt.P[i][j] * ev[j];
-      uf[i * g.n_nodes + node] += s;
+      ub[i * nn + node] += s;
     }
   }
 }
@@ -201,16 +206,19 @@ __global__ void restrict_time_kernel(T* __restrict__ rc, const T* __restrict__ r
                                      SideJob<T> side) {
   pdl_wait();
   pdl_trigger();
-  for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
-       node += (int64_t)gridDim.x * blockDim.x) {
-    for (int j = 0; j < tt.ntc; ++j) side.run(j * g.n_nodes + node);
+  const int64_t nn = g.n_nodes;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn * tt.nb; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / nn, node = e - b * nn;
+    T* cb = rc + b * tt.ntc * nn;
+    const T* fb = rf + b * tt.ntf * nn;
+    for (int j = 0; j < tt.ntc; ++j) side.run(b * tt.ntc * nn + j * nn + node);
     const bool bnd = node_on_boundary(node, g);
-    T rv[kMaxNT];
-    for (int i = 0; i < tt.ntf; ++i) rv[i] = bnd ? T(0) : rf[i * g.n_nodes + node];
+    T rv[2 * kMaxNT];
+    for (int i = 0; i < tt.ntf; ++i) rv[i] = bnd ? T(0) : fb[i * nn + node];
     for (int j = 0; j < tt.ntc; ++j) {
       T s = 0;
       for (int i = 0; i < tt.ntf; ++i) s += (T)tt.P[i][j] * rv[i];
-      rc[j * g.n_nodes + node] = s;
+      cb[j * nn + node] = s;
     }
   }
 }
@@ -240,7 +248,7 @@ cudaError_t launch_prolong_time_add(T* uf, const T* ec, const GridDesc& g, const
   SideJob<T> side;
   side.copy_src = copy_src;
   side.copy_dst = copy_dst;
-  { const cudaError_t e_ = launch_k(prolong_time_add_kernel<T>, dim3(grid_blocks(g.n_nodes)), dim3(256), 0, s, uf, ec, g, t, side); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_k(prolong_time_add_kernel<T>, dim3(grid_blocks(g.n_nodes * t.nb)), dim3(256), 0, s, uf, ec, g, t, side); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 template <typename T>
@@ -248,7 +256,7 @@ cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const Ti
                                  cudaStream_t s) {
   SideJob<T> side;
   side.zero_dst = zero_dst;
-  { const cudaError_t e_ = launch_k(restrict_time_kernel<T>, dim3(grid_blocks(g.n_nodes)), dim3(256), 0, s, rc, rf, g, t, side); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_k(restrict_time_kernel<T>, dim3(grid_blocks(g.n_nodes * t.nb)), dim3(256), 0, s, rc, rf, g, t, side); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
