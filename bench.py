@@ -201,7 +201,7 @@ def run_ours(args):
     inv_prec = {"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64}[args.inverse] if not args.plain else stmg.FP64
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                        vcycle_precision=vprec, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
-                       coarse_max_dofs=args.coarse_max_dofs)
+                       coarse_max_dofs=args.coarse_max_dofs, asm_weighting=args.asm_weighting)
     nt, nn = ctx.nt, ctx.n_nodes
     n = nt * nn
     X = ctx.node_coords()
@@ -309,7 +309,7 @@ def run_ours(args):
                                                     "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_m]))}
         ctx64 = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                              vcycle_precision=stmg.FP64, rtol=1e-8, restart=30, max_it=200,
-                             coarse_max_dofs=args.coarse_max_dofs)
+                             coarse_max_dofs=args.coarse_max_dofs, asm_weighting=args.asm_weighting)
         def plain(s):
             prev_end = sols[s][(nt - 1) * nn:]
             ctx64.rhs(F[s], rhs, u0=prev_end)
@@ -321,6 +321,25 @@ def run_ours(args):
         compare["plain_fp64_previous_slab_guess"] = {"value": dofs_per_step * k3 / (t_p / 1e3), "unit": UNIT,
                                                      "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_p]))}
         ctx64.close()
+        if not use_net:
+            # the same solve with the other Schwarz sum (printed eq. vanka0 <-> weighted by node multiplicity)
+            other = 1 - args.asm_weighting
+            ctxw = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
+                                vcycle_precision=vprec, inverse_precision=inv_prec, rtol=1e-8, restart=30,
+                                max_it=200, coarse_max_dofs=args.coarse_max_dofs, asm_weighting=other)
+
+            def weighted(s):
+                prev_end = sols[s][(nt - 1) * nn:]
+                ctxw.rhs(F[s], rhs, u0=prev_end)
+                ctxw.guess_previous(prev_end, u)
+                return ctxw.solve(rhs, u)
+            weighted(slab_of(args.warmup))
+            k4 = min(args.steps, 8)
+            t_w, o_w = timed(weighted, k4)
+            compare[f"asm_weighting_{other}"] = {"value": dofs_per_step * k4 / (t_w / 1e3), "unit": UNIT,
+                                          "fgmres_iterations_mean": float(np.mean([x["iterations"] for x in o_w])),
+                                          "omega": [ctxw.level_info(l)["omega"] for l in range(ctxw.n_levels - 1)]}
+            ctxw.close()
         if args.atonce_slabs > 1:
             compare["at_once"] = at_once_arm(args, stmg, wl, F, sols, dofs_per_step, nt, nn, inv_prec, dev)
 
@@ -396,6 +415,8 @@ def run_ours(args):
             "config": {"workload": wl["name"], "cells": wl["N"] ** 3, "p": wl["p"], "time": f"dG({wl['k']})",
                        "dofs_per_step": dofs_per_step, "rtol": 1e-8, "vcycle": "fp64" if args.plain else "fp32",
                        "guess": "learned (fallback previous slab)" if use_net else "previous slab",
+                       "schwarz_sum": "weighted by inverse node multiplicity" if args.asm_weighting else
+                                      "eq. vanka0 as printed (unweighted)",
                        "dtype_note": f"FP64 FGMRES vectors, dot products and residuals; FGMRES operator apply in double-float "
                                      f"(FP32 pairs) on the FP32 V-cycle outputs; FP32 V-cycle; "
                                      f"{args.inverse.upper()} Schwarz inverses",
@@ -428,7 +449,7 @@ def at_once_arm(args, stmg, wl, F, sols, dofs_per_step, nt, nn, inv_prec, dev):
     n = nt * nn
     ctxb = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                         vcycle_precision=stmg.FP32, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
-                        n_slabs=nc)
+                        n_slabs=nc, asm_weighting=args.asm_weighting)
     rb = torch.empty(nc * n, dtype=torch.float64, device=dev)
     ub = torch.empty_like(rb)
     prev_end = sols[0][(nt - 1) * nn:]
@@ -467,7 +488,8 @@ def run_learned_c5(args):
     N, p, k, n_slabs = args.n_cells if args.n_cells != 32 else 48, 2, 1, 256
     tau = 1.0 / n_slabs
     n_train = n_slabs // 2
-    ctx = stmg.Context(3, N, p, k, tau, vcycle_precision=stmg.FP32, rtol=1e-8, restart=30, max_it=200)
+    ctx = stmg.Context(3, N, p, k, tau, vcycle_precision=stmg.FP32, rtol=1e-8, restart=30, max_it=200,
+                       asm_weighting=args.asm_weighting)
     nt, nn = ctx.nt, ctx.n_nodes
     n = nt * nn
     X = ctx.node_coords()
@@ -572,7 +594,7 @@ def run_c4(args):
     for name, prec in (("mixed_fp32_vcycle", stmg.FP32), ("plain_fp64", stmg.FP64)):
         t0 = time.perf_counter()
         ctx = stmg.Context(3, N, p, k, tau, vertices=None, coeff=rho_qp.reshape(-1), coeff_mode=stmg.COEFF_PER_QPOINT,
-                           vcycle_precision=prec, rtol=1e-8, restart=30, max_it=200)
+                           vcycle_precision=prec, rtol=1e-8, restart=30, max_it=200, asm_weighting=args.asm_weighting)
         t_setup = time.perf_counter() - t0
         nt, nn = ctx.nt, ctx.n_nodes
         X = ctx.node_coords()
@@ -685,6 +707,9 @@ def main():
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")
+    ap.add_argument("--asm-weighting", type=int, default=1, choices=[0, 1],
+                    help="1: each cell's Schwarz correction divided by the node's cell count (reading of the "
+                         "paper's omega range and iteration tables); 0: the sum of eq. vanka0 as printed")
     ap.add_argument("--atonce-slabs", type=int, default=8,
                     help="comparison arm: the first n slabs as one system with tau-multigrid (0 = off)")
     ap.add_argument("--coarse-max-dofs", type=int, default=1500,

@@ -100,7 +100,8 @@ typedef struct {
 /* Solver options.  Zero-initialised fields take the defaults in brackets.
  * omega: HOST array with one relaxation weight per smoothed level (all levels
  * but the coarsest), copied at create; NULL estimates each by eq. relaxation
- * (20-step Arnoldi on S_l B_l, omega = 2/(Re lambda_max + Re lambda_min)). */
+ * (20-step Arnoldi on S_l B_l, omega = min(1, 2/(Re lambda_max + Re lambda_min)):
+ * the paper takes omega_l in (0, 1)). */
 typedef struct {
   int nu_pre;              /* pre-smoothing sweeps nu_1 of Algorithm stmg [1] */
   int nu_post;             /* post-smoothing sweeps nu_2 [1] */
@@ -122,6 +123,10 @@ typedef struct {
   int coarse_max_dofs;     /* 1..4096: the hierarchy ends at the first coarser level with at most this many
                               unknowns, solved exactly by its dense inverse; 0: the full sequence down to
                               2^dim cells and the lowest time degree [0] */
+  int asm_weighting;       /* 0: the additive Schwarz sum of eq. vanka0 as printed; 1: each cell's
+                              correction at a node divided by the number of cells that contain the
+                              node (a partition of unity; with it the omega estimate reaches the cap 1
+                              on the coarse levels) [0] */
 } stmg_options;
 
 enum { STMG_COARSEN_P_THEN_H = 0, STMG_COARSEN_H = 1 };

@@ -112,7 +112,7 @@ class AtOnceLevel:
 class AtOnceHierarchy:
     """V-cycle (Algorithm stmg) for the at-once system, finest level first."""
 
-    def __init__(self, dim, N, p, k, tau, nc, vertices, rho_cell=None, omegas=None, estimate=True):
+    def __init__(self, dim, N, p, k, tau, nc, vertices, rho_cell=None, omegas=None, estimate=True, weighted=False):
         self.specs = level_sequence(p, N, k, nc, tau)
         fine = Grid(N, dim, p, vertices)
         rho_cell = np.ones(fine.n_cells) if rho_cell is None else np.asarray(rho_cell, np.float64)
@@ -146,7 +146,7 @@ class AtOnceHierarchy:
             Dc = sp.diags((~c.prob.bmask_full).astype(np.float64))
             f.P = (Df @ P @ Dc).tocsr()
         for li, lev in enumerate(self.levels[:-1]):
-            lev.B = sp.kron(sp.identity(lev.spec.nc), mg.asm_operator(lev.prob.slab)).tocsr()
+            lev.B = sp.kron(sp.identity(lev.spec.nc), mg.asm_operator(lev.prob.slab, weighted)).tocsr()
             if omegas is not None:
                 lev.omega = float(omegas[li])
             elif estimate:

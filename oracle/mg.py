@@ -19,11 +19,15 @@ Paper sections and the readings taken where it is silent:
   * smoother (eqs. vanka0, vanka): blocks = all unconstrained DoFs of one
     space-time cell (one spatial cell x all N_t time DoFs of the slab), local
     matrix = R_T S R_T^T of the global S (neighbour contributions included),
-    solved exactly; u <- u + omega * sum_T R_T^T L_T^-1 R_T (f - S u).
+    solved exactly; u <- u + omega * sum_T R_T^T L_T^-1 R_T (f - S u).  Option
+    (weighted=True, not in the printed eq. vanka0): each cell's correction at a node is
+    divided by the number of cells that contain the node, sum_T R_T^T D_T L_T^-1 R_T
+    with sum_T R_T^T D_T R_T = I (a partition of unity).
   * relaxation (eq. relaxation): omega = 2 / (lambda_max + lambda_min), with the
     extreme real parts of the Ritz values of an Arnoldi process on S_l B_l with
     min(20, number of unconstrained DoFs) steps from the counter-based start
-    vector synth.splitmix_uniform(n, key=level).
+    vector synth.splitmix_uniform(n, key=level); capped at 1, since the paper takes
+    omega_l in (0, 1) (Section 3.3).
   * coarsest level: exact solve; no smoothing there (Algorithm stmg).
 """
 from __future__ import annotations
@@ -139,8 +143,17 @@ class Level:
     interior: np.ndarray = field(default=None)
 
 
-def asm_operator(prob: SlabProblem) -> sp.csr_matrix:
-    """sum over spatial cells T of R_T^T [R_T S R_T^T]^-1 R_T  (eq. vanka0), unconstrained DoFs only."""
+def node_multiplicity(grid: Grid) -> np.ndarray:
+    """Number of cells that contain each node."""
+    m = np.zeros(grid.n_nodes)
+    for c in grid.cell_dofs():
+        m[c] += 1.0
+    return m
+
+
+def asm_operator(prob: SlabProblem, weighted: bool = False) -> sp.csr_matrix:
+    """sum over spatial cells T of R_T^T [R_T S R_T^T]^-1 R_T  (eq. vanka0), unconstrained DoFs only;
+    weighted: rows scaled by the inverse node multiplicity (partition of unity over the cells)."""
     g = prob.grid
     dofs = g.cell_dofs()
     S = prob.S.tocsr()
@@ -157,7 +170,10 @@ def asm_operator(prob: SlabProblem) -> sp.csr_matrix:
         cols.append(np.tile(idx, len(idx)))
         vals.append(Li.reshape(-1))
     n = prob.n
-    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    B = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    if weighted:
+        B = (sp.diags(np.tile(1.0 / node_multiplicity(g), prob.nt)) @ B).tocsr()
+    return B
 
 
 def arnoldi_ritz(matvec, v0: np.ndarray, m: int) -> np.ndarray:
@@ -197,14 +213,14 @@ def estimate_omega(prob: SlabProblem, B: sp.csr_matrix, key: int, steps: int = 2
     ritz = arnoldi_ritz(lambda v: prob.S @ (B @ v), v0, steps)
     re = np.real(ritz)
     re = re[np.abs(ritz) > 1e-12]
-    return float(2.0 / (re.max() + re.min()))
+    return float(min(1.0, 2.0 / (re.max() + re.min())))
 
 
 class Hierarchy:
     """All levels of the STMG V-cycle for one slab problem (finest level first)."""
 
     def __init__(self, dim, N, p, k, pde, scheme, tau, vertices, rho_cell=None, rho_qp=None,
-                 omegas=None, estimate=True, p_coarsening=True, coarse_max_dofs=0):
+                 omegas=None, estimate=True, p_coarsening=True, coarse_max_dofs=0, weighted=False):
         self.specs = level_sequence(p, N, k, scheme, p_coarsening, coarse_max_dofs, dim)
         self.pde, self.scheme = pde, scheme
         fine = Grid(N, dim, p, vertices)
@@ -238,7 +254,7 @@ class Hierarchy:
             Dc = sp.diags(c.interior.astype(np.float64))
             f.P = (Df @ P @ Dc).tocsr()
         for li, lev in enumerate(self.levels[:-1]):
-            lev.B = asm_operator(lev.prob)
+            lev.B = asm_operator(lev.prob, weighted)
             if omegas is not None:
                 lev.omega = float(omegas[li])
             elif estimate:

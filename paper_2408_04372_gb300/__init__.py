@@ -55,7 +55,8 @@ class Options(ctypes.Structure):
                 ("inverse_precision", ctypes.c_int), ("smoother_kind", ctypes.c_int),
                 ("omega", ctypes.POINTER(ctypes.c_double)), ("fgmres_restart", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("outer_apply", ctypes.c_int),
-                ("atol", ctypes.c_double), ("space_coarsening", ctypes.c_int), ("coarse_max_dofs", ctypes.c_int)]
+                ("atol", ctypes.c_double), ("space_coarsening", ctypes.c_int), ("coarse_max_dofs", ctypes.c_int),
+                ("asm_weighting", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -135,7 +136,7 @@ class Context:
     def __init__(self, dim, n_cells, p, k, tau, pde=HEAT, scheme=DG, vertices=None, coeff=None,
                  coeff_mode=COEFF_PER_CELL, nu_pre=1, nu_post=1, vcycle_precision=FP32, inverse_precision=0,
                  omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO,
-                 outer_apply=0, atol=0.0, space_coarsening=0, coarse_max_dofs=0, n_slabs=1):
+                 outer_apply=0, atol=0.0, space_coarsening=0, coarse_max_dofs=0, n_slabs=1, asm_weighting=0):
         import numpy as np
         import torch
         self.lib = load()
@@ -148,7 +149,7 @@ class Context:
         mesh = Mesh(dim, n_cells, _dptr(v))
         prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c), int(n_slabs))
         opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, smoother_kind, _dptr(om), restart, rtol,
-                       max_it, outer_apply, float(atol), space_coarsening, coarse_max_dofs)
+                       max_it, outer_apply, float(atol), space_coarsening, coarse_max_dofs, asm_weighting)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -246,6 +246,7 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
   if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
   const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
   const bool live = active && !bnd;
+  const T wsc = mt.weighted ? mt.omega * node_weight<T>(gx, gy, gz, DIM, g.p) : mt.omega;
   T rr[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
@@ -307,7 +308,7 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
         o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
       }
     }
-    atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
+    atomicAdd(u + t * g.n_nodes + node, wsc * o);
   }
 }
 
@@ -448,7 +449,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
   // residual (and side-job source) of a group's node for this thread, loaded one group ahead so
   // that their latency overlaps the previous group's work
   const int slot = tid / NB, a = tid - slot * NB;
-  struct Pre { int64_t node; bool active, live; T rr[NT], cp[NT]; };
+  struct Pre { int64_t node; bool active, live; T w; T rr[NT], cp[NT]; };
   // work item (group grp, slab sl): the node of this thread and slab sl's residual there
   auto prefetch = [&](int64_t grp, int sl, Pre& P) {
     const int64_t cell = grp * CPG + slot;
@@ -465,6 +466,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
     P.node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
     P.live = !bnd;
+    P.w = mt.weighted ? mt.omega * node_weight<T>(gx, gy, gz, DIM, g.p) : mt.omega;
 #pragma unroll
     for (int t = 0; t < NT; ++t) P.rr[t] = P.live ? r[so + t * g.n_nodes + P.node] : T(0);
     if (copy_dst) {
@@ -483,6 +485,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     else prefetch(grp + gridDim.x, 0, nxt);
     const bool active = cur.active, live = cur.live;
     const int64_t node = so + cur.node;
+    const T wsc = cur.w;
     // modal residual of this group's cells (independent of the copy in flight)
     if (active) {
       if (copy_dst) {
@@ -554,7 +557,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
             o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
           }
         }
-        atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
+        atomicAdd(u + t * g.n_nodes + node, wsc * o);
       }
     }
     __syncthreads();  // s_r free again (and, after the last slab, the stage)

@@ -73,7 +73,19 @@ struct ModeTab {
   T Vr[kMaxNT][kMaxNT], Vi[kMaxNT][kMaxNT];
   T lre[kMaxNT], lim[kMaxNT];   // eigenvalues of the representative modes
   T omega;
+  int weighted;  // 1: each cell's correction at a node divided by the number of cells containing the node
 };
+
+// 1 / (number of cells that contain an unconstrained node) on the structured grid: a factor 1/2 for
+// every direction in which the node index is a multiple of p (a face shared by two cells)
+template <typename T>
+__device__ __forceinline__ T node_weight(int gx, int gy, int gz, int dim, int p) {
+  T w = T(1);
+  if (gx % p == 0) w *= T(0.5);
+  if (gy % p == 0) w *= T(0.5);
+  if (dim == 3 && gz % p == 0) w *= T(0.5);
+  return w;
+}
 
 // Fast diagonalisation tables for the three 1D cell types (first, interior, last cell):
 // S[t][a][i] = component a of the M1-orthonormal eigenvector i, lam[t][i] its eigenvalue.

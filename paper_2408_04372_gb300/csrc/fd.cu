@@ -158,6 +158,7 @@ fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict_
     const int gz = cz * g.p + k;
     if (!active || bxy || on_boundary(gz, g.nn1)) continue;
     const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+    const T wsc = mt.weighted ? mt.omega * node_weight<T>(gx, gy, gz, 3, g.p) : mt.omega;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       T o = 0;
@@ -170,7 +171,7 @@ fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict_
           o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
         }
       }
-      atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
+      atomicAdd(u + t * g.n_nodes + node, wsc * o);
     }
   }
 }

@@ -560,7 +560,7 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
     ctx->err += ")";
     return STMG_ERR_INTERNAL;
   }
-  L.omega = 2.0 / (lmax + lmin);
+  L.omega = std::min(1.0, 2.0 / (lmax + lmin));  // the paper takes omega_l in (0, 1) (Section 3.3)
   return STMG_OK;
 }
 
@@ -613,6 +613,7 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     }
   }
   mt.omega = 1.0;
+  mt.weighted = ctx->opt.asm_weighting;
   L.mt64 = mt;
   ModeTab<float> mf{};
   mf.nreal = mt.nreal; mf.ncplx = mt.ncplx;
@@ -623,6 +624,7 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     }
   for (int a = 0; a < kMaxNT; ++a) { mf.lre[a] = (float)mt.lre[a]; mf.lim[a] = (float)mt.lim[a]; }
   mf.omega = 1.0f;
+  mf.weighted = mt.weighted;
   L.mt32 = mf;
   if (L.fd) {
     std::vector<double> S, lamfd;
@@ -811,6 +813,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (o.space_coarsening != STMG_COARSEN_P_THEN_H && o.space_coarsening != STMG_COARSEN_H)
     return invalid(ctx, "space_coarsening out of range");
   if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096) return invalid(ctx, "coarse_max_dofs must be in 0..4096");
+  if (o.asm_weighting != 0 && o.asm_weighting != 1) return invalid(ctx, "asm_weighting must be 0 or 1");
   if (o.max_it <= 0) o.max_it = 200;
   if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
   if (o.outer_apply == 0) o.outer_apply = o.vcycle_precision == STMG_FP32 ? STMG_DF32 : STMG_FP64;

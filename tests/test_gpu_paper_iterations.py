@@ -45,11 +45,12 @@ def _source(pde, S, t):
     return 2 * W * W * np.sin(W * t) * S
 
 
-def _mean_iterations(torch, stmg, pde, scheme, k, r):
+def _mean_iterations(torch, stmg, pde, scheme, k, r, weighting=0):
     N, nsl = 2 ** (r + 1), 4 * 2 ** r
     tau = 1.0 / nsl
     ctx = stmg.Context(3, N, k, k, tau, pde=stmg.HEAT if pde == "heat" else stmg.WAVE,
-                       scheme=stmg.DG if scheme == "dg" else stmg.CGP, rtol=1e-12, atol=1e-12, max_it=400)
+                       scheme=stmg.DG if scheme == "dg" else stmg.CGP, rtol=1e-12, atol=1e-12, max_it=400,
+                       asm_weighting=weighting)
     nt, nn = ctx.nt, ctx.n_nodes
     X = ctx.node_coords()
     S = np.prod(np.sin(W * X), axis=1)
@@ -97,4 +98,19 @@ def test_iterations_grid_independent_and_near_the_paper(env, pde, scheme, k):
     assert its[3] <= its[2] + 1.0, its
     # convergence under refinement of h and tau together: at least the order k + 1 the paper reports
     # (Figures conv-heat and conv-wave)
+    assert res[3][1] < 1e-3 and res[2][1] / res[3][1] >= 0.8 * 2 ** (k + 1), res
+
+
+@pytest.mark.parametrize("pde,scheme,k", CASES, ids=lambda v: str(v))
+def test_weighted_smoother_iterations_at_most_the_papers(env, pde, scheme, k):
+    """With each cell's correction divided by the node's cell count (option asm_weighting) the counts
+    are at or below the printed ones, grid independent, with the same errors."""
+    torch, stmg = env
+    table = _table(pde, scheme)
+    res = {r: _mean_iterations(torch, stmg, pde, scheme, k, r, weighting=1) for r in (2, 3)}
+    its = {r: v[0] for r, v in res.items()}
+    print(f"\n{pde} {scheme}({k}) weighted: mean iterations {its}, errors at t = 1 {[res[r][1] for r in (2, 3)]}")
+    for r, v in its.items():
+        assert v <= 1.25 * table[k][r], (pde, scheme, k, r, v, table[k][r])
+    assert its[3] <= its[2] + 1.0, its
     assert res[3][1] < 1e-3 and res[2][1] / res[3][1] >= 0.8 * 2 ** (k + 1), res

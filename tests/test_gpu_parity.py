@@ -273,3 +273,51 @@ def test_fast_diagonalisation_as_approximate_solver_for_variable_coefficient(env
     ctx.apply(torch.from_numpy(x).cuda(), y)
     assert rel_err(y.cpu().numpy(), prob.S @ x) < TOL64
     ctx.close()
+
+
+_HW = {}
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[7]], ids=lambda c: c.name)
+def test_weighted_smoother_vcycle_and_solve(env, case):
+    """Option asm_weighting = 1: each cell's correction divided by the node's cell count (dense
+    inverses, TMA-fed and row-streamed, and fast diagonalisation), against the weighted oracle."""
+    torch, stmg = env
+    from oracle import mg
+    if case.name not in _HW:
+        _HW[case.name] = mg.Hierarchy(case.dim, case.N, case.p, case.k, case.pde, case.scheme, case.tau,
+                                      case.vertices(), rho_cell=case.rho_cell(), weighted=True)
+    H = _HW[case.name]
+    assert all(0.0 < w <= 1.0 for w in H.omegas())
+    ctx = make_context(stmg, case, H, vcycle_precision=stmg.FP64, asm_weighting=1)
+    for li, lev in enumerate(H.levels[:-1]):
+        prob = lev.prob
+        f = _rand(prob.n, 800 + li, prob.bmask_full)
+        u = _rand(prob.n, 900 + li, prob.bmask_full)
+        ref = u + lev.omega * (lev.B @ (f - prob.S @ u))
+        ud = torch.from_numpy(u).cuda()
+        ctx.smooth(torch.from_numpy(f).cuda(), ud, sweeps=1, level=li)
+        assert rel_err(ud.cpu().numpy(), ref) < 1e-9, (case.name, li)
+        u32 = torch.from_numpy(u).to("cuda", torch.float32)
+        ctx.smooth(torch.from_numpy(f).to("cuda", torch.float32), u32, sweeps=1, level=li)
+        assert rel_err(u32.cpu().numpy(), ref) < 1e-4, (case.name, li)
+    prob = H.levels[0].prob
+    r = _rand(prob.n, 1000, prob.bmask_full)
+    e = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.from_numpy(r).cuda(), e)
+    assert rel_err(e.cpu().numpy(), H.vcycle(r)) < 1e-9, case.name
+    ctx.close()
+    # the library's own relaxation estimate (capped at 1) and a mixed-precision solve
+    ctx = stmg.Context(case.dim, case.N, case.p, case.k, case.tau,
+                       pde=stmg.HEAT if case.pde == "heat" else stmg.WAVE,
+                       scheme=stmg.DG if case.scheme == "dg" else stmg.CGP, vertices=case.vertices(),
+                       coeff=case.rho_cell(), asm_weighting=1, rtol=1e-12, max_it=200)
+    for li in range(ctx.n_levels - 1):
+        assert 0.0 < ctx.level_info(li)["omega"] <= 1.0
+    b = _rand(prob.n, 1001, prob.bmask_full)
+    u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st = ctx.solve(torch.from_numpy(b).cuda(), u)
+    assert st["converged"]
+    xd = prob.solve(b).reshape(-1)
+    assert np.linalg.norm(u.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-8
+    ctx.close()

@@ -83,6 +83,45 @@ def test_asm_operator_brute_force_and_closed_form():
     assert np.isclose((B @ prob.S)[c, c], 4.0)
 
 
+def _multiplicity_by_coordinates(g):
+    """cells containing each node, from logical coordinates: a factor 2 per direction in which the
+    node lies on an interior cell face (index a multiple of p, not on the domain boundary)"""
+    gl = space.lex_indices(g.nn1, g.dim)
+    shared = (gl % g.p == 0) & (gl > 0) & (gl < g.nn1 - 1)
+    return np.prod(np.where(shared, 2.0, 1.0), axis=1)
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 3, 2), (3, 2, 2), (2, 4, 1)])
+def test_weighted_asm_is_a_partition_of_unity_and_matches_brute_force(dim, N, p):
+    g = space.Grid(N, dim, p, synth.jittered_vertices(N, dim))
+    prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, synth.block_coefficient(N, dim, blocks=1)), "heat", "dg",
+                            1, 0.1)
+    m = _multiplicity_by_coordinates(g)
+    inner = ~prob.bmask
+    assert np.array_equal(mg.node_multiplicity(g)[inner], m[inner])
+    # sum_T R_T^T D_T R_T = I on the unconstrained nodes
+    pu = np.zeros(g.n_nodes)
+    for c in g.cell_dofs():
+        pu[c] += 1.0 / m[c]
+    assert np.allclose(pu[inner], 1.0)
+    Bw = mg.asm_operator(prob, weighted=True).toarray()
+    ref = np.tile(1.0 / m, prob.nt)[:, None] * _explicit_asm_by_coordinates(prob)
+    assert np.abs(Bw - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,k", [(2, 0), (3, 1), (2, 2)])
+def test_weighted_asm_is_exact_when_every_cell_holds_all_unknowns(dim, k):
+    """Q1 on 2^dim cells: the one unconstrained node lies in every cell, each cell block is the whole
+    unconstrained system, and the weighted sum is its inverse: B S = I there (the plain sum gives 2^dim I)."""
+    g = space.Grid(2, dim, 1, synth.jittered_vertices(2, dim))
+    prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, np.ones(2 ** dim)), "heat", "dg", k, 0.1)
+    inner = ~prob.bmask_full
+    BS = (mg.asm_operator(prob, weighted=True) @ prob.S).toarray()[np.ix_(inner, inner)]
+    assert np.allclose(BS, np.eye(inner.sum()), atol=1e-12)
+    BS0 = (mg.asm_operator(prob) @ prob.S).toarray()[np.ix_(inner, inner)]
+    assert np.allclose(BS0, 2 ** dim * np.eye(inner.sum()), atol=1e-11)
+
+
 def test_asm_symmetric_positive_for_symmetric_operator():
     g = space.Grid(3, 2, 2, synth.jittered_vertices(3, 2))
     prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, np.ones(9)), "heat", "dg", 0, 0.1)
@@ -126,3 +165,15 @@ def test_vcycle_contracts_and_fgmres_reaches_direct_solution():
     xd = prob.solve(b).reshape(-1)
     assert res.rel_residual < 1e-11
     assert np.linalg.norm(res.x - xd) < 1e-9 * np.linalg.norm(xd)
+
+
+def test_relaxation_estimate_is_capped_at_one():
+    """eq. relaxation with omega_l in (0, 1) (Section 3.3): the weighted Schwarz sum has lambda_max near 1,
+    so the raw estimate 2 / (lambda_max + lambda_min) exceeds 1 and is capped; the plain sum stays below."""
+    V = synth.jittered_vertices(4, 2)
+    Hw = mg.Hierarchy(2, 4, 2, 1, "heat", "dg", 0.05, V, weighted=True)
+    Hp = mg.Hierarchy(2, 4, 2, 1, "heat", "dg", 0.05, V)
+    assert all(0.0 < w <= 1.0 for w in Hw.omegas()) and max(Hw.omegas()) == 1.0
+    assert all(0.0 < w < 1.0 for w in Hp.omegas())
+    # the coarse level with one unconstrained node: weighted B S = I, so lambda = 1 and omega = 1
+    assert Hw.omegas()[-1] == 1.0
