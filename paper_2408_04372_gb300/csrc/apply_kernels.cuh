@@ -29,6 +29,16 @@ __device__ __forceinline__ void add_out(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void add_out(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void add_out(double* p, df64 v) { atomicAdd(p, df_to_double(v)); }
 
+// Gathered input in the arithmetic's terms: an FP64 input entering double-float arithmetic is split
+// into two floats (x = hi + lo to 48 bits, below the arithmetic's own 44); other inputs keep their type.
+template <typename T, typename TI> struct gather_of { using type = TI; };
+template <> struct gather_of<df64, double> { using type = df64; };
+template <typename G, typename TI> __device__ __forceinline__ G to_gather(TI v) { return (G)v; }
+template <> __device__ __forceinline__ df64 to_gather<df64, double>(double v) {
+  const float h = __double2float_rn(v);
+  return df64(h, __double2float_rn(v - (double)h));
+}
+
 // T: arithmetic (float, double or double-float), TI: input vector type, TO: output vector type.
 // MASS: mass part only, y (+)= sign * (TM (x) M_h) x (no derivative sweeps, TA ignored).
 template <int N, int NT, typename T, int CPB, typename TI, typename TO, bool MASS = false>
@@ -69,7 +79,8 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
 
   // gather + interpolation in z (registers)
   {
-    TI xcol[NT][N];
+    using GI = typename gather_of<T, TI>::type;
+    GI xcol[NT][N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const int gz = cz * g.p + k;
@@ -77,7 +88,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
 #pragma unroll
       for (int t = 0; t < NT; ++t)
-        xcol[t][k] = (active && !(mask_input && bnd)) ? x[t * g.n_nodes + node] : TI(0);
+        xcol[t][k] = (active && !(mask_input && bnd)) ? to_gather<GI>(x[t * g.n_nodes + node]) : GI(0);
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t)
@@ -254,7 +265,8 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   const int gx = cx * g.p + i;
   const bool bx = on_boundary(gx, g.nn1);
   {
-    TI xcol[NT][N];
+    using GI = typename gather_of<T, TI>::type;
+    GI xcol[NT][N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const int gy = cy * g.p + k;
@@ -262,7 +274,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       const int64_t node = gx + (int64_t)g.nn1 * gy;
 #pragma unroll
       for (int t = 0; t < NT; ++t)
-        xcol[t][k] = (active && !(mask_input && bnd)) ? x[t * g.n_nodes + node] : TI(0);
+        xcol[t][k] = (active && !(mask_input && bnd)) ? to_gather<GI>(x[t * g.n_nodes + node]) : GI(0);
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t)

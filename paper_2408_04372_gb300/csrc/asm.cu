@@ -47,7 +47,8 @@ __device__ inline double2 cinv(double2 a) {
 template <int DIM, int N>
 __global__ void __launch_bounds__(256)
 asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const double* __restrict__ lam_re,
-                 const double* __restrict__ lam_im, int nreal, int ncplx, void* __restrict__ inv_out, int inv_prec) {
+                 const double* __restrict__ lam_im, int nreal, int ncplx, void* __restrict__ inv_out, int inv_prec,
+                 int weighted) {
   constexpr int NB = Shape<DIM, N>::NB;
   constexpr int NQ = NB;
   constexpr int NG = DIM == 3 ? 7 : 4;
@@ -188,7 +189,10 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
       for (int pr = tid; pr < NB * NBP; pr += blockDim.x) {
         const int a = pr / NBP, b = pr % NBP;
         const double2 v = b < NB ? C[a * NB + b] : make_double2(0.0, 0.0);
-        const double x = pl == 0 ? v.x : v.y;
+        double x = pl == 0 ? v.x : v.y;
+        // weighted sum: row a (the cell's node a) divided by the number of cells containing the node;
+        // the factor is a power of two, exact in every storage type, and commutes with the time modes
+        if (weighted) x *= node_weight<double>(cx * p + a % N, cy * p + (a / N) % N, cz * p + a / (N * N), DIM, p);
         if (inv_prec == 0) reinterpret_cast<double*>(inv_out)[base + pr] = x;
         else if (inv_prec == 1) reinterpret_cast<float*>(inv_out)[base + pr] = (float)x;
         else reinterpret_cast<__nv_bfloat16*>(inv_out)[base + pr] = __float2bfloat16((float)x);
@@ -246,7 +250,6 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
   if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
   const int64_t node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
   const bool live = active && !bnd;
-  const T wsc = mt.weighted ? mt.omega * node_weight<T>(gx, gy, gz, DIM, g.p) : mt.omega;
   T rr[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) rr[t] = live ? r[t * g.n_nodes + node] : T(0);
@@ -308,7 +311,7 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
         o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
       }
     }
-    atomicAdd(u + t * g.n_nodes + node, wsc * o);
+    atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
   }
 }
 
@@ -335,6 +338,8 @@ struct TmaCfg {
   static constexpr int S = 2;  // measured on GB300: two stages (more CTAs per SM) beat three or four
   static constexpr size_t SMEM = (size_t)S * STAGE_BYTES;
 };
+
+
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -402,11 +407,14 @@ __global__ void wait_selftest_kernel(int* status) {
   if (!mbar_wait(&bar, 0u, nullptr)) atomicExch(status, STMG_DEVICE_TIMEOUT);
 }
 
-template <int DIM, int N, int NT, typename T, typename TI>
+// MULTI: several slabs (the slab loop and its offsets exist only in this instance, so that the
+// one-slab kernel keeps its registers and occupancy)
+template <int DIM, int N, int NT, typename T, typename TI, bool MULTI>
 __global__ void __launch_bounds__(TmaCfg<DIM, N, NT, TI>::THREADS)
 asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restrict__ inv, GridDesc g,
                      ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst, int* status,
-                     int nslab, int64_t slab_stride) {
+                     int nslab_arg, int64_t slab_stride) {
+  const int nslab = MULTI ? nslab_arg : 1;
   pdl_wait();
   pdl_trigger();
   using C = TmaCfg<DIM, N, NT, TI>;
@@ -449,7 +457,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
   // residual (and side-job source) of a group's node for this thread, loaded one group ahead so
   // that their latency overlaps the previous group's work
   const int slot = tid / NB, a = tid - slot * NB;
-  struct Pre { int64_t node; bool active, live; T w; T rr[NT], cp[NT]; };
+  struct Pre { int64_t node; bool active, live; T rr[NT], cp[NT]; };
   // work item (group grp, slab sl): the node of this thread and slab sl's residual there
   auto prefetch = [&](int64_t grp, int sl, Pre& P) {
     const int64_t cell = grp * CPG + slot;
@@ -457,7 +465,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     P.live = false;
     P.node = 0;
     if (!P.active) return;
-    const int64_t so = (int64_t)sl * slab_stride;
+    const int64_t so = MULTI ? (int64_t)sl * slab_stride : 0;
     const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
     const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
     const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
@@ -466,7 +474,6 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
     P.node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
     P.live = !bnd;
-    P.w = mt.weighted ? mt.omega * node_weight<T>(gx, gy, gz, DIM, g.p) : mt.omega;
 #pragma unroll
     for (int t = 0; t < NT; ++t) P.rr[t] = P.live ? r[so + t * g.n_nodes + P.node] : T(0);
     if (copy_dst) {
@@ -480,12 +487,11 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     const int stage = (int)(k % S);
     const uint32_t parity = (uint32_t)((k / S) & 1);
    for (int sl = 0; sl < nslab; ++sl) {
-    const int64_t so = (int64_t)sl * slab_stride;
+    const int64_t so = MULTI ? (int64_t)sl * slab_stride : 0;
     if (sl + 1 < nslab) prefetch(grp, sl + 1, nxt);
     else prefetch(grp + gridDim.x, 0, nxt);
     const bool active = cur.active, live = cur.live;
     const int64_t node = so + cur.node;
-    const T wsc = cur.w;
     // modal residual of this group's cells (independent of the copy in flight)
     if (active) {
       if (copy_dst) {
@@ -557,11 +563,11 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
             o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
           }
         }
-        atomicAdd(u + t * g.n_nodes + node, wsc * o);
+        atomicAdd(u + t * g.n_nodes + node, mt.omega * o);
       }
     }
     __syncthreads();  // s_r free again (and, after the last slab, the stage)
-    cur = nxt;
+    if (sl + 1 < nslab) cur = nxt;
    }
     if (s_fail) break;
     const int64_t next = grp + (int64_t)S * gridDim.x;
@@ -570,6 +576,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
         tma_bulk_load(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage]);
       ++issued;
     }
+    cur = nxt;  // the next group's first slab
   }
   // after a timeout: wait (bounded) for the copies still in flight before the CTA exits
   if (s_fail) {
@@ -579,14 +586,36 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
 
 template <int DIM, int N>
 cudaError_t setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, const double* lr, const double* li,
-                    int nreal, int ncplx, void* inv, int inv_prec, cudaStream_t s) {
+                    int nreal, int ncplx, void* inv, int inv_prec, int weighted, cudaStream_t s) {
   constexpr int NB = Shape<DIM, N>::NB;
   const size_t smem = (size_t)2 * NB * NB * sizeof(double) + (size_t)NB * NB * sizeof(double2) +
                       NB * sizeof(double2) + NB * sizeof(int);
   auto k = asm_setup_kernel<DIM, N>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)g.n_cells, 256, smem, s>>>(g, geo64, lt, lr, li, nreal, ncplx, inv, inv_prec);
+  k<<<(unsigned)g.n_cells, 256, smem, s>>>(g, geo64, lt, lr, li, nreal, ncplx, inv, inv_prec, weighted);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NT, typename T, typename TI, bool MULTI>
+cudaError_t launch_tma(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd,
+                       int* status, int nslab, int64_t ss, cudaStream_t s) {
+  using C = TmaCfg<DIM, N, NT, TI>;
+  auto k = asm_apply_tma_kernel<DIM, N, NT, T, TI, MULTI>;
+  static int per_sm = 0, sms = 0;  // one value per instantiation (same device for all contexts)
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
+  const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+  { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), C::SMEM, s, r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status, nslab, ss); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -608,23 +637,8 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
     }
     return cudaGetLastError();
   }
-  using C = TmaCfg<DIM, N, NT, TI>;
-  auto k = asm_apply_tma_kernel<DIM, N, NT, T, TI>;
-  static int per_sm = 0, sms = 0;  // one value per instantiation (same device for all contexts)
-  if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::THREADS, C::SMEM);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
-  const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
-  const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
-  { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), C::SMEM, s, r, u, reinterpret_cast<const TI*>(inv), g, mt, cs, cd, status, nslab, ss); if (e_ != cudaSuccess) return e_; }
-  return cudaGetLastError();
+  return nslab > 1 ? launch_tma<DIM, N, NT, T, TI, true>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s)
+                   : launch_tma<DIM, N, NT, T, TI, false>(r, u, inv, g, mt, cs, cd, status, 1, ss, s);
 }
 
 }  // namespace
@@ -638,17 +652,17 @@ int64_t asm_cell_stride(int dim, int n, int nt) { return cell_stride(dim == 3 ? 
 
 cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
                              const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
-                             int inv_prec, cudaStream_t s) {
+                             int inv_prec, int weighted, cudaStream_t s) {
   (void)nt;
   if (dim == 3) {
-    if (n == 2) return setup_t<3, 2>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
-    if (n == 3) return setup_t<3, 3>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
-    if (n == 4) return setup_t<3, 4>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 2) return setup_t<3, 2>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
+    if (n == 3) return setup_t<3, 3>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
+    if (n == 4) return setup_t<3, 4>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
   } else {
-    if (n == 2) return setup_t<2, 2>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
-    if (n == 3) return setup_t<2, 3>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
-    if (n == 4) return setup_t<2, 4>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
-    if (n == 5) return setup_t<2, 5>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, s);
+    if (n == 2) return setup_t<2, 2>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
+    if (n == 3) return setup_t<2, 3>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
+    if (n == 4) return setup_t<2, 4>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
+    if (n == 5) return setup_t<2, 5>(g, geo64, lt, lam_re, lam_im, nreal, ncplx, inv, inv_prec, weighted, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -73,7 +73,8 @@ struct ModeTab {
   T Vr[kMaxNT][kMaxNT], Vi[kMaxNT][kMaxNT];
   T lre[kMaxNT], lim[kMaxNT];   // eigenvalues of the representative modes
   T omega;
-  int weighted;  // 1: each cell's correction at a node divided by the number of cells containing the node
+  int weighted;  // fast diagonalisation: each cell's correction at a node divided by the node's cell count
+                 // (stored inverses carry the factor in their rows)
 };
 
 // 1 / (number of cells that contain an unconstrained node) on the structured grid: a factor 1/2 for

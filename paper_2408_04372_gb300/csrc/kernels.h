@@ -28,6 +28,9 @@ cudaError_t launch_mass_couple(int dim, int n, int nt, const TI* x, TO* y, const
 // an FP64 output: the FGMRES apply on V-cycle outputs, which are exact in FP32.
 cudaError_t launch_apply_df(int dim, int n, int nt, const float* x, double* y, const df64* geo, const GridDesc& g,
                             const OpTab<df64>& tab, int mask_input, cudaStream_t s);
+// Same for an FP64 input vector, split into two floats per entry (the FGMRES residual on level 0).
+cudaError_t launch_apply_df_d(int dim, int n, int nt, const double* x, double* y, const df64* geo, const GridDesc& g,
+                              const OpTab<df64>& tab, int mask_input, cudaStream_t s);
 // y = constrained ? x : 0 for an FP32 x and FP64 y (initialisation for launch_apply_df)
 cudaError_t launch_init_rows_f2d(double* y, const float* x, const GridDesc& g, int nt, cudaStream_t s);
 // mode 0: y = constrained ? x : 0 ; mode 1: y = constrained ? f - x : f ; mode 2: y = 0
@@ -46,10 +49,11 @@ struct LocalTab {        // 1D tables of the nodal basis at Gauss points (setup 
   double Dn[kMaxN][kMaxN];  // derivative of node basis i at Gauss point q
 };
 // Builds, per cell and time mode, the inverse of (A_K + lambda_m M_K) with A_K, M_K the
-// global matrices restricted to the cell's nodes; writes planes of the storage type.
+// global matrices restricted to the cell's nodes; writes planes of the storage type.  weighted:
+// row a scaled by 1 / (number of cells containing node a), the weighted Schwarz sum.
 cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
                              const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
-                             int inv_prec, cudaStream_t s);
+                             int inv_prec, int weighted, cudaStream_t s);
 // elements per cell in the inverse store (N_t planes, padded to a 16-byte multiple)
 int64_t asm_cell_stride(int dim, int n, int nt);
 // copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell.

@@ -279,12 +279,35 @@ stmg_status op_apply_df(stmg_ctx* ctx, Level& L, const float* x, double* y) {
   return STMG_OK;
 }
 
+// r = f - S u on the finest level for FGMRES.  df: the slab blocks in double-float arithmetic on u
+// split into float pairs (FP32 pipe, about 44 bits; used when the stopping target is at least
+// 1e-10 of ||b||, so that the residual's own error stays far below it), else FP64.
+stmg_status op_residual_outer(stmg_ctx* ctx, Level& L, const double* f, const double* u, double* r, bool df);
+
 // r = f - S u
 template <typename T>
 stmg_status op_residual(stmg_ctx* ctx, Level& L, const T* f, const T* u, T* r) {
   CK(launch_init_rows<T>(r, f, u, L.g, L.nt * L.nc, 1, ctx->stream));
   ctx->launches += 1;
   return apply_slabs<T>(ctx, L, u, r, T(-1));
+}
+
+stmg_status op_residual_outer(stmg_ctx* ctx, Level& L, const double* f, const double* u, double* r, bool df) {
+  if (!df || !L.geodf) return op_residual<double>(ctx, L, f, u, r);
+  CK(launch_init_rows<double>(r, f, u, L.g, L.nt * L.nc, 1, ctx->stream));
+  OpTab<df64> t = L.tabdf;
+  t.sign = df64(-1.0f);
+  OpTab<double> c = L.cpl64;
+  for (int i = 0; i < kMaxNT; ++i) c.TM[i][L.nt - 1] = -c.TM[i][L.nt - 1];
+  const int64_t ss = L.slab_size();
+  for (int i = 0; i < L.nc; ++i) {
+    CK(launch_apply_df_d(L.dim, L.n, L.nt, u + i * ss, r + i * ss, L.geodf, L.g, t, 1, ctx->stream));
+    if (i > 0)
+      CK(launch_mass_couple<double, double, double>(L.dim, L.n, L.nt, u + (i - 1) * ss, r + i * ss, L.geo64, L.g, c,
+                                                    ctx->stream));
+  }
+  ctx->launches += 2 * L.nc;
+  return STMG_OK;
 }
 
 // u += omega * ASM r ; optionally also copy_dst := copy_src (a fused side job for the V-cycle)
@@ -676,7 +699,7 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
   for (size_t r = 0; r < lr.size(); ++r) { lam_host[r] = lr[r]; lam_host[kMaxNT + r] = li[r]; }
   CK(cudaMemcpyAsync(dl, lam_host.data(), sizeof(double) * 2 * kMaxNT, cudaMemcpyHostToDevice, ctx->stream));
   CK(launch_asm_setup(L.dim, L.n, nt, L.g, L.geo64, L.lt, dl, dl + kMaxNT, L.nreal, L.ncplx, L.inv, L.inv_prec,
-                      ctx->stream));
+                      ctx->opt.asm_weighting, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return STMG_OK;
 }
@@ -1122,6 +1145,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
   if (!std::isfinite(bnorm)) { ctx->err = "right-hand side is not finite"; return STMG_ERR_NONFINITE; }
   // stopping rule: ||b - S x|| <= max(rtol ||b||, atol) (the absolute part only when atol > 0)
   const double target = std::max(ctx->opt.rtol * bnorm, ctx->opt.atol);
+  const bool df_residual = ctx->outer_df && target >= 1e-10 * bnorm;
   std::vector<double*> V(m + 1), Z(m);
   for (int j = 0; j <= m; ++j) V[j] = ctx->V + (size_t)j * ctx->vld;
   for (int j = 0; j < m; ++j) Z[j] = ctx->Z + (size_t)j * n;
@@ -1129,7 +1153,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
   bool first = true;
   stmg_status result = STMG_OK;
   while (true) {
-    CKS(op_residual<double>(ctx, L, b, x, V[0]));
+    CKS(op_residual_outer(ctx, L, b, x, V[0], df_residual));
     double beta = 0.0;
     CKS(norm2(ctx, V[0], n, beta));
     if (!std::isfinite(beta)) { ctx->err = "residual is not finite"; return STMG_ERR_NONFINITE; }

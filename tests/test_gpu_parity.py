@@ -207,6 +207,16 @@ def test_solve_matches_direct_solution(env, case):
         err = np.linalg.norm(u.cpu().numpy() - xd) / np.linalg.norm(xd)
         assert err < 1e-8, (case.name, prec, outer, err, st)
         ctx.close()
+    # rtol 1e-9: the stopping test runs on the double-float residual (default outer apply); it agrees
+    # with the oracle's FP64 residual of the returned solution
+    ctx = make_context(stmg, case, H, rtol=1e-9, max_it=300)
+    u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st = ctx.solve(torch.from_numpy(b).cuda(), u)
+    un = u.cpu().numpy()
+    rres = np.linalg.norm(b - prob.S @ un) / np.linalg.norm(b)
+    assert st["converged"] and rres <= 1e-9, (case.name, rres, st)
+    assert abs(rres - st["rel_residual"]) <= 0.01 * rres + 1e-13, (case.name, rres, st)
+    ctx.close()
 
 
 @pytest.mark.parametrize("case", CASES[:3], ids=lambda c: c.name)
