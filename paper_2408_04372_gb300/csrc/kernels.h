@@ -111,7 +111,9 @@ cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const Ti
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s);
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
-cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64_t n, cudaStream_t s);
+// x *= *inv_scale_src; copy32 (may be NULL) also receives (float) x
+cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64_t n, cudaStream_t s,
+                                   float* copy32 = nullptr);
 // One classical Gram-Schmidt pass over V_0..V_{nv-1} (nv <= 64), single launch, bit-reproducible:
 // optionally w -= sum_j c[j] V_j, then s_j = V_j . w and/or s_nv = w . w; fin 0 writes s to out,
 // fin 1 the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = ||w||, out[nv+1] = 1/||w||.
@@ -122,10 +124,14 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
                             double* out, cudaStream_t s, int* status = nullptr);
 int cgs_blocks();
-// w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride)
-cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,
+// w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride; V in FP64 or FP32)
+template <typename TV>
+cudaError_t launch_multi_axpy(double* w, const TV* V0, int64_t stride, const double* h, int nv, double sign,
                               int64_t n, cudaStream_t s);
 cudaError_t launch_broadcast_time(const double* u0, double* u, int nt, int64_t n_nodes, cudaStream_t s);
+// out[pt][c] = sum_a w[pt][a] u[c n_nodes + nodes[pt][a]] for npts points, ncomp components, nb nodes each
+cudaError_t launch_point_values(const double* u, int64_t n_nodes, int ncomp, const int64_t* nodes, const double* w,
+                                int nb, int npts, double* out, cudaStream_t s);
 // y[i][node] = sum_j C[i][j] x_j[node] over nin vectors (time-only mixing)
 cudaError_t launch_time_mix(const double* const* xs, int nin, const double* C, int nout, double* y,
                             int64_t n_nodes, int accumulate, cudaStream_t s);

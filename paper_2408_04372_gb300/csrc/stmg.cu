@@ -81,6 +81,7 @@ struct stmg_ctx {
   double* V = nullptr;   // (nvec) vectors, stride vld
   int64_t vld = 0;       // stride of the Krylov basis: n0 rounded up to 32 (256-byte aligned vectors)
   double* Z = nullptr;   // (m) vectors
+  float* Z32 = nullptr;  // (m) preconditioned vectors in FP32 (FP32 V-cycle with the double-float apply: exact)
   double* partial = nullptr;        // per-block partial sums of the Gram-Schmidt passes
   unsigned int* counter = nullptr;  // arrival counter of those passes (zero between launches)
   int* status = nullptr;            // device status word: nonzero after a bounded device wait gave up
@@ -262,11 +263,15 @@ stmg_status op_apply(stmg_ctx* ctx, Level& L, const T* x, T* y) {
 }
 
 // y = S x for an FP32 x, in double-float arithmetic, FP64 y (identity on constrained rows)
-// (slab blocks in double-float; the coupling between slabs in FP64 from the FP32 input)
-stmg_status op_apply_df(stmg_ctx* ctx, Level& L, const float* x, double* y) {
+// (slab blocks in double-float; the coupling between slabs in FP64 from the FP32 input).  init false:
+// y is already 0 and x vanishes on constrained rows (a V-cycle output), so no initialisation pass.
+stmg_status op_apply_df(stmg_ctx* ctx, Level& L, const float* x, double* y, bool init = true) {
   if (!L.geodf) { ctx->err = "no double-float geometry on this level"; return STMG_ERR_UNSUPPORTED; }
-  CK(launch_init_rows_f2d(y, x, L.g, L.nt * L.nc, ctx->stream));
-  ctx->launches += 2 * L.nc;
+  if (init) {
+    CK(launch_init_rows_f2d(y, x, L.g, L.nt * L.nc, ctx->stream));
+    ctx->launches += 1;
+  }
+  ctx->launches += 2 * L.nc - 1;
   OpTab<df64> t = L.tabdf;
   t.sign = df64(1.0f);
   const int64_t ss = L.slab_size();
@@ -500,8 +505,9 @@ stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
 
 // enqueue part: no host synchronisation (capturable).  Classical Gram-Schmidt twice in three
 // fused passes over the basis: h1 = V^T w ; w -= V h1, h2 = V^T w ; w -= V h2, ||w|| and the
-// column h1 + h2 ; then w /= ||w||.
-stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, int nv, double* w, int64_t n) {
+// column h1 + h2 ; then w /= ||w|| (and, with copy32, its FP32 copy: the next V-cycle's input).
+stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, int nv, double* w, int64_t n,
+                                  float* copy32 = nullptr) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
   double* d_out = ctx->dsm + 384;
@@ -510,7 +516,7 @@ stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, i
   CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st));
   CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 1, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream, st));
   ctx->launches += 4;
-  CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream));
+  CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream, copy32));
   CK(cudaMemcpyAsync(ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
   return STMG_OK;
 }
@@ -978,6 +984,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   ctx->vld = (n0 + 31) / 32 * 32;
   CKS(dev_alloc(ctx, &ctx->V, (size_t)ctx->nvec * ctx->vld));
   CKS(dev_alloc(ctx, &ctx->Z, (size_t)std::max(ctx->m, 1) * n0));
+  if (o.vcycle_precision == STMG_FP32 && ctx->outer_df) CKS(dev_alloc(ctx, &ctx->Z32, (size_t)std::max(ctx->m, 1) * n0));
   CKS(dev_alloc(ctx, &ctx->partial, (size_t)cgs_blocks() * 80));
   CKS(dev_alloc(ctx, &ctx->counter, 1));
   CK(cudaMemsetAsync(ctx->counter, 0, sizeof(unsigned int), ctx->stream));
@@ -1066,15 +1073,32 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
   double* v = ctx->V + (size_t)j * ctx->vld;
   double* z = ctx->Z + (size_t)j * n;
   double* w = ctx->V + (size_t)(j + 1) * ctx->vld;
+  if (ctx->opt.vcycle_precision == STMG_FP32 && ctx->outer_df) {
+    // z_j is exact in FP32: the V-cycle writes it straight into the FP32 basis Z32[j] (level 0's
+    // output pointer is redirected for this iteration's graph), the double-float apply reads it,
+    // and w starts from 0 (z_j vanishes on constrained rows).  The V-cycle input (float) v_j was
+    // written by the previous iteration's normalisation, except at j = 0.
+    float* z32 = ctx->Z32 + (size_t)j * n;
+    if (j == 0) {
+      CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
+      ctx->launches += 1;
+    }
+    float* saved = L.u32;
+    L.u32 = z32;
+    stmg_status st = in_capture ? vcycle_level<float>(ctx, 0) : run_vcycle<float>(ctx);
+    L.u32 = saved;
+    CKS(st);
+    CK(cudaMemsetAsync(w, 0, sizeof(double) * n, ctx->stream));
+    CKS(op_apply_df(ctx, L, z32, w, false));
+    return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n, j + 1 < ctx->m ? L.f32 : nullptr);
+  }
   if (ctx->opt.vcycle_precision == STMG_FP32) {
     CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
     if (in_capture) CKS(vcycle_level<float>(ctx, 0));
     else CKS(run_vcycle<float>(ctx));
     CK(launch_convert<float, double>(L.u32, z, n, ctx->stream));
     ctx->launches += 2;
-    // z_j is exact in FP32: the double-float apply reads the V-cycle output itself
-    if (ctx->outer_df) CKS(op_apply_df(ctx, L, L.u32, w));
-    else CKS(op_apply<double>(ctx, L, z, w));
+    CKS(op_apply<double>(ctx, L, z, w));
   } else {
     CK(cudaMemcpyAsync(L.f64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     if (in_capture) CKS(vcycle_level<double>(ctx, 0));
@@ -1203,7 +1227,10 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
       y[i] = t / H[(size_t)i * m + i];
     }
     CK(cudaMemcpyAsync(ctx->dsm + 320, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, ctx->stream));
-    CK(launch_multi_axpy(x, ctx->Z, n, ctx->dsm + 320, jend, 1.0, n, ctx->stream));
+    if (ctx->opt.vcycle_precision == STMG_FP32 && ctx->outer_df)
+      CK(launch_multi_axpy<float>(x, ctx->Z32, n, ctx->dsm + 320, jend, 1.0, n, ctx->stream));
+    else
+      CK(launch_multi_axpy<double>(x, ctx->Z, n, ctx->dsm + 320, jend, 1.0, n, ctx->stream));
     ctx->launches += 1;
     (void)breakdown;
   }
@@ -1434,6 +1461,128 @@ static void map_point(const Level& L, int64_t cell, const double* xi, double* ou
     const int64_t vid = (cx + bits[0]) + nv1 * ((cy + bits[1]) + nv1 * (cz + bits[2]));
     for (int d = 0; d < dim; ++d) out[d] += f * L.vertices[vid * dim + d];
   }
+}
+
+// Q1 map of a cell and its Jacobian J[d][e] = d x_d / d xi_e at reference point xi.
+static void map_point_jac(const Level& L, int64_t cell, const double* xi, double* x, double J[3][3]) {
+  const int dim = L.dim;
+  const int64_t nv1 = L.N + 1;
+  const int64_t cx = cell % L.N, cy = (cell / L.N) % L.N, cz = dim == 3 ? cell / ((int64_t)L.N * L.N) : 0;
+  for (int d = 0; d < 3; ++d) {
+    x[d] = 0.0;
+    for (int e = 0; e < 3; ++e) J[d][e] = 0.0;
+  }
+  const int nvert = dim == 3 ? 8 : 4;
+  for (int b = 0; b < nvert; ++b) {
+    const int bits[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+    double f[3], df[3];
+    for (int d = 0; d < dim; ++d) { f[d] = bits[d] ? xi[d] : 1.0 - xi[d]; df[d] = bits[d] ? 1.0 : -1.0; }
+    double val = 1.0;
+    for (int d = 0; d < dim; ++d) val *= f[d];
+    const int64_t vid = (cx + bits[0]) + nv1 * ((cy + bits[1]) + nv1 * (cz + bits[2]));
+    for (int e = 0; e < dim; ++e) {
+      double g = df[e];
+      for (int d = 0; d < dim; ++d) if (d != e) g *= f[d];
+      for (int d = 0; d < dim; ++d) J[d][e] += g * L.vertices[vid * dim + d];
+    }
+    for (int d = 0; d < dim; ++d) x[d] += val * L.vertices[vid * dim + d];
+  }
+}
+
+// Cell and reference coordinates of physical point p on level L (Newton on the Q1 map of the cells
+// whose vertex bounding box contains p); false if no cell contains it.
+static bool locate_point(const Level& L, const double* p, int64_t& cell, double* xi) {
+  const int dim = L.dim;
+  const int64_t nv1 = L.N + 1;
+  for (int64_t c = 0; c < L.g.n_cells; ++c) {
+    const int64_t cx = c % L.N, cy = (c / L.N) % L.N, cz = dim == 3 ? c / ((int64_t)L.N * L.N) : 0;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int b = 0; b < (dim == 3 ? 8 : 4); ++b) {
+      const int64_t vid = (cx + (b & 1)) + nv1 * ((cy + ((b >> 1) & 1)) + nv1 * (cz + ((b >> 2) & 1)));
+      for (int d = 0; d < dim; ++d) {
+        lo[d] = std::min(lo[d], L.vertices[vid * dim + d]);
+        hi[d] = std::max(hi[d], L.vertices[vid * dim + d]);
+      }
+    }
+    bool in = true;
+    for (int d = 0; d < dim; ++d) in = in && p[d] >= lo[d] - 1e-9 && p[d] <= hi[d] + 1e-9;
+    if (!in) continue;
+    double r[3] = {0.5, 0.5, 0.5}, x[3], J[3][3];
+    for (int it = 0; it < 50; ++it) {
+      map_point_jac(L, c, r, x, J);
+      // solve J s = x - p (dim <= 3, Cramer)
+      double b[3] = {x[0] - p[0], x[1] - p[1], dim == 3 ? x[2] - p[2] : 0.0}, st[3] = {0.0, 0.0, 0.0};
+      if (dim == 2) {
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        st[0] = (b[0] * J[1][1] - J[0][1] * b[1]) / det;
+        st[1] = (J[0][0] * b[1] - b[0] * J[1][0]) / det;
+      } else {
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        for (int k = 0; k < 3; ++k) {
+          double M[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = j == k ? b[i] : J[i][j];
+          st[k] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                   M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+        }
+      }
+      double mx = 0.0;
+      for (int d = 0; d < dim; ++d) { r[d] -= st[d]; mx = std::max(mx, std::fabs(st[d])); }
+      if (mx < 1e-15) break;
+    }
+    bool inside = true;
+    for (int d = 0; d < dim; ++d) inside = inside && r[d] >= -1e-12 && r[d] <= 1.0 + 1e-12;
+    if (inside) {
+      cell = c;
+      for (int d = 0; d < dim; ++d) xi[d] = std::min(1.0, std::max(0.0, r[d]));
+      return true;
+    }
+  }
+  return false;
+}
+
+stmg_status stmg_point_values(stmg_ctx* ctx, const double* u, int npts, const double* xyz, double* out) {
+  if (!ctx || !u || !xyz || !out || npts < 0) return STMG_ERR_INVALID_ARG;
+  if (npts == 0) return STMG_OK;
+  StreamJoin join_(ctx);
+  const Level& L = ctx->levels[0];
+  const int n = L.n, dim = L.dim, nb = dim == 3 ? n * n * n : n * n;
+  const int ncomp = L.nc * L.nt;
+  std::vector<double> xn = space_nodes(L.p);
+  std::vector<int64_t> nodes((size_t)npts * nb);
+  std::vector<double> w((size_t)npts * nb);
+  for (int pt = 0; pt < npts; ++pt) {
+    int64_t c = 0;
+    double xi[3] = {0.0, 0.0, 0.0};
+    if (!locate_point(L, xyz + (size_t)pt * dim, c, xi))
+      return invalid(ctx, "point " + std::to_string(pt) + " lies outside the grid");
+    const int64_t cx = c % L.N, cy = (c / L.N) % L.N, cz = dim == 3 ? c / ((int64_t)L.N * L.N) : 0;
+    for (int a = 0; a < nb; ++a) {
+      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+      double phi = 1.0;
+      for (int d = 0; d < dim; ++d) phi *= lagrange(xn, ai[d], xi[d]);
+      const int64_t gx = cx * L.p + ai[0], gy = cy * L.p + ai[1], gz = dim == 3 ? cz * L.p + ai[2] : 0;
+      nodes[(size_t)pt * nb + a] = gx + (int64_t)L.g.nn1 * (gy + (int64_t)L.g.nn1 * gz);
+      w[(size_t)pt * nb + a] = phi;
+    }
+  }
+  void* buf = nullptr;
+  const size_t bytes = (size_t)npts * nb * (sizeof(int64_t) + sizeof(double)) + (size_t)npts * ncomp * sizeof(double);
+  CK(cudaMalloc(&buf, bytes));
+  int64_t* d_nodes = reinterpret_cast<int64_t*>(buf);
+  double* d_w = reinterpret_cast<double*>(d_nodes + (size_t)npts * nb);
+  double* d_out = d_w + (size_t)npts * nb;
+  cudaError_t e = cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(int64_t) * nodes.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_point_values(u, L.g.n_nodes, ncomp, d_nodes, d_w, nb, npts, d_out, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double) * npts * ncomp, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  ctx->launches += 1;
+  cudaFree(buf);
+  CK(e);
+  return STMG_OK;
 }
 
 stmg_status stmg_node_coords(const stmg_ctx* ctx, int level, double* xyz) {

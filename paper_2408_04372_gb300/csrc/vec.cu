@@ -34,12 +34,17 @@ __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, d
     y[i] = a * x[i] + b * y[i];
 }
 
-__global__ void scale_by_device_kernel(double* __restrict__ x, const double* __restrict__ sc, int64_t n) {
+// x *= sc[0]; with y32, also y32 = (float) x (the next V-cycle's input, written in the same pass)
+__global__ void scale_by_device_kernel(double* __restrict__ x, const double* __restrict__ sc, int64_t n,
+                                       float* __restrict__ y32) {
   pdl_wait();
   pdl_trigger();
   const double s = sc[0];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] *= s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i] * s;
+    x[i] = v;
+    if (y32) y32[i] = (float)v;
+  }
 }
 
 // One pass of classical Gram-Schmidt against V_0..V_{nv-1} (V_j = V0 + j * stride):
@@ -325,7 +330,8 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   if (tid == 0) *counter = 0u;
 }
 
-__global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V0, int64_t stride,
+template <typename TV>
+__global__ void multi_axpy_kernel(double* __restrict__ w, const TV* __restrict__ V0, int64_t stride,
                                   const double* __restrict__ h, int nv, double sign, int64_t n) {
   pdl_wait();
   pdl_trigger();
@@ -334,8 +340,22 @@ __global__ void multi_axpy_kernel(double* __restrict__ w, const double* __restri
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int j = 0; j < nv; ++j) s += sh[j] * __ldg(V0 + j * stride + i);
+    for (int j = 0; j < nv; ++j) s += sh[j] * (double)__ldg(V0 + j * stride + i);
     w[i] += sign * s;
+  }
+}
+
+// out[pt][c] = sum_a w[pt][a] u[c][nodes[pt][a]]: one block per point, threads over components
+__global__ void point_values_kernel(const double* __restrict__ u, int64_t nn, int ncomp,
+                                    const int64_t* __restrict__ nodes, const double* __restrict__ w, int nb,
+                                    double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  const int pt = blockIdx.x;
+  for (int c = threadIdx.x; c < ncomp; c += blockDim.x) {
+    double s = 0.0;
+    for (int a = 0; a < nb; ++a) s += w[(int64_t)pt * nb + a] * u[(int64_t)c * nn + nodes[(int64_t)pt * nb + a]];
+    out[(int64_t)pt * ncomp + c] = s;
   }
 }
 
@@ -418,8 +438,8 @@ cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaStream_t s) {
-  { const cudaError_t e_ = launch_k(scale_by_device_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, x, sc, n); if (e_ != cudaSuccess) return e_; }
+cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaStream_t s, float* copy32) {
+  { const cudaError_t e_ = launch_k(scale_by_device_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, x, sc, n, copy32); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -470,10 +490,21 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_axpy(double* w, const double* V0, int64_t stride, const double* h, int nv, double sign,
+template <typename TV>
+cudaError_t launch_multi_axpy(double* w, const TV* V0, int64_t stride, const double* h, int nv, double sign,
                               int64_t n, cudaStream_t s) {
   if (nv > kMaxVec) return cudaErrorInvalidValue;
-  { const cudaError_t e_ = launch_k(multi_axpy_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, w, V0, stride, h, nv, sign, n); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_k(multi_axpy_kernel<TV>, dim3(grid_blocks(n)), dim3(256), 0, s, w, V0, stride, h, nv, sign, n); if (e_ != cudaSuccess) return e_; }
+  return cudaGetLastError();
+}
+template cudaError_t launch_multi_axpy<double>(double*, const double*, int64_t, const double*, int, double, int64_t,
+                                               cudaStream_t);
+template cudaError_t launch_multi_axpy<float>(double*, const float*, int64_t, const double*, int, double, int64_t,
+                                              cudaStream_t);
+
+cudaError_t launch_point_values(const double* u, int64_t nn, int ncomp, const int64_t* nodes, const double* w, int nb,
+                                int npts, double* out, cudaStream_t s) {
+  { const cudaError_t e_ = launch_k(point_values_kernel, dim3((unsigned)npts), dim3(64), 0, s, u, nn, ncomp, nodes, w, nb, out); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
