@@ -635,6 +635,73 @@ def run_c4(args):
     return 0
 
 
+def run_shm(args):
+    """Structural-health-monitoring-like wave problem (Section 4.3), reduced: [-1, 1]^3 on N^3 Cartesian
+    cells (N a multiple of 5), Q2, cGP(2), highly heterogeneous coefficient (layers 1 / 9 / 16 times
+    c ~ U[0.4, 1.6] per cell of the 5^3 coarse grid), bump initial displacement (radius s = 4h instead
+    of 0.01: resolvable on the reduced grid), v = 0, f = 0, tau = 2 / (5 * 2^(r+1)) with N = 5 * 2^r.
+    Slab by slab for nu = 1, 2, 4 smoothing steps (the paper's table iter-wave-hc), point values at
+    the three goal points every slab."""
+    import torch
+    import paper_2408_04372_gb300 as stmg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N = args.n_cells if args.n_cells != 32 else 40
+    r = int(round(np.log2(N / 5)))
+    p, k = 2, 2
+    tau = 2.0 / (5 * 2 ** (r + 1))
+    V = synth.cartesian_vertices(N, 3, lo=-1.0, hi=1.0)
+    rho = synth.shm_coefficient(N, rough=True)
+    steps = max(args.steps, 3)
+    out = {}
+    for nu in (1, 2, 4):
+        ctx = stmg.Context(3, N, p, k, tau, pde=stmg.WAVE, scheme=stmg.CGP, vertices=V, coeff=rho,
+                           nu_pre=nu, nu_post=nu, vcycle_precision=stmg.FP32, inverse_precision=stmg.BF16, rtol=1e-8,
+                           restart=30, max_it=200, coarse_max_dofs=args.coarse_max_dofs,
+                           asm_weighting=args.asm_weighting)
+        nt, nn = ctx.nt, ctx.n_nodes
+        X = ctx.node_coords()
+        u0 = synth.shm_initial(X, s=4.0 * 2.0 / N)
+        u0[np.any(np.abs(np.abs(X) - 1.0) < 1e-12, axis=1)] = 0.0
+        rhs = torch.empty(nt * nn, dtype=torch.float64, device=dev)
+        u = torch.empty_like(rhs)
+        v = torch.empty_like(rhs)
+        zf = torch.zeros(nt * nn, dtype=torch.float64, device=dev)
+        zn = torch.zeros(nn, dtype=torch.float64, device=dev)
+        u_prev = torch.from_numpy(u0).to(dev)
+        v_prev = torch.zeros(nn, dtype=torch.float64, device=dev)
+        its, goal, ms = [], [], 0.0
+        for s_ in range(args.warmup + steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.rhs(zf, rhs, f0=zn, u0=u_prev, v0=v_prev)
+            ctx.guess_previous(u_prev, u)
+            st = ctx.solve(rhs, u)
+            ctx.wave_velocity(u, u_prev, v_prev, v)
+            e1.record()
+            torch.cuda.synchronize()
+            assert st["converged"], st
+            if s_ >= args.warmup:
+                ms += e0.elapsed_time(e1)
+                its.append(st["iterations"])
+            goal.append(ctx.point_values(u, synth.SHM_POINTS)[:, -1].tolist())
+            u_prev.copy_(u[(nt - 1) * nn:])
+            v_prev.copy_(v[(nt - 1) * nn:])
+        dofs = nt * (N * p - 1) ** 3
+        out[f"nu_{nu}"] = {"value": dofs * steps / (ms / 1e3), "unit": UNIT, "ms_per_slab": ms / steps,
+                           "fgmres_iterations_mean": float(np.mean(its)), "slabs_timed": steps,
+                           "goal_point_values_at_slab_ends": goal}
+        ctx.close()
+    line = {"metric": "space-time DoFs/s solved to 1e-8 rel. residual", "value": out["nu_1"]["value"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64+df32+f32", "data": "synthetic",
+            "config": {"workload": f"wave3d_q2_cgp2_{N}cubed_shm_rough", "dofs_per_slab": 2 * (N * p - 1) ** 3,
+                       "tau": tau, "goal_points": list(synth.SHM_POINTS)},
+            "arms": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def aggregate_replicas(ms_local, dofs_per_step, steps, world, device):
     """Replicas only: slowest rank's time, every rank's DoFs.  Returns (max ms, whole-job DoF/s)."""
     import torch
@@ -699,7 +766,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-compare", action="store_true", help="skip the no-network and plain-FP64 comparison arms")
     ap.add_argument("--net", action="store_true", help="learned guess on this workload too (trained on slabs 0-15)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "shm"])
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64"],
                     help="storage of the Schwarz inverses in the mixed solver")
@@ -725,6 +792,8 @@ def main():
         return run_learned_c5(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "shm":
+        return run_shm(args)
     return run_ours(args)
 
 

@@ -155,6 +155,12 @@ stmg_status stmg_level_info(const stmg_ctx* ctx, int level, int* p, int* n_cells
                             int64_t* n_nodes, int* n_t, double* omega);
 /* Physical node coordinates of a level (HOST output, n_nodes x dim).  Synchronous. */
 stmg_status stmg_node_coords(const stmg_ctx* ctx, int level, double* xyz);
+/* Point values (goal quantities of the structural-health-monitoring example, Section 4.3): the
+ * finest-level finite-element function u (DEVICE, [n_slabs][N_t][n_nodes]) evaluated at npts physical
+ * points (HOST xyz, npts x dim) for every slab and time DoF -> out (HOST, npts x n_slabs N_t).  Each
+ * point is located by Newton on the Q1 map of the cells; STMG_ERR_INVALID_ARG if a point lies outside
+ * the grid.  Synchronous. */
+stmg_status stmg_point_values(stmg_ctx* ctx, const double* u, int npts, const double* xyz, double* out);
 /* Physical Gauss-point coordinates of a level (HOST output, cells x (p+1)^dim x dim). */
 stmg_status stmg_qpoint_coords(const stmg_ctx* ctx, int level, double* xyz);
 

@@ -15,6 +15,7 @@ Every function is a direct, slow, readable restatement of the paper:
                V-cycle (Algorithm stmg), relaxation (eq. relaxation), FGMRES
   atonce    -- several heat dG(k) slabs in one system (eq. heat-cg-dg-at-once) and tau-multigrid
                (Algorithm mg-sequence, mgType tau)
+  points    -- point values of a finite-element function (goal quantities, Section 4.3)
   conv      -- direct 3D convolution network used for the learned initial guess
 
 Parity status per function is stated in each module header.

@@ -30,7 +30,7 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_wave_velocity", "stmg_guess_previous", "stmg_solve_slab_host", "stmg_launch_count",
            "stmg_time_kernel", "stmg_smooth_noalloc", "stmg_net_create", "stmg_net_destroy", "stmg_net_predict",
            "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights", "stmg_select_guess",
-           "stmg_solve_slab_host_learned", "stmg_selftest_device_timeout", "stmg_level_slabs"]
+           "stmg_solve_slab_host_learned", "stmg_selftest_device_timeout", "stmg_level_slabs", "stmg_point_values"]
 KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
 
 
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "stmg_level_info": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                             ctypes.POINTER(i64), ctypes.POINTER(i32), dp],
         "stmg_level_slabs": [vp, i32, ctypes.POINTER(i32), dp],
+        "stmg_point_values": [vp, vp, i32, vp, vp],
         "stmg_node_coords": [vp, i32, vp],
         "stmg_qpoint_coords": [vp, i32, vp],
         "stmg_apply": [vp, i32, i32, vp, vp],
@@ -192,6 +193,20 @@ class Context:
         self._check(self.lib.stmg_level_slabs(self.h, level, ctypes.byref(nc), ctypes.byref(tau)))
         return dict(p=p.value, n_cells=N.value, k=k.value, n_nodes=nn.value, nt=nt.value, omega=om.value,
                     n_slabs=nc.value, tau=tau.value)
+
+    def point_values(self, u, points):
+        """u (float64 CUDA tensor, n_slabs * N_t * n_nodes) at physical points (npts x dim) ->
+        numpy (npts, n_slabs * N_t): every slab's time DoFs (goal quantities)."""
+        import numpy as np
+        import torch
+        self._vec(u)
+        if u.dtype != torch.float64:
+            raise TypeError("point_values takes a float64 vector")
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, self.dim)
+        out = np.zeros((len(pts), self.n_slabs * self.nt))
+        self._check(self.lib.stmg_point_values(self.h, _ptr(u), len(pts), pts.ctypes.data_as(ctypes.c_void_p),
+                                               out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def node_coords(self, level=0):
         import numpy as np

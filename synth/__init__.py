@@ -133,6 +133,35 @@ def wave_pulse(x: np.ndarray, x0=(0.5, 0.5, 0.25), sigma=0.05) -> np.ndarray:
     return np.exp(-r2 / (2.0 * sigma ** 2))
 
 
+# ---- structural-health-monitoring-like wave problem (Section 4.3 of the paper, reduced) ----
+
+SHM_POINTS = ((0.75, 0.0, 0.0), (0.0, 0.0, 0.75), (0.75, 0.1, 0.75))  # goal-quantity points
+
+
+def shm_coefficient(N, rough=False, seed=SEED_COEFF, coarse=5) -> np.ndarray:
+    """Per-cell coefficient on [-1, 1]^3 with N cells per direction (N a multiple of `coarse`):
+    1 for y < 0.2, 9 for y >= 0.2 and z < 0.2, 16 for y >= 0.2 and z >= 0.2 (at the cell centre);
+    rough: times c ~ U[0.4, 1.6] drawn per cell of the coarse^3 grid (seeded)."""
+    assert N % coarse == 0
+    c = cell_index_grid(N, 3)
+    ctr = -1.0 + (c + 0.5) * (2.0 / N)
+    y, z = ctr[:, 1], ctr[:, 2]
+    rho = np.where(y < 0.2, 1.0, np.where(z < 0.2, 9.0, 16.0))
+    if rough:
+        fac = np.random.default_rng(seed).uniform(0.4, 1.6, size=coarse ** 3)
+        cc = c // (N // coarse)
+        rho = rho * fac[cc[:, 0] + coarse * (cc[:, 1] + coarse * cc[:, 2])]
+    return rho.astype(np.float64)
+
+
+def shm_initial(x: np.ndarray, s=0.01) -> np.ndarray:
+    """u0 = exp(-|x/s|^2) (1 - |x/s|^2) for |x| < s, else 0."""
+    r2 = np.zeros(x.shape[:-1])
+    for d in range(x.shape[-1]):
+        r2 = r2 + (x[..., d] / s) ** 2
+    return np.where(r2 < 1.0, np.exp(-r2) * (1.0 - r2), 0.0)
+
+
 class MovingGaussians:
     """Source f(x, t) = sum_g A_g exp(-|x - c_g(t)|^2 / (2 w^2)), c_g(t) = 0.5 + 0.3 sin(2 pi om t + phi)."""
 

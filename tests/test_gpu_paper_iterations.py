@@ -114,3 +114,18 @@ def test_weighted_smoother_iterations_at_most_the_papers(env, pde, scheme, k):
         assert v <= 1.25 * table[k][r], (pde, scheme, k, r, v, table[k][r])
     assert its[3] <= its[2] + 1.0, its
     assert res[3][1] < 1e-3 and res[2][1] / res[3][1] >= 0.8 * 2 ** (k + 1), res
+
+
+@pytest.mark.parametrize("pde", ["heat", "wave"])
+def test_weighted_smoother_counts_stay_flat_up_to_degree_four(env, pde):
+    """Robustness in the polynomial degree (the paper's open point, Section 4.2 and the conclusion):
+    cGP(k), p = k, k = 2, 3, 4 (Q4: fast diagonalisation on the Cartesian grid) with the weighted
+    Schwarz sum and p-multigrid levels; the counts stay within 2 of each other and at or below the
+    printed ones."""
+    torch, stmg = env
+    table = _table(pde, "cgp")
+    its = {k: _mean_iterations(torch, stmg, pde, "cgp", k, 2, weighting=1)[0] for k in (2, 3, 4)}
+    print(f"\n{pde} cgp weighted, r = 2: mean iterations by k {its}, printed {[table[k][2] for k in (2, 3, 4)]}")
+    assert max(its.values()) - min(its.values()) <= 2.0, its
+    for k, v in its.items():
+        assert v <= 1.25 * table[k][2], (k, v, table[k][2])
