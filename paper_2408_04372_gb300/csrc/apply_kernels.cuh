@@ -59,6 +59,14 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   T* s0 = smem + (size_t)slot * 3 * NT * N3;
   T* s1 = s0 + NT * N3;
   T* s2 = s1 + NT * N3;
+  // the 1D tables, for the reads indexed by this thread's node (i, j): from shared memory every
+  // thread reads its own entry in one pass (the parameter bank would serialise differing addresses);
+  // the first read follows the barrier after the z sweep
+  __shared__ T sB[N][N], sD[N][N];
+  if (threadIdx.x < N2) {
+    sB[threadIdx.x / N][threadIdx.x % N] = tab.B[threadIdx.x / N][threadIdx.x % N];
+    sD[threadIdx.x / N][threadIdx.x % N] = tab.D[threadIdx.x / N][threadIdx.x % N];
+  }
   auto I4 = [](int t, int c, int b, int a) { return ((t * N + c) * N + b) * N + a; };
 
   const int64_t cc = active ? cell : 0;
@@ -108,7 +116,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int qz = 0; qz < N; ++qz) {
       Acc v = 0;
 #pragma unroll
-      for (int b = 0; b < N; ++b) v += tab.B[j][b] * s0[I4(t, qz, b, i)];
+      for (int b = 0; b < N; ++b) v += sB[j][b] * s0[I4(t, qz, b, i)];
       s1[I4(t, qz, j, i)] = v;
     }
   __syncthreads();
@@ -120,7 +128,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int qz = 0; qz < N; ++qz) {
       Acc v = 0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[i][a] * s1[I4(t, qz, j, a)];
+      for (int a = 0; a < N; ++a) v += sB[i][a] * s1[I4(t, qz, j, a)];
       const T vt = v;
       u[t][qz] = vt;
       if constexpr (!MASS) s0[I4(t, qz, j, i)] = vt;
@@ -156,8 +164,8 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       Acc a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        a0 += tab.D[i][a] * s0[I4(t, qz, j, a)];
-        a1 += tab.D[j][a] * s0[I4(t, qz, a, i)];
+        a0 += sD[i][a] * s0[I4(t, qz, j, a)];
+        a1 += sD[j][a] * s0[I4(t, qz, a, i)];
         a2 += tab.D[qz][a] * u[t][a];
       }
       ux[t] = a0; uy[t] = a1; uz[t] = a2;
@@ -194,8 +202,8 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       Acc v = val[it][qz];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        v += tab.D[a][i] * s1[I4(it, qz, j, a)];
-        v += tab.D[a][j] * s2[I4(it, qz, a, i)];
+        v += sD[a][i] * s1[I4(it, qz, j, a)];
+        v += sD[a][j] * s2[I4(it, qz, a, i)];
         v += tab.D[a][qz] * fz[it][a];
       }
       u[it][qz] = v;
@@ -214,7 +222,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int qz = 0; qz < N; ++qz) {
       Acc v = 0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[a][i] * s0[I4(it, qz, j, a)];
+      for (int a = 0; a < N; ++a) v += sB[a][i] * s0[I4(it, qz, j, a)];
       s1[I4(it, qz, j, i)] = v;
     }
   __syncthreads();
@@ -226,7 +234,7 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int qz = 0; qz < N; ++qz) {
       Acc v = 0;
 #pragma unroll
-      for (int b = 0; b < N; ++b) v += tab.B[b][j] * s1[I4(it, qz, b, i)];
+      for (int b = 0; b < N; ++b) v += sB[b][j] * s1[I4(it, qz, b, i)];
       r[qz] = v;
     }
 #pragma unroll
@@ -259,6 +267,11 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   const bool active = cell < g.n_cells;
   T* s0 = smem + (size_t)slot * 2 * NT * N2;
   T* s1 = s0 + NT * N2;
+  __shared__ T sB[N][N], sD[N][N];  // as in the 3D kernel
+  if (threadIdx.x < N2) {
+    sB[threadIdx.x / N][threadIdx.x % N] = tab.B[threadIdx.x / N][threadIdx.x % N];
+    sD[threadIdx.x / N][threadIdx.x % N] = tab.D[threadIdx.x / N][threadIdx.x % N];
+  }
   auto I3 = [](int t, int b, int a) { return (t * N + b) * N + a; };
   const int64_t cc = active ? cell : 0;
   const int cx = (int)(cc % g.N), cy = (int)(cc / g.N);
@@ -294,7 +307,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int qy = 0; qy < N; ++qy) {
       Acc v = 0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[i][a] * s0[I3(t, qy, a)];
+      for (int a = 0; a < N; ++a) v += sB[i][a] * s0[I3(t, qy, a)];
       const T vt = v;
       u[t][qy] = vt;
       if constexpr (!MASS) s1[I3(t, qy, i)] = vt;
@@ -328,7 +341,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       Acc a0 = 0, a1 = 0;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        a0 += tab.D[i][a] * s1[I3(t, qy, a)];
+        a0 += sD[i][a] * s1[I3(t, qy, a)];
         a1 += tab.D[qy][a] * u[t][a];
       }
       ux[t] = a0; uy[t] = a1;
@@ -355,7 +368,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       Acc v = val[it][qy];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        v += tab.D[a][i] * s0[I3(it, qy, a)];
+        v += sD[a][i] * s0[I3(it, qy, a)];
         v += tab.D[a][qy] * fy[it][a];
       }
       u[it][qy] = v;
@@ -373,7 +386,7 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     for (int qy = 0; qy < N; ++qy) {
       Acc v = 0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) v += tab.B[a][i] * s1[I3(it, qy, a)];
+      for (int a = 0; a < N; ++a) v += sB[a][i] * s1[I3(it, qy, a)];
       r[qy] = v;
     }
 #pragma unroll
