@@ -127,6 +127,10 @@ typedef struct {
                               correction at a node divided by the number of cells that contain the
                               node (a partition of unity; with it the omega estimate reaches the cap 1
                               on the coarse levels) [0] */
+  int outer_relax;         /* 1: relaxed FGMRES (inexact Krylov, Simoncini & Szyld 2003; FP32 V-cycle with
+                              the DF32 outer apply only): an iteration whose residual estimate is at most
+                              1e5 x the stopping target applies S in FP32 arithmetic (relative error about
+                              1e-5); the stopping test stays on the accurate residual [0] */
 } stmg_options;
 
 enum { STMG_COARSEN_P_THEN_H = 0, STMG_COARSEN_H = 1 };
@@ -136,6 +140,7 @@ typedef struct {
   int restarts;
   double rel_residual;     /* ||rhs - S u||_2 / ||rhs||_2 computed in FP64 at exit */
   double initial_rel_residual;
+  int relaxed_iterations;  /* iterations that used the FP32 operator apply (outer_relax) */
 } stmg_solve_stats;
 
 /* Builds all levels, geometry, smoother inverses, transfers and the coarse

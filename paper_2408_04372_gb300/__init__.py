@@ -56,12 +56,12 @@ class Options(ctypes.Structure):
                 ("omega", ctypes.POINTER(ctypes.c_double)), ("fgmres_restart", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("outer_apply", ctypes.c_int),
                 ("atol", ctypes.c_double), ("space_coarsening", ctypes.c_int), ("coarse_max_dofs", ctypes.c_int),
-                ("asm_weighting", ctypes.c_int)]
+                ("asm_weighting", ctypes.c_int), ("outer_relax", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("initial_rel_residual", ctypes.c_double)]
+                ("initial_rel_residual", ctypes.c_double), ("relaxed_iterations", ctypes.c_int)]
 
 
 _lib = None
@@ -137,7 +137,8 @@ class Context:
     def __init__(self, dim, n_cells, p, k, tau, pde=HEAT, scheme=DG, vertices=None, coeff=None,
                  coeff_mode=COEFF_PER_CELL, nu_pre=1, nu_post=1, vcycle_precision=FP32, inverse_precision=0,
                  omega=None, restart=30, rtol=1e-8, max_it=200, stream=None, smoother_kind=SMOOTHER_AUTO,
-                 outer_apply=0, atol=0.0, space_coarsening=0, coarse_max_dofs=0, n_slabs=1, asm_weighting=0):
+                 outer_apply=0, atol=0.0, space_coarsening=0, coarse_max_dofs=0, n_slabs=1, asm_weighting=0,
+                 outer_relax=0):
         import numpy as np
         import torch
         self.lib = load()
@@ -150,7 +151,7 @@ class Context:
         mesh = Mesh(dim, n_cells, _dptr(v))
         prob = Problem(pde, scheme, p, k, float(tau), coeff_mode, _dptr(c), int(n_slabs))
         opts = Options(nu_pre, nu_post, vcycle_precision, inverse_precision, smoother_kind, _dptr(om), restart, rtol,
-                       max_it, outer_apply, float(atol), space_coarsening, coarse_max_dofs, asm_weighting)
+                       max_it, outer_apply, float(atol), space_coarsening, coarse_max_dofs, asm_weighting, outer_relax)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -286,7 +287,8 @@ class Context:
         if code not in (0, 4):
             self._check(code)
         return dict(iterations=st.iterations, restarts=st.restarts, rel_residual=st.rel_residual,
-                    initial_rel_residual=st.initial_rel_residual, converged=code == 0)
+                    initial_rel_residual=st.initial_rel_residual, relaxed_iterations=st.relaxed_iterations,
+                    converged=code == 0)
 
     def wave_velocity(self, u, u0, v0, v):
         self._check(self.lib.stmg_wave_velocity(self.h, _ptr(u), _ptr(u0), _ptr(v0), _ptr(v)))

@@ -71,6 +71,22 @@ cudaError_t launch_mass_apply(int dim, int n, int nt, const double* x, double* y
   return cudaErrorInvalidValue;
 }
 
+#define STMG_F2D_CASE(DIM, N, NT)                                              \
+  if (dim == DIM && n == N && nt == NT) return launch_apply_t<DIM, N, NT, float, float, double>(x, y, geo, g, tab, mask_input, s);
+
+cudaError_t launch_apply_f2d(int dim, int n, int nt, const float* x, double* y, const float* geo, const GridDesc& g,
+                             const OpTab<float>& tab, int mask_input, cudaStream_t s) {
+  STMG_F2D_CASE(3, 2, 1) STMG_F2D_CASE(3, 2, 2) STMG_F2D_CASE(3, 2, 3) STMG_F2D_CASE(3, 2, 4)
+  STMG_F2D_CASE(3, 3, 1) STMG_F2D_CASE(3, 3, 2) STMG_F2D_CASE(3, 3, 3) STMG_F2D_CASE(3, 3, 4)
+  STMG_F2D_CASE(3, 4, 1) STMG_F2D_CASE(3, 4, 2) STMG_F2D_CASE(3, 4, 3) STMG_F2D_CASE(3, 4, 4)
+  STMG_F2D_CASE(3, 5, 1) STMG_F2D_CASE(3, 5, 2) STMG_F2D_CASE(3, 5, 3) STMG_F2D_CASE(3, 5, 4)
+  STMG_F2D_CASE(2, 2, 1) STMG_F2D_CASE(2, 2, 2) STMG_F2D_CASE(2, 2, 3) STMG_F2D_CASE(2, 2, 4)
+  STMG_F2D_CASE(2, 3, 1) STMG_F2D_CASE(2, 3, 2) STMG_F2D_CASE(2, 3, 3) STMG_F2D_CASE(2, 3, 4)
+  STMG_F2D_CASE(2, 4, 1) STMG_F2D_CASE(2, 4, 2) STMG_F2D_CASE(2, 4, 3) STMG_F2D_CASE(2, 4, 4)
+  STMG_F2D_CASE(2, 5, 1) STMG_F2D_CASE(2, 5, 2) STMG_F2D_CASE(2, 5, 3) STMG_F2D_CASE(2, 5, 4)
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, int nt, int mode, cudaStream_t s) {
   const int64_t total = g.n_nodes * nt;

@@ -27,6 +27,7 @@ template <int N> constexpr int cells_per_block(int dim) {
 // Output accumulation: the result of every cell is added to its nodes' rows.
 __device__ __forceinline__ void add_out(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void add_out(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void add_out(double* p, float v) { atomicAdd(p, (double)v); }
 __device__ __forceinline__ void add_out(double* p, df64 v) { atomicAdd(p, df_to_double(v)); }
 
 // Gathered input in the arithmetic's terms: an FP64 input entering double-float arithmetic is split

@@ -94,6 +94,8 @@ struct stmg_ctx {
   int64_t graph32_kernels = 0, graph64_kernels = 0;
   std::vector<cudaGraphExec_t> iter_graphs;      // one FGMRES iteration per Krylov index j
   std::vector<int64_t> iter_graph_kernels;
+  std::vector<cudaGraphExec_t> iter_graphs_low;  // the same with the relaxed (FP32) operator apply
+  std::vector<int64_t> iter_graph_kernels_low;
   bool warmed32 = false, warmed64 = false;
   int64_t launches = 0;  // kernels issued by this context (graph replays count their kernel nodes)
   std::vector<stmg_net*> nets;  // networks bound to this context; detached when it is destroyed
@@ -843,6 +845,7 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     return invalid(ctx, "space_coarsening out of range");
   if (o.coarse_max_dofs < 0 || o.coarse_max_dofs > 4096) return invalid(ctx, "coarse_max_dofs must be in 0..4096");
   if (o.asm_weighting != 0 && o.asm_weighting != 1) return invalid(ctx, "asm_weighting must be 0 or 1");
+  if (o.outer_relax != 0 && o.outer_relax != 1) return invalid(ctx, "outer_relax must be 0 or 1");
   if (o.max_it <= 0) o.max_it = 200;
   if (o.inverse_precision == 0) o.inverse_precision = o.vcycle_precision;
   if (o.outer_apply == 0) o.outer_apply = o.vcycle_precision == STMG_FP32 ? STMG_DF32 : STMG_FP64;
@@ -1066,8 +1069,29 @@ stmg_status precondition(stmg_ctx* ctx, const double* v, double* z) {
   return STMG_OK;
 }
 
-// z_j = B v_j, v_{j+1} = S z_j, CGS2 against v_0..v_j, Hessenberg column to the host buffer
-stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
+// Relative error assumed for the FP32 operator apply in the relaxed FGMRES (inexact Krylov,
+// Simoncini & Szyld 2003): iteration j may use it once the residual estimate |g_j| is at most
+// target / kRelaxDelta, so that the apply's error stays below the target.
+constexpr double kRelaxDelta = 1e-5;
+
+// w = S z for an FP32 z vanishing on constrained rows, FP32 arithmetic, FP64 w (already 0)
+stmg_status op_apply_f2d(stmg_ctx* ctx, Level& L, const float* x, double* y) {
+  OpTab<float> t = L.tab32;
+  t.sign = 1.0f;
+  const int64_t ss = L.slab_size();
+  for (int i = 0; i < L.nc; ++i) {
+    CK(launch_apply_f2d(L.dim, L.n, L.nt, x + i * ss, y + i * ss, L.geo32, L.g, t, 1, ctx->stream));
+    if (i > 0)
+      CK(launch_mass_couple<double, float, double>(L.dim, L.n, L.nt, x + (i - 1) * ss, y + i * ss, L.geo64, L.g,
+                                                   L.cpl64, ctx->stream));
+  }
+  ctx->launches += 2 * L.nc - 1;
+  return STMG_OK;
+}
+
+// z_j = B v_j, v_{j+1} = S z_j, CGS2 against v_0..v_j, Hessenberg column to the host buffer.
+// low: the operator apply in FP32 arithmetic (relaxed FGMRES), else double-float / FP64.
+stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool low = false) {
   Level& L = ctx->levels[0];
   const int64_t n = L.size();
   double* v = ctx->V + (size_t)j * ctx->vld;
@@ -1089,7 +1113,8 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
     L.u32 = saved;
     CKS(st);
     CK(cudaMemsetAsync(w, 0, sizeof(double) * n, ctx->stream));
-    CKS(op_apply_df(ctx, L, z32, w, false));
+    if (low) CKS(op_apply_f2d(ctx, L, z32, w));
+    else CKS(op_apply_df(ctx, L, z32, w, false));
     return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n, j + 1 < ctx->m ? L.f32 : nullptr);
   }
   if (ctx->opt.vcycle_precision == STMG_FP32) {
@@ -1109,18 +1134,20 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture) {
   return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n);
 }
 
-stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
+stmg_status fgmres_iteration(stmg_ctx* ctx, int j, bool low = false) {
   const bool warmed = ctx->opt.vcycle_precision == STMG_FP32 ? ctx->warmed32 : ctx->warmed64;
-  if (!warmed) return fgmres_iteration_enqueue(ctx, j, false);  // first V-cycle runs eagerly
-  if ((int)ctx->iter_graphs.size() < ctx->m) {
-    ctx->iter_graphs.assign(ctx->m, nullptr);
-    ctx->iter_graph_kernels.assign(ctx->m, 0);
+  if (!warmed) return fgmres_iteration_enqueue(ctx, j, false, low);  // first V-cycle runs eagerly
+  std::vector<cudaGraphExec_t>& graphs = low ? ctx->iter_graphs_low : ctx->iter_graphs;
+  std::vector<int64_t>& kernels = low ? ctx->iter_graph_kernels_low : ctx->iter_graph_kernels;
+  if ((int)graphs.size() < ctx->m) {
+    graphs.assign(ctx->m, nullptr);
+    kernels.assign(ctx->m, 0);
   }
-  if (!ctx->iter_graphs[j]) {
+  if (!graphs[j]) {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     const int64_t saved = ctx->launches;
-    stmg_status st = fgmres_iteration_enqueue(ctx, j, true);
+    stmg_status st = fgmres_iteration_enqueue(ctx, j, true, low);
     ctx->launches = saved;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
     if (st != STMG_OK) return st;
@@ -1135,13 +1162,13 @@ stmg_status fgmres_iteration(stmg_ctx* ctx, int j) {
       cudaGraphNodeGetType(nd, &ty);
       if (ty == cudaGraphNodeTypeKernel) ++nk;
     }
-    e = cudaGraphInstantiate(&ctx->iter_graphs[j], graph, 0);
+    e = cudaGraphInstantiate(&graphs[j], graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { ctx->err = std::string("instantiate: ") + cudaGetErrorString(e); ctx->iter_graphs[j] = nullptr; return STMG_ERR_CUDA; }
-    ctx->iter_graph_kernels[j] = nk;
+    if (e != cudaSuccess) { ctx->err = std::string("instantiate: ") + cudaGetErrorString(e); graphs[j] = nullptr; return STMG_ERR_CUDA; }
+    kernels[j] = nk;
   }
-  CK(cudaGraphLaunch(ctx->iter_graphs[j], ctx->stream));
-  ctx->launches += ctx->iter_graph_kernels[j];
+  CK(cudaGraphLaunch(graphs[j], ctx->stream));
+  ctx->launches += kernels[j];
   return STMG_OK;
 }
 
@@ -1192,8 +1219,10 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     g[0] = beta;
     int jend = 0;
     bool breakdown = false;
+    bool low = false;  // relaxed apply: only after the residual estimate has fallen far enough
     for (int j = 0; j < m; ++j) {
-      CKS(fgmres_iteration(ctx, j));
+      CKS(fgmres_iteration(ctx, j, low));
+      if (low) s.relaxed_iterations++;
       std::vector<double> h;
       double hn = 0.0;
       CKS(orthogonalise_read(ctx, j + 1, h, hn));
@@ -1217,6 +1246,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
       g[j] = cs[j] * g[j];
       ++its;
       jend = j + 1;
+      low = ctx->opt.outer_relax && ctx->outer_df && std::fabs(g[j + 1]) <= target / kRelaxDelta;
       if (hn == 0.0) { breakdown = true; break; }
       if (std::fabs(g[j + 1]) <= target || its >= ctx->opt.max_it) break;
     }
@@ -1406,6 +1436,8 @@ stmg_status stmg_destroy(stmg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (stmg_net* net : ctx->nets) net_detach(net);
   for (auto g : ctx->iter_graphs)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto g : ctx->iter_graphs_low)
     if (g) cudaGraphExecDestroy(g);
   if (ctx->graph32) cudaGraphExecDestroy(ctx->graph32);
   if (ctx->graph64) cudaGraphExecDestroy(ctx->graph64);

@@ -331,3 +331,26 @@ def test_weighted_smoother_vcycle_and_solve(env, case):
     xd = prob.solve(b).reshape(-1)
     assert np.linalg.norm(u.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-8
     ctx.close()
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[6]], ids=lambda c: c.name)
+def test_relaxed_outer_apply_reaches_the_same_solution(env, case):
+    """outer_relax = 1 (inexact Krylov): once the residual estimate is below 1e5 x the target, the
+    FGMRES apply runs in FP32; the stopping test stays on the accurate residual, so the solution and
+    its true residual are as without relaxation."""
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    prob = H.levels[0].prob
+    b = _rand(prob.n, 710, prob.bmask_full)
+    xd = prob.solve(b).reshape(-1)
+    for rtol in (1e-9, 1e-12):
+        ctx = make_context(stmg, case, H, rtol=rtol, max_it=300, outer_relax=1)
+        u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        st = ctx.solve(torch.from_numpy(b).cuda(), u)
+        un = u.cpu().numpy()
+        rres = np.linalg.norm(b - prob.S @ un) / np.linalg.norm(b)
+        assert st["converged"] and rres <= 1.05 * rtol, (case.name, rtol, rres, st)
+        assert st["relaxed_iterations"] >= 1, st
+        if rtol == 1e-12:
+            assert np.linalg.norm(un - xd) / np.linalg.norm(xd) < 1e-8, (case.name, st)
+        ctx.close()
