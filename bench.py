@@ -165,7 +165,9 @@ def run_kernel_only(args):
     torch.cuda.set_device(0)
     wl = workload(args.n_cells)
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
-                       vcycle_precision=stmg.FP32, inverse_precision=stmg.BF16, omega=[0.2] * 16)
+                       vcycle_precision=stmg.FP32, omega=[0.2] * 16,
+                       inverse_precision={"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64,
+                                          "fp8": stmg.FP8}[args.inverse])
     kind, prec = {"apply64": (stmg.KERNEL_APPLY, stmg.FP64), "apply32": (stmg.KERNEL_APPLY, stmg.FP32),
                   "applydf": (stmg.KERNEL_APPLY, stmg.DF32),
                   "asm32": (stmg.KERNEL_ASM, stmg.FP32), "asm64": (stmg.KERNEL_ASM, stmg.FP64),
@@ -198,7 +200,8 @@ def run_ours(args):
 
     wl = workload(args.n_cells)
     vprec = stmg.FP64 if args.plain else stmg.FP32
-    inv_prec = {"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64}[args.inverse] if not args.plain else stmg.FP64
+    inv_prec = {"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64, "fp8": stmg.FP8}[args.inverse] \
+        if not args.plain else stmg.FP64
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                        vcycle_precision=vprec, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
                        coarse_max_dofs=args.coarse_max_dofs, asm_weighting=args.asm_weighting,
@@ -387,7 +390,7 @@ def run_ours(args):
     if rank == 0:
         apply_ms = ctx.time_kernel(stmg.KERNEL_APPLY, 0, stmg.FP64, reps=20)
         asm_ms = ctx.time_kernel(stmg.KERNEL_ASM, 0, stmg.FP32, reps=20)
-        inv_bytes = {"fp32": 4, "bf16": 2, "fp64": 8}[args.inverse if not args.plain else "fp64"]
+        inv_bytes = {"fp32": 4, "bf16": 2, "fp64": 8, "fp8": 1}[args.inverse if not args.plain else "fp64"]
         vc_ms = ctx.time_kernel(stmg.KERNEL_VCYCLE, 0, vprec, reps=10)
         nq = wl["p"] + 1
         cells = wl["N"] ** 3
@@ -403,11 +406,15 @@ def run_ours(args):
                      "peak_source": "FP64 1.25 TFLOP/s nominal (GB300 table; no measured FP64 peak)",
                      "avg_launch_ms": apply_ms}
         nb = nq ** 3
-        asm_bytes = cells * nt * nb * ((nb + 3) // 4 * 4) * inv_bytes + 2 * 4 * n  # rows padded to 4
+        # the stored cell blocks (planes with rows padded to 4 entries; FP8: one FP32 scale per plane)
+        plane_entries = nt * nb * ((nb + 3) // 4 * 4)
+        cell_bytes = ((plane_entries + 4 * nt + 15) // 16 * 16 if inv_bytes == 1 else
+                      (plane_entries + 7) // 8 * 8 * inv_bytes)
+        asm_bytes = cells * cell_bytes + 2 * 4 * n
         asm_roof = {"kernel": "asm_apply_tma_kernel<3,3,3,float,bf16> (finest-level additive Schwarz, TMA-fed)",
                     "bound": "hbm", "achieved": asm_bytes / (asm_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": asm_bytes / (asm_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                    "traffic": read_traffic("asm_bf16") if args.inverse == "bf16" else None,
+                    "traffic": read_traffic(f"asm_{args.inverse}") if args.inverse in ("bf16", "fp8") else None,
                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "algorithmic_bytes": asm_bytes, "inverse_storage": args.inverse, "avg_launch_ms": asm_ms}
         if args.plain:
@@ -795,7 +802,7 @@ def main():
     ap.add_argument("--net", action="store_true", help="learned guess on this workload too (trained on slabs 0-15)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "shm"])
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64"],
+    ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64", "fp8"],
                     help="storage of the Schwarz inverses in the mixed solver")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],

@@ -60,7 +60,8 @@ enum { STMG_DG = 0, STMG_CGP = 1 };                    /* time discretisation, S
 enum { STMG_COEFF_PER_CELL = 0, STMG_COEFF_PER_QPOINT = 1 };
 /* STMG_DF32 = double-float: FP32 input vector, arithmetic on pairs of FP32 numbers (about 44
  * significand bits), FP64 output; only for the finest-level operator (outer_apply, stmg_apply). */
-enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3, STMG_DF32 = 4 };   /* 0 in an option = default */
+/* STMG_FP8: e4m3 with one FP32 scale per stored plane (Schwarz inverses only, FP32 V-cycle). */
+enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3, STMG_DF32 = 4, STMG_FP8 = 5 };   /* 0 in an option = default */
 enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2 };
 
 /* Structured grid of n_cells^dim cells.  vertices: HOST array of
@@ -106,7 +107,7 @@ typedef struct {
   int nu_pre;              /* pre-smoothing sweeps nu_1 of Algorithm stmg [1] */
   int nu_post;             /* post-smoothing sweeps nu_2 [1] */
   int vcycle_precision;    /* STMG_FP32 (mixed) or STMG_FP64 (plain) [FP32] */
-  int inverse_precision;   /* storage of dense local inverses: FP64/FP32/BF16 [same as V-cycle] */
+  int inverse_precision;   /* storage of dense local inverses: FP64/FP32/BF16/FP8 [same as V-cycle] */
   int smoother_kind;       /* AUTO, DENSE or FD [AUTO: FD on Cartesian grids with constant rho, else DENSE] */
   const double* omega;     /* host, may be NULL */
   int fgmres_restart;      /* [30] */

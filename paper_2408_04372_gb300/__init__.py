@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libstmg.so")
 HEAT, WAVE = 0, 1
 DG, CGP = 0, 1
 COEFF_PER_CELL, COEFF_PER_QPOINT = 0, 1
-FP64, FP32, BF16, DF32 = 1, 2, 3, 4
+FP64, FP32, BF16, DF32, FP8 = 1, 2, 3, 4, 5
 SMOOTHER_AUTO, SMOOTHER_DENSE, SMOOTHER_FD = 0, 1, 2
 COARSEN_P_THEN_H, COARSEN_H = 0, 1
 

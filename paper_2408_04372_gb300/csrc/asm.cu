@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -33,10 +35,22 @@ struct Shape {
 };
 
 // Inverse store: per cell N_t planes of NB rows x NBP columns, row-major, NBP = NB rounded up to a
-// multiple of 4 (zero padding), so that a row starts on an 8-byte boundary (BF16) and is read four
-// entries at a time; cell blocks padded to a multiple of 8 elements (16-byte boundaries).
+// multiple of 4 (zero padding), so that a row starts on a 4-entry boundary and is read four entries
+// at a time; cell blocks padded to 16-byte boundaries.  FP8 (e4m3) planes carry one FP32 scale each
+// (entry = stored value x scale, the plane's largest magnitude mapped to 448), stored after the
+// cell's planes, so that one bulk copy brings a cell's planes and scales together.
 __host__ __device__ constexpr int nb_pad(int nb) { return (nb + 3) / 4 * 4; }
-__host__ __device__ constexpr int64_t cell_stride(int nb, int nt) { return ((int64_t)nt * nb * nb_pad(nb) + 7) / 8 * 8; }
+__host__ __device__ constexpr int64_t cell_stride(int nb, int nt, int esz = 2) {
+  return esz == 1 ? ((int64_t)nt * nb * nb_pad(nb) + 4 * nt + 15) / 16 * 16
+                  : ((int64_t)nt * nb * nb_pad(nb) + 7) / 8 * 8;
+}
+template <typename TI> constexpr bool is_fp8() { return std::is_same<TI, __nv_fp8_e4m3>::value; }
+// FP8 planes: the scale of plane m, stored after the cell's planes (other types: 1)
+template <typename TI, int NB, int NT>
+__device__ __forceinline__ float plane_scale(const TI* cell, int m) {
+  if constexpr (is_fp8<TI>()) return reinterpret_cast<const float*>(cell + (int64_t)NT * NB * nb_pad(NB))[m];
+  else return 1.0f;
+}
 
 __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ inline double2 cinv(double2 a) {
@@ -60,6 +74,7 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
   double2* fcol = C + NB * NB;
   int* ipiv = reinterpret_cast<int*>(fcol + NB);
   __shared__ int s_piv;
+  __shared__ double s_scale;
   const int64_t cell = blockIdx.x;
   const int tid = threadIdx.x;
   const int p = g.p;
@@ -185,7 +200,28 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
     constexpr int NBP = nb_pad(NB);
     const int nplanes = m < nreal ? 1 : 2;
     for (int pl = 0; pl < nplanes; ++pl) {
-      const int64_t base = (int64_t)cell * cell_stride(NB, nt) + (int64_t)(plane + pl) * NB * NBP;
+      const int64_t cbase = (int64_t)cell * cell_stride(NB, nt, inv_prec == 3 ? 1 : 2);
+      const int64_t base = cbase + (int64_t)(plane + pl) * NB * NBP;
+      double fp8_inv_scale = 1.0;
+      if (inv_prec == 3) {
+        // the plane's largest weighted magnitude maps to 448, the largest finite e4m3 value
+        if (tid == 0) {
+          double mx = 0.0;
+          for (int a = 0; a < NB; ++a) {
+            double wa = 1.0;
+            if (weighted) wa = node_weight<double>(cx * p + a % N, cy * p + (a / N) % N, cz * p + a / (N * N), DIM, p);
+            for (int b = 0; b < NB; ++b) {
+              const double2 v = C[a * NB + b];
+              mx = fmax(mx, fabs((pl == 0 ? v.x : v.y) * wa));
+            }
+          }
+          reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(inv_out) + cbase + (int64_t)nt * NB * NBP)[plane + pl] =
+              mx > 0.0 ? (float)(mx / 448.0) : 1.0f;
+          s_scale = mx > 0.0 ? 448.0 / mx : 1.0;
+        }
+        __syncthreads();
+        fp8_inv_scale = s_scale;
+      }
       for (int pr = tid; pr < NB * NBP; pr += blockDim.x) {
         const int a = pr / NBP, b = pr % NBP;
         const double2 v = b < NB ? C[a * NB + b] : make_double2(0.0, 0.0);
@@ -195,8 +231,10 @@ asm_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, const 
         if (weighted) x *= node_weight<double>(cx * p + a % N, cy * p + (a / N) % N, cz * p + a / (N * N), DIM, p);
         if (inv_prec == 0) reinterpret_cast<double*>(inv_out)[base + pr] = x;
         else if (inv_prec == 1) reinterpret_cast<float*>(inv_out)[base + pr] = (float)x;
-        else reinterpret_cast<__nv_bfloat16*>(inv_out)[base + pr] = __float2bfloat16((float)x);
+        else if (inv_prec == 2) reinterpret_cast<__nv_bfloat16*>(inv_out)[base + pr] = __float2bfloat16((float)x);
+        else reinterpret_cast<__nv_fp8_e4m3*>(inv_out)[base + pr] = __nv_fp8_e4m3((float)(x * fp8_inv_scale));
       }
+      __syncthreads();  // s_scale is rewritten by the next plane
     }
     plane += nplanes;
     __syncthreads();
@@ -210,6 +248,7 @@ template <> __device__ inline __nv_bfloat16 ldg_inv<__nv_bfloat16>(const __nv_bf
   return __ushort_as_bfloat16(v);
 }
 template <> __device__ inline float to_f<float>(float v) { return v; }
+template <> __device__ inline float to_f<__nv_fp8_e4m3>(__nv_fp8_e4m3 v) { return (float)v; }
 template <> __device__ inline float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <typename T, typename TI> __device__ inline T inv_val(TI v) { return (T)to_f<TI>(v); }
 template <> __device__ inline double inv_val<double, double>(double v) { return v; }
@@ -219,7 +258,7 @@ template <int DIM, int N, int NT, typename TI>
 struct AsmCfg {
   static constexpr int NB = Shape<DIM, N>::NB;
   static constexpr int TPC = (NB + 31) / 32 * 32;
-  static constexpr int64_t CS = cell_stride(NB, NT);
+  static constexpr int64_t CS = cell_stride(NB, NT, (int)sizeof(TI));
   static constexpr int CPB = TPC >= 128 ? 1 : 128 / TPC;
 };
 
@@ -328,7 +367,7 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
 template <int DIM, int N, int NT, typename TI>
 struct TmaCfg {
   static constexpr int NB = Shape<DIM, N>::NB;
-  static constexpr int64_t CS = cell_stride(NB, NT);
+  static constexpr int64_t CS = cell_stride(NB, NT, (int)sizeof(TI));
   static constexpr int CELL_BYTES = (int)(CS * sizeof(TI));
   static constexpr int CPG0 = 128 / NB;
   static constexpr int CPG_MEM = 20480 / CELL_BYTES;
@@ -350,6 +389,13 @@ __device__ __forceinline__ float4 inv4(const __nv_bfloat16* p) {
                      __uint_as_float(w.y & 0xffff0000u));
 }
 __device__ __forceinline__ float4 inv4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 inv4(const __nv_fp8_e4m3* p) {  // 4-byte aligned
+  const unsigned int w = *reinterpret_cast<const unsigned int*>(p);
+  const __half2 lo = __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3));
+  const __half2 hi = __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3));
+  const float2 a = __half22float2(lo), b = __half22float2(hi);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
 __device__ __forceinline__ float4 inv4(const double* p) {
   const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
   return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
@@ -524,24 +570,26 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
       for (int m = 0; m < NT; ++m) {
         const TI* rr = ic + (m * NB + a) * NBP;  // row a of plane m
         if (m < mt.nreal) {
+          const T sc = (T)plane_scale<TI, NB, NT>(ic, m);
           if constexpr (std::is_same<T, float>::value) {
-            z[m] = dot_row<NBP>(rr, s_r[slot][m]);
+            z[m] = sc * dot_row<NBP>(rr, s_r[slot][m]);
           } else {
             T acc = 0;
 #pragma unroll
             for (int b = 0; b < NB; ++b) acc += inv_val<T, TI>(rr[b]) * s_r[slot][m][b];
-            z[m] = acc;
+            z[m] = sc * acc;
           }
         } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
           const TI* ri = rr + NB * NBP;  // imaginary part: the next plane
+          const T sr = (T)plane_scale<TI, NB, NT>(ic, m), si = (T)plane_scale<TI, NB, NT>(ic, m + 1);
           if constexpr (std::is_same<T, float>::value) {
-            z[m] = dot_row<NBP>(rr, s_r[slot][m]) - dot_row<NBP>(ri, s_r[slot][m + 1]);
-            z[m + 1] = dot_row<NBP>(rr, s_r[slot][m + 1]) + dot_row<NBP>(ri, s_r[slot][m]);
+            z[m] = sr * dot_row<NBP>(rr, s_r[slot][m]) - si * dot_row<NBP>(ri, s_r[slot][m + 1]);
+            z[m + 1] = sr * dot_row<NBP>(rr, s_r[slot][m + 1]) + si * dot_row<NBP>(ri, s_r[slot][m]);
           } else {
             T zr = 0, zi = 0;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-              const T ir = inv_val<T, TI>(rr[b]), ii = inv_val<T, TI>(ri[b]);
+              const T ir = sr * inv_val<T, TI>(rr[b]), ii = si * inv_val<T, TI>(ri[b]);
               const T sre = s_r[slot][m][b], sim = s_r[slot][m + 1][b];
               zr += ir * sre - ii * sim;
               zi += ir * sim + ii * sre;
@@ -626,6 +674,9 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
   // timeout to, or when S stages of one cell's planes exceed the shared memory of an SM (p = 3,
   // N_t = 4, FP64)
   if (!status || TmaCfg<DIM, N, NT, TI>::SMEM > (size_t)200 * 1024) {
+    if constexpr (is_fp8<TI>()) {
+      return cudaErrorInvalidValue;  // FP8 planes carry scales that only the bulk-copy kernel reads
+    } else {
     using C = AsmCfg<DIM, N, NT, TI>;
     const int64_t blocks = (g.n_cells + C::CPB - 1) / C::CPB;
     for (int sl = 0; sl < nslab; ++sl) {
@@ -636,6 +687,7 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
       if (e_ != cudaSuccess) return e_;
     }
     return cudaGetLastError();
+    }
   }
   return nslab > 1 ? launch_tma<DIM, N, NT, T, TI, true>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s)
                    : launch_tma<DIM, N, NT, T, TI, false>(r, u, inv, g, mt, cs, cd, status, 1, ss, s);
@@ -648,7 +700,7 @@ cudaError_t launch_wait_selftest(int* status, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int64_t asm_cell_stride(int dim, int n, int nt) { return cell_stride(dim == 3 ? n * n * n : n * n, nt); }
+int64_t asm_cell_stride(int dim, int n, int nt, int esz) { return cell_stride(dim == 3 ? n * n * n : n * n, nt, esz); }
 
 cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const double* geo64, const LocalTab& lt,
                              const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
@@ -671,7 +723,8 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
   if (dim == DIM && n == N && nt == NT) {                                                          \
     if (inv_prec == 0) return apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s); \
     if (inv_prec == 1) return apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);  \
-    return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);             \
+    if (inv_prec == 2) return apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s); \
+    return apply_t<DIM, N, NT, T, __nv_fp8_e4m3>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);            \
   }
 
 template <typename T>

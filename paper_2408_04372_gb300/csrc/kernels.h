@@ -59,7 +59,7 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
                              const double* lam_re, const double* lam_im, int nreal, int ncplx, void* inv,
                              int inv_prec, int weighted, cudaStream_t s);
 // elements per cell in the inverse store (N_t planes, padded to a 16-byte multiple)
-int64_t asm_cell_stride(int dim, int n, int nt);
+int64_t asm_cell_stride(int dim, int n, int nt, int esz);
 // copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell.
 // status (device int, may be NULL): with it the inverses arrive by bulk copies (TMA) into shared memory and
 // a timed-out wait stores STMG_DEVICE_TIMEOUT there; without it each thread streams its rows itself.

@@ -693,9 +693,9 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     ctx->err = "dense additive Schwarz setup supports p <= 3 in 3D";
     return STMG_ERR_UNSUPPORTED;
   }
-  const size_t esz = L.inv_prec == 0 ? 8 : L.inv_prec == 1 ? 4 : 2;
+  const size_t esz = L.inv_prec == 0 ? 8 : L.inv_prec == 1 ? 4 : L.inv_prec == 2 ? 2 : 1;
   (void)NB;
-  const size_t count = (size_t)L.g.n_cells * asm_cell_stride(L.dim, L.n, nt);
+  const size_t count = (size_t)L.g.n_cells * asm_cell_stride(L.dim, L.n, nt, (int)esz);
   void* inv = nullptr;
   cudaError_t e = cudaMalloc(&inv, count * esz);
   if (e != cudaSuccess) { ctx->err = std::string("cudaMalloc inverses: ") + cudaGetErrorString(e); return STMG_ERR_OOM; }
@@ -853,8 +853,13 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (o.outer_apply == STMG_DF32 && o.vcycle_precision != STMG_FP32)
     return invalid(ctx, "the double-float outer apply needs the FP32 V-cycle");
   ctx->outer_df = o.outer_apply == STMG_DF32;
-  if (o.inverse_precision < STMG_FP64 || o.inverse_precision > STMG_BF16) return invalid(ctx, "inverse_precision out of range");
-  const int inv_prec = o.inverse_precision == STMG_FP64 ? 0 : o.inverse_precision == STMG_FP32 ? 1 : 2;
+  if (o.inverse_precision != STMG_FP64 && o.inverse_precision != STMG_FP32 && o.inverse_precision != STMG_BF16 &&
+      o.inverse_precision != STMG_FP8)
+    return invalid(ctx, "inverse_precision out of range");
+  if (o.inverse_precision == STMG_FP8 && o.vcycle_precision != STMG_FP32)
+    return invalid(ctx, "FP8 inverses need the FP32 V-cycle");
+  const int inv_prec = o.inverse_precision == STMG_FP64 ? 0 : o.inverse_precision == STMG_FP32 ? 1
+                     : o.inverse_precision == STMG_BF16 ? 2 : 3;
   ctx->opt = o;
   const int64_t nv1 = N + 1;
   const int64_t nverts = dim == 3 ? nv1 * nv1 * nv1 : nv1 * nv1;

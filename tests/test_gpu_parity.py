@@ -354,3 +354,32 @@ def test_relaxed_outer_apply_reaches_the_same_solution(env, case):
         if rtol == 1e-12:
             assert np.linalg.norm(un - xd) / np.linalg.norm(xd) < 1e-8, (case.name, st)
         ctx.close()
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=lambda c: c.name)
+def test_fp8_inverses(env, case):
+    """inverse_precision = FP8 (e4m3, one FP32 scale per plane, weighted sum): one smoothing sweep
+    differs from the oracle's exact one by the rounding of 4 significant bits (2^-4 relative per
+    stored plane entry; the planes are time modes, so the bound passes through the time transforms:
+    10 % norm-wise), and FGMRES reaches the same solution (the smoother's precision does not enter
+    the solution, only the iteration count)."""
+    torch, stmg = env
+    from oracle import mg
+    H = mg.Hierarchy(case.dim, case.N, case.p, case.k, case.pde, case.scheme, case.tau, case.vertices(),
+                     rho_cell=case.rho_cell(), weighted=True)
+    ctx = make_context(stmg, case, H, inverse_precision=stmg.FP8, asm_weighting=1, rtol=1e-12, max_it=300)
+    lev = H.levels[0]
+    prob = lev.prob
+    f = _rand(prob.n, 820, prob.bmask_full)
+    u = np.zeros(prob.n)
+    corr = lev.omega * (lev.B @ f)
+    u32 = torch.zeros(prob.n, dtype=torch.float32, device="cuda")
+    ctx.smooth(torch.from_numpy(f).to("cuda", torch.float32), u32, sweeps=1, level=0)
+    rel = np.linalg.norm(u32.cpu().numpy() - corr) / np.linalg.norm(corr)
+    assert 1e-4 < rel < 0.1, (case.name, rel)  # FP8 rounding is visible, and bounded
+    b = _rand(prob.n, 821, prob.bmask_full)
+    ud = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st = ctx.solve(torch.from_numpy(b).cuda(), ud)
+    xd = prob.solve(b).reshape(-1)
+    assert st["converged"] and np.linalg.norm(ud.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-8, st
+    ctx.close()
