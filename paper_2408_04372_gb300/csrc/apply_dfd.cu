@@ -24,4 +24,20 @@ cudaError_t launch_apply_df_d(int dim, int n, int nt, const double* x, double* y
   return cudaErrorInvalidValue;
 }
 
+#define STMG_MASS_DFD_CASE(DIM, N, NT)                                              \
+  if (dim == DIM && n == N && nt == NT) return launch_apply_t<DIM, N, NT, df64, double, double, true>(x, y, geo, g, tab, 0, s);
+
+cudaError_t launch_mass_apply_df(int dim, int n, int nt, const double* x, double* y, const df64* geo, const GridDesc& g,
+                                 const OpTab<df64>& tab, cudaStream_t s) {
+  STMG_MASS_DFD_CASE(3, 2, 1) STMG_MASS_DFD_CASE(3, 2, 2) STMG_MASS_DFD_CASE(3, 2, 3) STMG_MASS_DFD_CASE(3, 2, 4)
+  STMG_MASS_DFD_CASE(3, 3, 1) STMG_MASS_DFD_CASE(3, 3, 2) STMG_MASS_DFD_CASE(3, 3, 3) STMG_MASS_DFD_CASE(3, 3, 4)
+  STMG_MASS_DFD_CASE(3, 4, 1) STMG_MASS_DFD_CASE(3, 4, 2) STMG_MASS_DFD_CASE(3, 4, 3) STMG_MASS_DFD_CASE(3, 4, 4)
+  STMG_MASS_DFD_CASE(3, 5, 1) STMG_MASS_DFD_CASE(3, 5, 2) STMG_MASS_DFD_CASE(3, 5, 3) STMG_MASS_DFD_CASE(3, 5, 4)
+  STMG_MASS_DFD_CASE(2, 2, 1) STMG_MASS_DFD_CASE(2, 2, 2) STMG_MASS_DFD_CASE(2, 2, 3) STMG_MASS_DFD_CASE(2, 2, 4)
+  STMG_MASS_DFD_CASE(2, 3, 1) STMG_MASS_DFD_CASE(2, 3, 2) STMG_MASS_DFD_CASE(2, 3, 3) STMG_MASS_DFD_CASE(2, 3, 4)
+  STMG_MASS_DFD_CASE(2, 4, 1) STMG_MASS_DFD_CASE(2, 4, 2) STMG_MASS_DFD_CASE(2, 4, 3) STMG_MASS_DFD_CASE(2, 4, 4)
+  STMG_MASS_DFD_CASE(2, 5, 1) STMG_MASS_DFD_CASE(2, 5, 2) STMG_MASS_DFD_CASE(2, 5, 3) STMG_MASS_DFD_CASE(2, 5, 4)
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace stmg

@@ -28,6 +28,9 @@ cudaError_t launch_mass_couple(int dim, int n, int nt, const TI* x, TO* y, const
 // an FP64 output: the FGMRES apply on V-cycle outputs, which are exact in FP32.
 cudaError_t launch_apply_df(int dim, int n, int nt, const float* x, double* y, const df64* geo, const GridDesc& g,
                             const OpTab<df64>& tab, int mask_input, cudaStream_t s);
+// Mass part in double-float on an FP64 input split into float pairs (right-hand sides on level 0).
+cudaError_t launch_mass_apply_df(int dim, int n, int nt, const double* x, double* y, const df64* geo, const GridDesc& g,
+                                 const OpTab<df64>& tab, cudaStream_t s);
 // FP32 arithmetic on an FP32 input, accumulated into an FP64 output: the relaxed FGMRES apply once
 // the residual is small enough for its rounding (inexact Krylov).
 cudaError_t launch_apply_f2d(int dim, int n, int nt, const float* x, double* y, const float* geo, const GridDesc& g,

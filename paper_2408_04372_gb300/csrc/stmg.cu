@@ -1282,6 +1282,16 @@ stmg_status rhs_slab(stmg_ctx* ctx, const double* f, const double* f0, const dou
   const int nt = L.nt;
   const int64_t nn = L.g.n_nodes;
   CK(cudaMemsetAsync(rhs, 0, sizeof(double) * L.slab_size(), ctx->stream));
+  // mass terms: in double-float (FP32 pipe, about 44 bits) where the level has double-float geometry,
+  // else FP64
+  auto mass = [&](int ntm, const double* x, double* y, const OpTab<double>& tb) -> cudaError_t {
+    if (!L.geodf) return launch_mass_apply(L.dim, L.n, ntm, x, y, L.geo64, L.g, tb, ctx->stream);
+    OpTab<df64> td = L.tabdf;
+    for (int i = 0; i < kMaxNT; ++i)
+      for (int j = 0; j < kMaxNT; ++j) { td.TA[i][j] = df64(0.0f); td.TM[i][j] = df_split(tb.TM[i][j]); }
+    td.sign = df64(1.0f);
+    return launch_mass_apply_df(L.dim, L.n, ntm, x, y, L.geodf, L.g, td, ctx->stream);
+  };
   OpTab<double> t = L.tab64;
   for (int i = 0; i < kMaxNT; ++i)
     for (int j = 0; j < kMaxNT; ++j) {
@@ -1289,7 +1299,7 @@ stmg_status rhs_slab(stmg_ctx* ctx, const double* f, const double* f0, const dou
       t.TM[i][j] = (i < nt && j < nt) ? L.sc.RM_f[i * nt + j] : 0.0;
     }
   t.sign = 1.0;
-  if (f) CK(launch_mass_apply(L.dim, L.n, nt, f, rhs, L.geo64, L.g, t, ctx->stream));
+  if (f) CK(mass(nt, f, rhs, t));
   ctx->launches += 3;
   // single-block terms
   const double* srcs[4] = {f0, u0, u0, v0};
@@ -1310,7 +1320,7 @@ stmg_status rhs_slab(stmg_ctx* ctx, const double* f, const double* f0, const dou
     if (stiff[term]) t1.TA[0][0] = 1.0; else t1.TM[0][0] = 1.0;
     t1.sign = 1.0;
     if (stiff[term]) CK(launch_apply<double>(L.dim, L.n, 1, srcs[term], out, L.geo64, L.g, t1, 0, ctx->stream));
-    else CK(launch_mass_apply(L.dim, L.n, 1, srcs[term], out, L.geo64, L.g, t1, ctx->stream));
+    else CK(mass(1, srcs[term], out, t1));
     ctx->launches += 1;
     xs.push_back(out);
     used.push_back(term);

@@ -172,8 +172,8 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, const i
 }
 
 template <int K> struct CgsTma;
-template <> struct CgsTma<4> { static constexpr int E = 512, S = 4, BPS = 2; };
-template <> struct CgsTma<8> { static constexpr int E = 512, S = 3, BPS = 2; };
+template <> struct CgsTma<4> { static constexpr int E = 1024, S = 2, BPS = 2; };
+template <> struct CgsTma<8> { static constexpr int E = 768, S = 2, BPS = 2; };
 template <> struct CgsTma<16> { static constexpr int E = 512, S = 2, BPS = 1; };
 template <> struct CgsTma<32> { static constexpr int E = 128, S = 3, BPS = 1; };
 template <> struct CgsTma<64> { static constexpr int E = 64, S = 3, BPS = 1; };
