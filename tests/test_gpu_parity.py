@@ -383,3 +383,27 @@ def test_fp8_inverses(env, case):
     xd = prob.solve(b).reshape(-1)
     assert st["converged"] and np.linalg.norm(ud.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-8, st
     ctx.close()
+
+
+def test_smoother_row_streaming_fallback(env):
+    """3D Q3, dG(3) (N_t = 4), FP64 inverses: two stages of one cell's planes exceed the shared memory
+    of the bulk-copy kernel, so the row-streaming smoother runs; one sweep and the V-cycle against the
+    oracle."""
+    torch, stmg = env
+    from gpu_cases import Case
+    case = Case("heat3d_q3_dg3_jit", 3, 2, 3, 3, "heat", "dg", 0.1, True, "blocks")
+    H = oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H, vcycle_precision=stmg.FP64)
+    lev = H.levels[0]
+    prob = lev.prob
+    f = _rand(prob.n, 830, prob.bmask_full)
+    u = _rand(prob.n, 831, prob.bmask_full)
+    ref = u + lev.omega * (lev.B @ (f - prob.S @ u))
+    ud = torch.from_numpy(u).cuda()
+    ctx.smooth(torch.from_numpy(f).cuda(), ud, sweeps=1, level=0)
+    assert rel_err(ud.cpu().numpy(), ref) < 1e-9
+    r = _rand(prob.n, 832, prob.bmask_full)
+    e = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.from_numpy(r).cuda(), e)
+    assert rel_err(e.cpu().numpy(), H.vcycle(r)) < 1e-9
+    ctx.close()
