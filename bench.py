@@ -432,6 +432,13 @@ def run_ours(args):
                 "peak_source": "FP32 pipe 152 x 128 x 2.07 GHz / 15 instructions per double-float multiply-add, "
                                "in FP64-equivalent flop/s (derived)", "avg_launch_ms": df_ms}
             extra["apply_fp64_finest"] = roof_fp64
+            f32_ms = ctx.time_kernel(stmg.KERNEL_APPLY, 0, stmg.FP32, reps=20)
+            f32_peak = 152 * 128 * 2 * 2.07e9  # FP32 FMA lanes x 2 flop x max SM clock
+            extra["apply_fp32_finest"] = {
+                "kernel": "apply3d_kernel<N=3,NT=3,float> (finest level, V-cycle residuals)", "bound": "shared memory",
+                "achieved": flops / (f32_ms * 1e-3) / 1e12, "peak": f32_peak / 1e12, "unit": "TFLOP/s",
+                "frac": flops / (f32_ms * 1e-3) / f32_peak, "avg_launch_ms": f32_ms,
+                "note": "fraction of the FP32-pipe peak; the kernel is bound by its shared-memory transposes"}
         extra["vcycle_ms"] = vc_ms
         if not args.skip_cpu:
             v, d, dt = oracle_sample(10, 4, wl["tau"])
