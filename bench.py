@@ -149,7 +149,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "heat3d_q2_dg2_10cubed_jitter0.15_rho2blocks (oracle sample)"},
+            "data": "synthetic",
+            "config": {"workload": workload(args.n_cells)["name"], "cells": args.n_cells ** 3, "p": 2, "time": "dG(2)",
+                       "rtol": 1e-8, "oracle_sample": "10^3 cells of the same family, direct solves (see cpu_baseline)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
