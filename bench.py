@@ -532,7 +532,7 @@ def run_learned_c5(args):
     tau = 1.0 / n_slabs
     n_train = n_slabs // 2
     ctx = stmg.Context(3, N, p, k, tau, vcycle_precision=stmg.FP32, rtol=1e-8, restart=30, max_it=200,
-                       asm_weighting=args.asm_weighting)
+                       asm_weighting=args.asm_weighting, outer_relax=args.outer_relax)
     nt, nn = ctx.nt, ctx.n_nodes
     n = nt * nn
     X = ctx.node_coords()
