@@ -104,3 +104,41 @@ def test_at_once_vcycle_in_fgmres_reaches_the_direct_solution(nc):
     e0 = x.copy()
     e1 = e0 - H.vcycle(prob.S @ e0)
     assert np.linalg.norm(e1) < 0.5 * np.linalg.norm(e0)
+
+
+def test_weighted_at_once_smoother_brute_force_and_fewer_iterations():
+    """Weighted Schwarz sum on the at-once system: each cell block's inverse rows divided by the number
+    of cells containing the node, built here from the at-once matrix; the weighted V-cycle needs no
+    more FGMRES iterations than the plain one."""
+    from oracle import space
+    V = synth.jittered_vertices(2, 2)
+    H = atonce.AtOnceHierarchy(2, 2, 2, 1, 0.05, 3, V, estimate=False, weighted=True)
+    lev = H.levels[0]
+    S = lev.prob.S.toarray()
+    g = lev.prob.grid
+    nn, nt = g.n_nodes, lev.prob.nt
+    gl = space.lex_indices(g.nn1, g.dim)
+    shared = (gl % g.p == 0) & (gl > 0) & (gl < g.nn1 - 1)
+    mult = np.prod(np.where(shared, 2.0, 1.0), axis=1)
+    B = np.zeros_like(S)
+    for i in range(lev.prob.nc):
+        for cell in g.cell_dofs():
+            nodes = cell[~g.boundary_mask()[cell]]
+            idx = (i * nt * nn + np.arange(nt)[:, None] * nn + nodes[None, :]).reshape(-1)
+            w = np.tile(1.0 / mult[nodes], nt)
+            B[np.ix_(idx, idx)] += w[:, None] * np.linalg.inv(S[np.ix_(idx, idx)])
+    assert np.abs(lev.B.toarray() - B).max() <= 1e-12 * np.abs(B).max()
+    # iterations: weighted (capped omega) against plain, same problem
+    Vj = synth.jittered_vertices(4, 2)
+    rho = synth.block_coefficient(4, 2, blocks=2)
+    its = {}
+    for wt in (False, True):
+        Hw = atonce.AtOnceHierarchy(2, 4, 2, 1, 0.1, 4, Vj, rho_cell=rho, weighted=wt)
+        prob = Hw.levels[0].prob
+        b = synth.random_vector(prob.n, seed=6)
+        b[prob.bmask_full] = 0.0
+        res = mg.fgmres(lambda v: prob.S @ v, Hw.vcycle, b, np.zeros_like(b), rtol=1e-10)
+        x = prob.solve(b).reshape(-1)
+        assert np.linalg.norm(res.x - x) <= 1e-8 * np.linalg.norm(x)
+        its[wt] = res.iterations
+    assert its[True] <= its[False], its
