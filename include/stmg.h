@@ -175,7 +175,8 @@ stmg_status stmg_qpoint_coords(const stmg_ctx* ctx, int level, double* xyz);
 stmg_status stmg_apply(stmg_ctx* ctx, int level, int precision, const void* x, void* y);
 /* r = f - S_l u. */
 stmg_status stmg_residual(stmg_ctx* ctx, int level, int precision, const void* f, const void* u, void* r);
-/* sweeps of u <- u + omega_l sum_T R_T^T [R_T S_l R_T^T]^-1 R_T (f - S_l u)  (eqs. vanka0, vanka). */
+/* sweeps of u <- u + omega_l sum_T R_T^T D_T [R_T S_l R_T^T]^-1 R_T (f - S_l u)  (eqs. vanka0, vanka;
+ * D_T = I, or with asm_weighting the inverse number of cells containing each node). */
 stmg_status stmg_smooth(stmg_ctx* ctx, int level, int precision, int sweeps, const void* f, void* u);
 /* r_{l+1} = P_l^T r_l (restriction from level l to level l+1, Section 3.2). */
 stmg_status stmg_restrict(stmg_ctx* ctx, int level, int precision, const void* r_fine, void* r_coarse);

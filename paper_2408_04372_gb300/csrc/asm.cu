@@ -12,11 +12,14 @@
 // rounding) and takes N_t times less memory than the dense (N_t (p+1)^dim)^2 block.
 // Constrained (Dirichlet) nodes get identity rows/columns and zero residual.
 //
-// asm_apply: u += omega * sum_T R_T^T L_T^-1 R_T r, one warp-multiple per cell:
-// time transform of the residual, the planes' matrix-vector products with the
-// inverse rows streamed from HBM (the kernel is bound by this stream: N_t
-// (p+1)^(2 dim) numbers per cell), inverse transform; the additive sum over
-// overlapping cells uses atomic adds.
+// asm_apply: u += omega * sum_T R_T^T D_T L_T^-1 R_T r (D_T = I, or the inverse number of
+// cells containing each node for the weighted sum; the set-up folds D_T into the stored rows):
+// time transform of the residual, the planes' matrix-vector products, inverse transform; the
+// additive sum over overlapping cells uses atomic adds.  The bulk-copy kernel streams groups of
+// cells' planes (FP64, FP32, BF16, or FP8 with per-plane scales) into shared memory -- the kernel is
+// bound by this stream, N_t (p+1)^(2 dim) numbers per cell -- and, with several slabs in one
+// system, applies each landed group to every slab; the row-streaming kernel serves the cases
+// whose stages would not fit in shared memory.
 #include <algorithm>
 #include <type_traits>
 
