@@ -1057,23 +1057,6 @@ stmg_status vcycle_public(stmg_ctx* ctx, const T* r, T* e) {
   return STMG_OK;
 }
 
-// preconditioner z = B v on the finest level (FP64 in/out), V-cycle in the configured precision
-stmg_status precondition(stmg_ctx* ctx, const double* v, double* z) {
-  Level& L = ctx->levels[0];
-  const int64_t n = L.size();
-  if (ctx->opt.vcycle_precision == STMG_FP32) {
-    CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
-    CKS(run_vcycle<float>(ctx));
-    CK(launch_convert<float, double>(L.u32, z, n, ctx->stream));
-    ctx->launches += 2;
-  } else {
-    CK(cudaMemcpyAsync(L.f64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    CKS(run_vcycle<double>(ctx));
-    CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-  }
-  return STMG_OK;
-}
-
 // Relative error assumed for the FP32 operator apply in the relaxed FGMRES (inexact Krylov,
 // Simoncini & Szyld 2003): iteration j may use it once the residual estimate |g_j| is at most
 // target / kRelaxDelta, so that the apply's error stays below the target.
@@ -1223,7 +1206,6 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), cs(m, 0.0), sn(m, 0.0);
     g[0] = beta;
     int jend = 0;
-    bool breakdown = false;
     bool low = false;  // relaxed apply: only after the residual estimate has fallen far enough
     for (int j = 0; j < m; ++j) {
       CKS(fgmres_iteration(ctx, j, low));
@@ -1252,7 +1234,7 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
       ++its;
       jend = j + 1;
       low = ctx->opt.outer_relax && ctx->outer_df && std::fabs(g[j + 1]) <= target / kRelaxDelta;
-      if (hn == 0.0) { breakdown = true; break; }
+      if (hn == 0.0) break;  // breakdown: the Krylov space is invariant, the update below is exact
       if (std::fabs(g[j + 1]) <= target || its >= ctx->opt.max_it) break;
     }
     std::vector<double> y(jend, 0.0);
@@ -1267,7 +1249,6 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     else
       CK(launch_multi_axpy<double>(x, ctx->Z, n, ctx->dsm + 320, jend, 1.0, n, ctx->stream));
     ctx->launches += 1;
-    (void)breakdown;
   }
   s.iterations = its;
   if (st) *st = s;
@@ -1762,7 +1743,6 @@ stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f
   double* d_f0 = ctx->u_buf + 3 * n;        // nn each
   double* d_u0 = d_f0 + nn;
   double* d_v0 = d_u0 + nn;
-  double* d_v = ctx->tmp[4];
   CK(cudaMemcpyAsync(d_f, f, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d_u0, u0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
   if (f0) CK(cudaMemcpyAsync(d_f0, f0, sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream));
@@ -1774,7 +1754,6 @@ stmg_status stmg_solve_slab_host(stmg_ctx* ctx, const double* f, const double* f
   if (s != STMG_OK && s != STMG_ERR_NOT_CONVERGED) return s;
   CK(cudaMemcpyAsync(u, d_u, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
   if (v && ctx->pde == STMG_WAVE) {
-    (void)d_v;
     double* vbuf = ctx->rhs_buf;  // rhs no longer needed
     CKS(velocity_impl(ctx, d_u, d_u0, v0 ? d_v0 : nullptr, vbuf));
     CK(cudaMemcpyAsync(v, vbuf, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
