@@ -22,3 +22,16 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == "heat3d_q2_dg2_32cubed_jitter0.15_rho4blocks"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_records_match_the_current_sources_and_go_null_on_change(monkeypatch):
+    """profiles/traffic.json holds the DRAM bytes of the ncu captures; a record counts only while the
+    kernel's sources hash to the recorded value."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for key in ("asm_bf16", "apply_df32"):
+        assert bench.read_traffic(key) is not None and bench.read_traffic(key) > 1e7, key
+    monkeypatch.setattr(bench, "source_sha", lambda paths: "0" * 16)
+    assert bench.read_traffic("asm_bf16") is None
