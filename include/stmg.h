@@ -260,13 +260,15 @@ stmg_status stmg_net_weights(stmg_net* net, double* weights, double* biases);
  * not call cudaMalloc (or any allocating routine) on the path that smooths, for
  * example code whose device memory is fully handed to another allocator once
  * the context exists, or code that must not touch the context's own scratch.
- * Every GPU that loads the library holds the buffer until the process exits.
  * The paper has no counterpart; this is an interface variant only.
+ * - stmg_create looks up the buffer's device address on the device current at
+ *   create time; that lookup loads the library's device image there, so the
+ *   buffer is taken when the context is created, not at the first smoothing
+ *   call.  Every device on which a context was created holds it until the
+ *   process exits.  The same device must be current at every call
+ *   (STMG_ERR_INVALID_ARG otherwise).
  * - Returns STMG_ERR_INVALID_ARG, before any device work, when N_t * n_nodes of
  *   the level times the element size (8 for FP64, 4 for FP32) exceeds the buffer.
- * - The first call on a device looks up the buffer's device address on that
- *   device (the device must be current); make that first call before any
- *   stream capture.
  * - All calls share the one buffer and it keeps the last call's contents:
  *   calls that overlap on the GPU (other streams, other contexts, other
  *   threads) race; order them on one stream. */

@@ -233,6 +233,13 @@ class Context:
             return FP32
         raise TypeError("vectors must be float32 or float64")
 
+    @staticmethod
+    def _same(*ts):
+        """The library reads every vector of one call in the precision of the last one: all must agree."""
+        ts = [t for t in ts if t is not None]
+        if any(t.dtype != ts[0].dtype or t.device != ts[0].device for t in ts):
+            raise TypeError("vectors of one call must share dtype and device")
+
     def _vec(self, t, level=0):
         if t is None:
             return
@@ -242,6 +249,7 @@ class Context:
 
     def apply(self, x, y, level=0):
         self._vec(x, level); self._vec(y, level)
+        self._same(x, y)
         self._check(self.lib.stmg_apply(self.h, level, self._prec(x), _ptr(x), _ptr(y)))
 
     def apply_df(self, x, y):
@@ -255,27 +263,33 @@ class Context:
     def residual(self, f, u, r, level=0):
         for t in (f, u, r):
             self._vec(t, level)
+        self._same(f, u, r)
         self._check(self.lib.stmg_residual(self.h, level, self._prec(u), _ptr(f), _ptr(u), _ptr(r)))
 
     def smooth(self, f, u, sweeps=1, level=0):
         self._vec(f, level); self._vec(u, level)
+        self._same(f, u)
         self._check(self.lib.stmg_smooth(self.h, level, self._prec(u), sweeps, _ptr(f), _ptr(u)))
 
     def smooth_noalloc(self, f, u, sweeps=1, level=0):
         """stmg_smooth without device allocation: residual scratch in the library's fixed buffer."""
         self._vec(f, level); self._vec(u, level)
+        self._same(f, u)
         self._check(self.lib.stmg_smooth_noalloc(self.h, level, self._prec(u), sweeps, _ptr(f), _ptr(u)))
 
     def restrict(self, r_fine, r_coarse, level=0):
         self._vec(r_fine, level); self._vec(r_coarse, level + 1)
+        self._same(r_fine, r_coarse)
         self._check(self.lib.stmg_restrict(self.h, level, self._prec(r_fine), _ptr(r_fine), _ptr(r_coarse)))
 
     def prolongate_add(self, e_coarse, u_fine, level=0):
         self._vec(e_coarse, level + 1); self._vec(u_fine, level)
+        self._same(e_coarse, u_fine)
         self._check(self.lib.stmg_prolongate_add(self.h, level, self._prec(u_fine), _ptr(e_coarse), _ptr(u_fine)))
 
     def vcycle(self, r, e):
         self._vec(r); self._vec(e)
+        self._same(r, e)
         self._check(self.lib.stmg_vcycle(self.h, self._prec(r), _ptr(r), _ptr(e)))
 
     def rhs(self, f, rhs, f0=None, u0=None, v0=None):

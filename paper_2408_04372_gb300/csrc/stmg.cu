@@ -100,6 +100,8 @@ struct stmg_ctx {
   int64_t launches = 0;  // kernels issued by this context (graph replays count their kernel nodes)
   std::vector<stmg_net*> nets;  // networks bound to this context; detached when it is destroyed
   bool outer_df = false;        // FGMRES apply on V-cycle outputs in double-float (FP32 V-cycle only)
+  int device = -1;                  // CUDA device current at stmg_create
+  void* noalloc_scratch = nullptr;  // device address of the fixed smoothing scratch on that device
 };
 
 // A network outliving its context keeps only its own device memory; every later call on it
@@ -1376,27 +1378,22 @@ stmg_status check_level(stmg_ctx* ctx, int level, int precision) {
 
 }  // namespace
 
-// Fixed scratch for stmg_smooth_noalloc: part of the module image, so every GPU that
-// loads the library holds it until the process exits.  Host code must not use the
-// symbol as a pointer; it asks the runtime for the device address instead.
+// Fixed scratch for stmg_smooth_noalloc: part of this file's device image.  stmg_create looks
+// up its address, which loads the image, so every device on which a context was created holds
+// the buffer until the process exits.  Host code must not use the symbol as a pointer; it asks
+// the runtime for the device address instead.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[STMG_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the fixed scratch on the current device (looked up once per device).
-stmg_status noalloc_scratch(stmg_ctx* ctx, void** out) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return invalid(ctx, "device index out of range for the fixed scratch");
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+// Device address of the fixed scratch on the current device.  Looking it up also loads this
+// file's device image on that device (under lazy module loading it would otherwise load at the
+// first lookup), so stmg_create calls this once and keeps the result in the context.
+stmg_status resolve_noalloc_scratch(stmg_ctx* ctx) {
+  CK(cudaGetDevice(&ctx->device));
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  ctx->noalloc_scratch = p;
   return STMG_OK;
 }
 
@@ -1418,7 +1415,11 @@ stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_proble
     *out = ctx;
     return STMG_ERR_CUDA;
   }
-  stmg_status s;
+  stmg_status s = resolve_noalloc_scratch(ctx);
+  if (s != STMG_OK) {
+    *out = ctx;
+    return s;
+  }
   {
     StreamJoin join(ctx);
     s = create_impl(ctx, mesh, problem, options);
@@ -1772,8 +1773,11 @@ stmg_status stmg_smooth_noalloc(stmg_ctx* ctx, int level, int precision, int swe
     return invalid(ctx, "stmg_smooth_noalloc: level needs " + std::to_string(bytes) +
                             " bytes of residual scratch, more than the fixed " +
                             std::to_string((long long)STMG_NOALLOC_SCRATCH_BYTES) + " bytes");
-  void* scratch = nullptr;
-  CKS(noalloc_scratch(ctx, &scratch));
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return invalid(ctx, "stmg_smooth_noalloc: the device that was current at stmg_create must be current");
+  void* scratch = ctx->noalloc_scratch;
   StreamJoin join_(ctx);
   // every sweep overwrites the whole residual before reading it: nothing to clear
   if (precision == STMG_FP64)

@@ -70,3 +70,41 @@ def test_noalloc_smoother_rejects_levels_larger_than_the_fixed_buffer(env):
     ctx.smooth_noalloc(f32, u_b, sweeps=1, level=0)
     assert rel_err(u_b.cpu().numpy(), u_a.cpu().numpy()) < 2e-5
     ctx.close()
+
+
+_FRESH_PROCESS = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+import paper_2408_04372_gb300 as stmg
+torch.cuda.set_device(0)
+N, p, k = 6, 2, 2  # 3D Q2 dG(2): 3 * 13^3 values
+ctx = stmg.Context(3, N, p, k, 0.05, omega=[0.3] * 8, vcycle_precision=stmg.FP32)
+n = ctx.nt * ctx.n_nodes
+f = torch.ones(n, dtype=torch.float32, device="cuda")
+u = torch.zeros_like(f)
+u_ref = torch.zeros_like(f)
+ctx.smooth(f, u_ref, sweeps=1, level=0)  # loads the smoother kernels; allocates the context's own scratch
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+ctx.smooth_noalloc(f, u, sweeps=1, level=0)  # first call of the process
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+err = float((u - u_ref).abs().max() / u_ref.abs().max())
+print(free0, free1, err)
+"""
+
+
+def test_first_noalloc_call_takes_no_device_memory(env):
+    """In a fresh process the first call must not take the fixed buffer: stmg_create already did."""
+    import subprocess
+    import sys
+
+    from gpu_cases import ROOT
+    res = subprocess.run([sys.executable, "-c", _FRESH_PROCESS, ROOT], capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    free0, free1, err = res.stdout.split()[-3:]
+    drop = int(free0) - int(free1)
+    assert drop < SCRATCH_BYTES // 4, f"free device memory fell by {drop} bytes at the first call"
+    assert float(err) < 2e-5
