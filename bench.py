@@ -96,23 +96,68 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(n_cells: int, n_slabs: int, tau: float):
-    """Oracle slab marching (assembly, sparse LU once, one solve per slab) on an n_cells^3 sample."""
-    from oracle import slab, space
+ORACLE_SAMPLE_CELLS = 16   # oracle sample of the headline family: 16^3 cells (1/8 of the 32^3 grid)
+
+
+def oracle_c2_run(n_cells, slabs, warmup):
+    """The oracle's slab solve on the headline workload family at n_cells^3: the same jitter, the same
+    4^3 coefficient blocks, Q2, dG(2), tau = 1/32; per slab the right-hand side, the previous-slab guess
+    and FGMRES (rtol 1e-8) preconditioned by the oracle's V-cycle with the GPU arm's options (Schwarz sum
+    weighted by the node multiplicity, omega = 1 on every level, hierarchy ending at the first level with
+    at most 1500 unknowns).  Hierarchy set-up (assembly, local inverses) is timed apart.  Returns a dict."""
+    from oracle import mg
+    tau = 1.0 / 32
     t0 = time.perf_counter()
     V = synth.jittered_vertices(n_cells, 3)
-    rho = synth.block_coefficient(n_cells, 3, blocks=2)
-    g = space.Grid(n_cells, 3, 2, V)
-    prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, rho), "heat", "dg", 2, tau)
-    X = g.node_coords()
-    u_prev = np.zeros(g.n_nodes)
-    for n in range(n_slabs):
+    rho = synth.block_coefficient(n_cells, 3, blocks=4)
+    H = mg.Hierarchy(3, n_cells, 2, 2, "heat", "dg", tau, V, rho_cell=rho, weighted=True, coarse_max_dofs=1500,
+                     omegas=[1.0] * 16)
+    setup_s = time.perf_counter() - t0
+    prob = H.levels[0].prob
+    X = prob.grid.node_coords()
+    nn = prob.grid.n_nodes
+    u_prev = np.zeros(nn)
+    its = []
+
+    def step(n):
+        nonlocal u_prev
         f = np.stack([synth.heat_sine_source(X, tau * (n + th)) for th in prob.sys.tw.nodes])
-        u = prob.solve(prob.rhs(f, None, u_prev))
-        u_prev = u[-1]
-    dt = time.perf_counter() - t0
+        rhs = prob.rhs(f, None, u_prev).reshape(-1)
+        res = mg.fgmres(lambda v: prob.S @ v, H.vcycle, rhs, np.tile(u_prev, prob.nt), rtol=1e-8)
+        its.append(res.iterations)
+        u_prev = res.x.reshape(prob.nt, nn)[-1].copy()
+
+    for n in range(warmup):
+        step(n)
+    t1 = time.perf_counter()
+    for n in range(slabs):
+        step(warmup + n)
+    dt = time.perf_counter() - t1
     dofs = prob.nt * int((~prob.bmask).sum())
-    return dofs * n_slabs / dt, dofs, dt
+    return {"value": dofs * slabs / dt, "unit": UNIT, "dofs_per_slab": dofs, "slabs": slabs, "solve_s": dt,
+            "setup_s": setup_s, "fgmres_iterations_mean": float(np.mean(its[warmup:])),
+            "threads": os.environ.get("OMP_NUM_THREADS", str(os.cpu_count()))}
+
+
+def oracle_subprocess(n_cells, slabs, warmup, threads):
+    """oracle_c2_run in a fresh interpreter with `threads` BLAS/OpenMP threads (spawned, not forked,
+    so it is safe after CUDA initialisation in the parent)."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[var] = str(threads)
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-run", str(n_cells),
+                          "--steps", str(slabs), "--warmup", str(warmup)],
+                         env=env, capture_output=True, text=True, timeout=3600)
+    if res.returncode != 0:
+        raise RuntimeError(f"oracle run failed: {res.stderr[-2000:]}")
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_text(r, n_cells):
+    return (f"oracle slab solves (FGMRES + the oracle's V-cycle, rtol 1e-8, {r['fgmres_iterations_mean']:.1f} "
+            f"iterations) on the headline family at {n_cells}^3 cells ({r['dofs_per_slab']} DoFs per slab): "
+            f"{r['slabs']} slabs in {r['solve_s']:.1f} s after warm-up, hierarchy set-up {r['setup_s']:.1f} s "
+            f"excluded; scipy sparse products run on one thread whatever the BLAS thread count")
 
 
 def run_reference(args):
@@ -120,41 +165,31 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n_cells, tau = 10, 1.0 / 32
-    from oracle import slab, space
-    V = synth.jittered_vertices(n_cells, 3)
-    rho = synth.block_coefficient(n_cells, 3, blocks=2)
-    g = space.Grid(n_cells, 3, 2, V)
-    prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, rho), "heat", "dg", 2, tau)
-    X = g.node_coords()
-    dofs = prob.nt * int((~prob.bmask).sum())
-    u_prev = np.zeros(g.n_nodes)
-
-    def step(n):
-        nonlocal u_prev
-        f = np.stack([synth.heat_sine_source(X, tau * (n + th)) for th in prob.sys.tw.nodes])
-        u = prob.solve(prob.rhs(f, None, u_prev))
-        u_prev = u[-1]
-
-    for n in range(args.warmup):
-        step(n)
-    t0 = time.perf_counter()
-    for n in range(args.steps):
-        step(args.warmup + n)
-    dt = time.perf_counter() - t0
-    value = dofs * args.steps / dt
-    sample = (f"oracle slab marching (sparse LU factorised in the warm-up, one triangular solve per slab) on "
-              f"the same workload family at 10^3 cells (Q2, dG(2), jitter 0.15h, 2^3 coefficient blocks), "
-              f"{dofs} DoFs per slab")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+    n_cells = ORACLE_SAMPLE_CELLS
+    r = oracle_c2_run(n_cells, args.steps, args.warmup)
+    one = oracle_subprocess(n_cells, 2, 1, 1)
+    cores = os.cpu_count()
+    wl_name = workload(n_cells)["name"]
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["solve_s"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload(args.n_cells)["name"], "cells": args.n_cells ** 3, "p": 2, "time": "dG(2)",
-                       "rtol": 1e-8, "oracle_sample": "10^3 cells of the same family, direct solves (see cpu_baseline)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": wl_name, "sample_of": workload(args.n_cells)["name"], "cells": n_cells ** 3,
+                       "p": 2, "time": "dG(2)", "rtol": 1e-8, "dofs_per_step": r["dofs_per_slab"]},
+            "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "value_1_thread": one["value"], "sample": oracle_sample_text(r, n_cells)},
+            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_oracle_full(args):
+    """The oracle on the full headline grid (32^3 cells), all host threads and one thread."""
+    out = {}
+    for threads in (os.cpu_count(), 1):
+        out[f"threads_{threads}"] = oracle_subprocess(args.n_cells, 2, 1, threads)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "impl": "oracle", "config": {"workload": workload(args.n_cells)["name"]},
+                      "runs": out}), flush=True)
     return 0
 
 
@@ -408,17 +443,9 @@ def run_ours(args):
                      "peak_source": "FP64 1.25 TFLOP/s nominal (GB300 table; no measured FP64 peak)",
                      "avg_launch_ms": apply_ms}
         nb = nq ** 3
-        # the stored cell blocks (planes with rows padded to 4 entries; FP8: one FP32 scale per plane)
-        plane_entries = nt * nb * ((nb + 3) // 4 * 4)
-        cell_bytes = ((plane_entries + 4 * nt + 15) // 16 * 16 if inv_bytes == 1 else
-                      (plane_entries + 7) // 8 * 8 * inv_bytes)
-        asm_bytes = cells * cell_bytes + 2 * 4 * n
-        asm_roof = {"kernel": "asm_apply_tma_kernel<3,3,3,float,bf16> (finest-level additive Schwarz, TMA-fed)",
-                    "bound": "hbm", "achieved": asm_bytes / (asm_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": asm_bytes / (asm_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                    "traffic": read_traffic(f"asm_{args.inverse}") if args.inverse in ("bf16", "fp8") else None,
-                    "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                    "algorithmic_bytes": asm_bytes, "inverse_storage": args.inverse, "avg_launch_ms": asm_ms}
+        asm_roof = smoother_roofline(args.inverse, cells, nt, nb, n, asm_ms, peaks,
+                                     f"asm_apply_tma_kernel<3,3,3,float,{args.inverse}> (finest-level additive Schwarz, "
+                                     "TMA-fed)", traffic_key=f"asm_{args.inverse}" if args.inverse in ("bf16", "fp8") else None)
         if args.plain:
             roof = roof_fp64
             extra["asm_finest"] = asm_roof
@@ -442,11 +469,19 @@ def run_ours(args):
                 "frac": flops / (f32_ms * 1e-3) / f32_peak, "avg_launch_ms": f32_ms,
                 "note": "fraction of the FP32-pipe peak; the kernel is bound by its shared-memory transposes"}
         extra["vcycle_ms"] = vc_ms
+        extra["apply_gdofs"] = apply_gdofs(stmg, ctx, dofs_per_step, df=not args.plain)
+        if not args.skip_compare and not args.plain:
+            mixed_kw = dict(vcycle_precision=stmg.FP32, inverse_precision=inv_prec, coarse_max_dofs=args.coarse_max_dofs,
+                            asm_weighting=args.asm_weighting, outer_relax=args.outer_relax)
+            extra["error_vs_fp64"] = {sp_["name"]: slab_error_vs_fp64(stmg, torch, dev, sp_, mixed_kw)
+                                      for sp_ in accuracy_specs(stmg)}
+            extra["error_vs_fp64"]["definition"] = ("relative L2 difference of the mixed solution (rtol 1e-8) from "
+                                                    "the plain FP64 solver's solution of the same slab at rtol 1e-12")
         if not args.skip_cpu:
-            v, d, dt = oracle_sample(10, 4, wl["tau"])
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"oracle marching of 4 slabs (assembly + sparse LU + 4 solves, {dt:.1f} s) of the same "
-                             f"workload family at 10^3 cells ({d} DoFs per slab)"}
+            r_all = oracle_subprocess(ORACLE_SAMPLE_CELLS, 4, 1, os.cpu_count())
+            r_one = oracle_subprocess(ORACLE_SAMPLE_CELLS, 2, 1, 1)
+            cpu = {"value": r_all["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "value_1_thread": r_one["value"], "sample": oracle_sample_text(r_all, ORACLE_SAMPLE_CELLS)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.plain else ("f64+df32+f32+bf16" if use_net else "f64+df32+f32"),
@@ -678,6 +713,113 @@ def run_c4(args):
     return 0
 
 
+def run_c3(args):
+    """Wave workload: first-order-in-time acoustic wave condensed to the displacement, Q3 on 24^3 cells
+    with interior vertices jittered by U[-0.15h, 0.15h], cGP(2), tau = 1/64 (64 slabs), rho = c^2 = 1
+    below z = 0.5 and 16 above (c = 1 / 4), Gaussian pulse u0 (sigma 0.05 at (0.5, 0.5, 0.25)), v0 = 0,
+    f = 0.  One step = one slab: right-hand side, previous-slab guess, FGMRES with the FP32 V-cycle to
+    rtol 1e-8, velocity update."""
+    import torch
+    import paper_2408_04372_gb300 as stmg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N, p, k, n_slabs = 24, 3, 2, 64
+    tau = 1.0 / n_slabs
+    V = synth.jittered_vertices(N, 3)
+    rho = synth.layer_coefficient(N, 3, 1.0, 16.0)
+    inv_prec = {"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64, "fp8": stmg.FP8}[args.inverse]
+    t0 = time.perf_counter()
+    ctx = stmg.Context(3, N, p, k, tau, pde=stmg.WAVE, scheme=stmg.CGP, vertices=V, coeff=rho,
+                       vcycle_precision=stmg.FP32, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
+                       coarse_max_dofs=args.coarse_max_dofs, asm_weighting=args.asm_weighting,
+                       outer_relax=args.outer_relax)
+    setup_s = time.perf_counter() - t0
+    nt, nn = ctx.nt, ctx.n_nodes
+    n = nt * nn
+    X = ctx.node_coords()
+    bnd = np.any((X < 1e-12) | (X > 1.0 - 1e-12), axis=1)
+    u0 = synth.wave_pulse(X)
+    u0[bnd] = 0.0
+    dofs = nt * (N * p - 1) ** 3
+    zf = torch.zeros(n, dtype=torch.float64, device=dev)
+    zn = torch.zeros(nn, dtype=torch.float64, device=dev)
+    rhs = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    v = torch.empty(n, dtype=torch.float64, device=dev)
+    u_prev = torch.from_numpy(u0).to(dev)
+    v_prev = torch.zeros(nn, dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.rhs(zf, rhs, f0=zn, u0=u_prev, v0=v_prev)
+        ctx.guess_previous(u_prev, u)
+        st = ctx.solve(rhs, u)
+        if not st["converged"]:
+            raise RuntimeError(f"wave slab did not converge: {st}")
+        ctx.wave_velocity(u, u_prev, v_prev, v)
+        u_prev.copy_(u[(nt - 1) * nn:])
+        v_prev.copy_(v[(nt - 1) * nn:])
+        return st
+
+    steps = min(args.steps, n_slabs - args.warmup)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    its, relaxed = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            st = step()
+            its.append(st["iterations"])
+            relaxed.append(st["relaxed_iterations"])
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    peaks = read_peaks()
+    asm_ms = ctx.time_kernel(stmg.KERNEL_ASM, 0, stmg.FP32, reps=20)
+    cells, nq = N ** 3, p + 1
+    roof = smoother_roofline(args.inverse, cells, nt, nq ** 3, n, asm_ms, peaks,
+                             f"asm_apply_tma_kernel<3,4,2,float,{args.inverse}> (finest-level additive Schwarz)")
+    ga = apply_gdofs(stmg, ctx, dofs)
+    flops = (12 * nq ** 4 + (16 + 8 * nt) * nq ** 3) * cells * nt
+    df_peak = 152 * 128 * 2.07e9 / 15 * 2
+    f32_peak = 152 * 128 * 2 * 2.07e9
+    kernels = {
+        "apply_gdofs": ga,
+        "apply_df_finest": {"bound": "alu", "achieved": flops / (ga["df32"]["median_ms"] * 1e-3) / 1e12,
+                            "peak": df_peak / 1e12, "unit": "TFLOP/s",
+                            "frac": flops / (ga["df32"]["median_ms"] * 1e-3) / df_peak},
+        "apply_fp32_finest": {"bound": "alu", "achieved": flops / (ga["fp32"]["median_ms"] * 1e-3) / 1e12,
+                              "peak": f32_peak / 1e12, "unit": "TFLOP/s",
+                              "frac": flops / (ga["fp32"]["median_ms"] * 1e-3) / f32_peak},
+        "vcycle_ms": ctx.time_kernel(stmg.KERNEL_VCYCLE, 0, stmg.FP32, reps=10)}
+    levels = [ctx.level_info(l) for l in range(ctx.n_levels)]
+    ctx.close()
+    err = None
+    if not args.skip_compare:
+        mixed_kw = dict(vcycle_precision=stmg.FP32, inverse_precision=inv_prec, coarse_max_dofs=args.coarse_max_dofs,
+                        asm_weighting=args.asm_weighting, outer_relax=args.outer_relax)
+        err = slab_error_vs_fp64(stmg, torch, dev, accuracy_specs(stmg)[2], mixed_kw)
+    line = {"metric": "space-time DoFs/s solved to 1e-8 rel. residual (mixed FP32 V-cycle in FP64 FGMRES)",
+            "value": dofs * steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms / steps, "higher_is_better": True, "dtype": "f64+df32+f32", "data": "synthetic",
+            "config": {"workload": C3_NAME, "cells": cells, "p": p, "time": "cGP(2)", "dofs_per_step": dofs,
+                       "slabs_timed": f"{args.warmup}..{args.warmup + steps - 1}", "rtol": 1e-8,
+                       "levels": [f"Q{l['p']} {l['n_cells']}^3 cGP({l['k']})" for l in levels],
+                       "inverse_storage": args.inverse, "setup_s": setup_s,
+                       "fgmres_iterations_mean": float(np.mean(its)),
+                       "relaxed_iterations_mean": float(np.mean(relaxed)),
+                       "schwarz_sum": "weighted by inverse node multiplicity" if args.asm_weighting else
+                                      "eq. vanka0 as printed (unweighted)"},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "kernels": kernels,
+            "error_vs_fp64": err}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_shm(args):
     """Structural-health-monitoring-like wave problem (Section 4.3), reduced: [-1, 1]^3 on N^3 Cartesian
     cells (N a multiple of 5), Q2, cGP(2), highly heterogeneous coefficient (layers 1 / 9 / 16 times
@@ -745,6 +887,101 @@ def run_shm(args):
     return 0
 
 
+def smoother_roofline(inverse, cells, nt, nb, n, asm_ms, peaks, kernel_name, traffic_key=None):
+    """Finest-level Schwarz sweep against the measured copy bandwidth.  Algorithmic bytes: the
+    inverse entries themselves, n_b^2 per time plane and cell (no padding), plus two FP32 vectors
+    (residual in, correction out); the stored block with its padding is reported apart."""
+    inv_bytes = {"fp32": 4, "bf16": 2, "fp64": 8, "fp8": 1}[inverse]
+    alg = cells * nt * nb * nb * inv_bytes + 2 * 4 * n
+    plane_entries = nt * nb * ((nb + 3) // 4 * 4)
+    cell_bytes = ((plane_entries + 4 * nt + 15) // 16 * 16 if inv_bytes == 1 else
+                  (plane_entries + 7) // 8 * 8 * inv_bytes)
+    stored = cells * cell_bytes + 2 * 4 * n
+    gbs = alg / (asm_ms * 1e-3) / 1e9
+    return {"kernel": kernel_name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"],
+            "traffic": read_traffic(traffic_key) if traffic_key else None,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured",
+            "algorithmic_bytes": alg, "stored_bytes_with_padding": stored, "inverse_storage": inverse,
+            "avg_launch_ms": asm_ms}
+
+
+def median_launch_ms(ctx, kind, level, prec, warm=10, reps=100):
+    """Median of `reps` single-launch CUDA-event timings after `warm` launches (each timing brackets one
+    launch on the context's stream)."""
+    for _ in range(warm):
+        ctx.time_kernel(kind, level, prec, reps=1)
+    return float(np.median([ctx.time_kernel(kind, level, prec, reps=1) for _ in range(reps)]))
+
+
+def apply_gdofs(stmg, ctx, dofs, df=True):
+    """Operator apply throughput on the finest level: N_t x interior nodes / median launch time."""
+    out = {}
+    precs = [("fp64", stmg.FP64), ("fp32", stmg.FP32)] + ([("df32", stmg.DF32)] if df else [])
+    for name, prec in precs:
+        ms = median_launch_ms(ctx, stmg.KERNEL_APPLY, 0, prec)
+        out[name] = {"gdofs": dofs / (ms * 1e-3) / 1e9, "median_ms": ms}
+    out["definition"] = "N_t x interior nodes / median of 100 single-launch CUDA-event timings after 10 warm-up"
+    return out
+
+
+def slab_error_vs_fp64(stmg, torch, dev, spec, mixed_kw):
+    """Relative L2 difference between the mixed solver's slab solution (rtol 1e-8, the bench's options)
+    and the plain FP64 solver's solution of the same slab from the same guess at rtol 1e-12."""
+    dim, N, p, k, pde, scheme, tau, V, rho, slab_index = (spec[x] for x in (
+        "dim", "N", "p", "k", "pde", "scheme", "tau", "vertices", "rho", "slab"))
+    sols = {}
+    for name, kw in (("mixed", dict(mixed_kw, rtol=1e-8)),
+                     ("fp64", dict(vcycle_precision=stmg.FP64, rtol=1e-12, coarse_max_dofs=mixed_kw.get("coarse_max_dofs", 0),
+                                   asm_weighting=mixed_kw.get("asm_weighting", 0)))):
+        ctx = stmg.Context(dim, N, p, k, tau, pde=pde, scheme=scheme, vertices=V, coeff=rho, restart=30, max_it=400, **kw)
+        nt, nn = ctx.nt, ctx.n_nodes
+        X = ctx.node_coords()
+        bnd = np.any((X < 1e-12) | (X > 1.0 - 1e-12), axis=1)
+        rhs = torch.empty(nt * nn, dtype=torch.float64, device=dev)
+        u = torch.empty_like(rhs)
+        t0 = tau * slab_index
+        if pde == stmg.HEAT:
+            tn = radau_nodes(k) if scheme == stmg.DG else np.linspace(0.0, 1.0, k + 1)[1:]
+            f = np.stack([synth.heat_sine_source(X, t0 + tau * th) for th in tn])
+            u0 = synth.heat_sine_solution(X, t0)
+            u0[bnd] = 0.0
+            u0d = torch.from_numpy(u0).to(dev)
+            ctx.rhs(torch.from_numpy(f.reshape(-1)).to(dev), rhs, u0=u0d)
+        else:
+            u0 = synth.wave_pulse(X)
+            u0[bnd] = 0.0
+            u0d = torch.from_numpy(u0).to(dev)
+            ctx.rhs(torch.zeros(nt * nn, dtype=torch.float64, device=dev), rhs,
+                    f0=torch.zeros(nn, dtype=torch.float64, device=dev), u0=u0d,
+                    v0=torch.zeros(nn, dtype=torch.float64, device=dev))
+        ctx.guess_previous(u0d, u)
+        st = ctx.solve(rhs, u)
+        if not st["converged"]:
+            raise RuntimeError(f"{spec['name']} {name} did not converge: {st}")
+        sols[name] = (u.clone(), st)
+        ctx.close()
+    um, ur = sols["mixed"][0], sols["fp64"][0]
+    return {"rel_l2_error": float((um - ur).norm() / ur.norm()), "mixed_iterations": sols["mixed"][1]["iterations"],
+            "fp64_iterations_rtol_1e-12": sols["fp64"][1]["iterations"], "slab": slab_index}
+
+
+def accuracy_specs(stmg):
+    """One slab of each of the three solved configurations: 2D heat (Q2 16^2, dG(1)), the headline 3D
+    heat workload, and the 3D wave workload (Q3 24^3 jittered, cGP(2), two layers, Gaussian pulse)."""
+    return [
+        dict(name="c1_heat2d_q2_dg1_16sq", dim=2, N=16, p=2, k=1, pde=stmg.HEAT, scheme=stmg.DG, tau=1 / 16,
+             vertices=None, rho=None, slab=1),
+        dict(name=workload()["name"], dim=3, N=32, p=2, k=2, pde=stmg.HEAT, scheme=stmg.DG, tau=1 / 32,
+             vertices=synth.jittered_vertices(32, 3), rho=synth.block_coefficient(32, 3, blocks=4), slab=3),
+        dict(name=C3_NAME, dim=3, N=24, p=3, k=2, pde=stmg.WAVE, scheme=stmg.CGP, tau=1 / 64,
+             vertices=synth.jittered_vertices(24, 3), rho=synth.layer_coefficient(24, 3, 1.0, 16.0), slab=0),
+    ]
+
+
+C3_NAME = "wave3d_q3_cgp2_24cubed_jitter0.15_layers1_16_pulse"
+
+
 def aggregate_replicas(ms_local, dofs_per_step, steps, world, device):
     """Replicas only: slowest rank's time, every rank's DoFs.  Returns (max ms, whole-job DoF/s)."""
     import torch
@@ -809,7 +1046,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-compare", action="store_true", help="skip the no-network and plain-FP64 comparison arms")
     ap.add_argument("--net", action="store_true", help="learned guess on this workload too (trained on slabs 0-15)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "shm"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "shm", "oracle_c2"])
+    ap.add_argument("--oracle-run", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64", "fp8"],
                     help="storage of the Schwarz inverses in the mixed solver")
@@ -827,6 +1065,9 @@ def main():
     ap.add_argument("--coarse-max-dofs", type=int, default=1500,
                     help="hierarchy ends at the first coarser level with at most this many unknowns (0: full)")
     args = ap.parse_args()
+    if args.oracle_run:
+        print(json.dumps(oracle_c2_run(args.oracle_run, args.steps, args.warmup)), flush=True)
+        return 0
     if args.only_kernel:
         return run_kernel_only(args)
     if args.warmup < 3:
@@ -837,6 +1078,10 @@ def main():
         return run_learned_c5(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "c3":
+        return run_c3(args)
+    if args.workload == "oracle_c2":
+        return run_oracle_full(args)
     if args.workload == "shm":
         return run_shm(args)
     return run_ours(args)

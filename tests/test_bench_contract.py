@@ -1,5 +1,5 @@
 """The bench's reference arm (the oracle on the host, no GPU): one JSON line with the contract's keys,
-on the GPU arm's workload name."""
+labelled with the sample of the headline workload that actually ran."""
 import json
 import os
 import subprocess
@@ -19,7 +19,9 @@ def test_reference_arm_prints_one_contract_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "heat3d_q2_dg2_32cubed_jitter0.15_rho4blocks"
+    assert d["config"]["workload"] == "heat3d_q2_dg2_16cubed_jitter0.15_rho4blocks"
+    assert d["config"]["sample_of"] == "heat3d_q2_dg2_32cubed_jitter0.15_rho4blocks"
+    assert d["cpu_baseline"]["value_1_thread"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 

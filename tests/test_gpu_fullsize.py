@@ -64,6 +64,45 @@ def test_full_size_apply_on_sampled_rows(env, name):
     ctx.close()
 
 
+def _cartesian_gauss_points(N, dim, p):
+    """Physical Gauss points of an N^dim Cartesian grid of [0, 1]^dim, [cell][point], x fastest."""
+    xq = np.polynomial.legendre.leggauss(p + 1)[0] * 0.5 + 0.5
+    ql = np.indices((p + 1,) * dim).reshape(dim, -1)[::-1].T
+    cells = np.indices((N,) * dim).reshape(dim, -1)[::-1].T
+    return (cells[:, None, :] + xq[ql][None, :, :]) / N
+
+
+def test_c4_full_size_apply_on_sampled_rows_with_qpoint_coefficient(env):
+    """Q4 on 64^3 Cartesian cells, dG(3), smooth coefficient given at every Gauss point (66.3M unknowns
+    per slab): sampled rows of S x against the oracle's element matrices, FP64 and FP32."""
+    torch, stmg = env
+    dim, N, p, k, tau = 3, 64, 4, 3, 1 / 8
+    a, phi = synth.smooth_coefficient_params(dim)
+    g = space.Grid(N, dim, p, synth.cartesian_vertices(N, dim))
+    pts = _cartesian_gauss_points(N, dim, p)
+    # the point order is the oracle's own (checked on a 4^3 grid of the same degree)
+    small = space.Grid(4, dim, p, synth.cartesian_vertices(4, dim))
+    assert np.allclose(small.quad_points_phys(), _cartesian_gauss_points(4, dim, p), atol=1e-14)
+    rq = synth.smooth_coefficient_at(pts, a, phi)
+    ctx = stmg.Context(dim, N, p, k, tau, vertices=None, coeff=rq.reshape(-1), coeff_mode=stmg.COEFF_PER_QPOINT,
+                       smoother_kind=stmg.SMOOTHER_FD, omega=[0.2] * 16)
+    nt, nn = ctx.nt, ctx.n_nodes
+    assert nt * (N * p - 1) ** 3 == 66325500
+    x = synth.random_vector((nt, nn), seed=23)
+    samples = _samples(nt, nn, 40, seed=24)
+    samples += [(0, 0), (nt - 1, nn - 1), (nt - 1, g.nn1 * g.nn1 + g.nn1 + 1), (1, nn // 2)]
+    ref = slab.sampled_rows(g, rq, "heat", "dg", k, tau, x, samples)
+    for dt, tol in ((torch.float64, 1e-10), (torch.float32, 2e-5)):
+        xd = torch.from_numpy(x.reshape(-1)).to("cuda", dt)
+        yd = torch.empty_like(xd)
+        ctx.apply(xd, yd)
+        y = yd.cpu().numpy().astype(np.float64).reshape(nt, nn)
+        got = np.array([y[t, n_] for t, n_ in samples])
+        assert np.abs(got - ref).max() < tol * np.abs(ref).max(), dt
+        del xd, yd
+    ctx.close()
+
+
 def test_full_size_bench_slab_solve_meets_rtol_in_oracle_residual(env):
     """Bench workload, one slab from the previous-slab guess: the oracle's assembled S confirms rtol."""
     torch, stmg = env
@@ -148,14 +187,35 @@ def test_c1_heat2d_marching_matches_oracle(env):
     assert slab.l2l2_error(prob, sols, synth.heat_sine_solution, np.zeros(prob.grid.n_nodes)) < 5e-3
 
 
-def test_c3_wave_marching_matches_oracle_on_reduced_grid(env):
-    """Config 3 family (Q3, cGP(2) wave, two layers, jittered) on 6^3 cells, 8 slabs, with velocities."""
+def _oracle_iterative_solve(H, rtol=1e-13):
+    """Slab solve by the oracle's FGMRES with its V-cycle (for grids whose direct LU is too slow);
+    checks that the oracle reached rtol."""
+    prob = H.levels[0].prob
+
+    def solve(rhs):
+        b = rhs.reshape(-1)
+        res = mg.fgmres(lambda v: prob.S @ v, H.vcycle, b, np.zeros_like(b), rtol=rtol, max_it=400)
+        assert res.rel_residual <= rtol, res.rel_residual
+        return res.x.reshape(prob.nt, -1)
+    return solve
+
+
+@pytest.mark.parametrize("N", [6, 12])
+def test_c3_wave_marching_matches_oracle_on_reduced_grid(env, N):
+    """Config 3 family (Q3, cGP(2) wave, two layers, jittered) on 6^3 (direct solves) and 12^3 cells
+    (oracle FGMRES with its V-cycle to 1e-13), 8 slabs, with velocities."""
     torch, stmg = env
-    dim, N, p, k, tau, slabs = 3, 6, 3, 2, 1 / 64, 8
+    dim, p, k, tau, slabs = 3, 3, 2, 1 / 64, 8
     V = synth.jittered_vertices(N, dim)
     rho = synth.layer_coefficient(N, dim, 1.0, 16.0)
-    g = space.Grid(N, dim, p, V)
-    prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, rho), "wave", "cgp", k, tau)
+    if N <= 6:
+        g = space.Grid(N, dim, p, V)
+        prob = slab.SlabProblem(g, space.rho_qp_from_cells(g, rho), "wave", "cgp", k, tau)
+    else:
+        H = mg.Hierarchy(dim, N, p, k, "wave", "cgp", tau, V, rho_cell=rho, weighted=True, omegas=[1.0] * 16)
+        prob = H.levels[0].prob
+        g = prob.grid
+        prob.solve = _oracle_iterative_solve(H)
     X = g.node_coords()
     u_init = synth.wave_pulse(X)
     u_init[prob.bmask] = 0.0
