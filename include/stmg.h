@@ -62,7 +62,16 @@ enum { STMG_COEFF_PER_CELL = 0, STMG_COEFF_PER_QPOINT = 1 };
  * significand bits), FP64 output; only for the finest-level operator (outer_apply, stmg_apply). */
 /* STMG_FP8: e4m3 with one FP32 scale per stored plane (Schwarz inverses only, FP32 V-cycle). */
 enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3, STMG_DF32 = 4, STMG_FP8 = 5 };   /* 0 in an option = default */
-enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2 };
+/* Local solvers of the additive Schwarz smoother (eqs. vanka0, vanka), all exact up to rounding:
+ *   DENSE: per cell and time mode the inverse plane (A_K + lambda_m M_K)^-1 (N_t planes per cell);
+ *   FD:    fast diagonalisation on 3D Cartesian cells (separable 1D eigenvectors; exact for a
+ *          coefficient constant on the cell patch, a cell-mean approximation otherwise);
+ *   EIG:   per cell the generalized eigendecomposition A_K Q = M_K Q diag(mu), Q^T M_K Q = I, so that
+ *          (A_K + lambda_m M_K)^-1 = Q diag(1 / (mu + lambda_m)) Q^T for every time mode: one matrix Q
+ *          and (p+1)^dim eigenvalues per cell instead of N_t planes (inverse_precision FP64, FP32 or
+ *          BF16 for Q; FP8 stores BF16); any grid, p <= 3 in 3D, p <= 4 in 2D.
+ *   AUTO:  FD on 3D Cartesian grids where it is exact (or p = 4), DENSE elsewhere. */
+enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2, STMG_SMOOTHER_EIG = 3 };
 
 /* Structured grid of n_cells^dim cells.  vertices: HOST array of
  * (n_cells+1)^dim x dim coordinates (lexicographic, x fastest), copied at
@@ -108,7 +117,7 @@ typedef struct {
   int nu_post;             /* post-smoothing sweeps nu_2 [1] */
   int vcycle_precision;    /* STMG_FP32 (mixed) or STMG_FP64 (plain) [FP32] */
   int inverse_precision;   /* storage of dense local inverses: FP64/FP32/BF16/FP8 [same as V-cycle] */
-  int smoother_kind;       /* AUTO, DENSE or FD [AUTO: FD on Cartesian grids with constant rho, else DENSE] */
+  int smoother_kind;       /* AUTO, DENSE, FD or EIG (see above) [AUTO] */
   const double* omega;     /* host, may be NULL */
   int fgmres_restart;      /* [30] */
   double rtol;             /* relative residual target of stmg_solve [1e-8] */

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["tables.cpp", "setup.cu", "apply.cu", "apply_df.cu", "apply_dfd.cu", "couple.cu", "asm.cu", "transfer.cu", "vec.cu", "net.cu", "fd.cu", "stmg.cu"]
+SOURCES = ["tables.cpp", "setup.cu", "apply.cu", "apply_df.cu", "apply_dfd.cu", "couple.cu", "asm.cu", "eig.cu", "transfer.cu", "vec.cu", "net.cu", "fd.cu", "stmg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", INCLUDE]

@@ -1,0 +1,505 @@
+// Space-time additive Schwarz local solves (eqs. vanka0, vanka) through a generalized eigen-
+// decomposition in space, per cell.
+//
+// The block of space-time cell T is L_T = TA (x) A_K + TM (x) M_K, with A_K, M_K the global
+// stiffness and mass matrices restricted to the unconstrained nodes of spatial cell K.  With the
+// M_K-orthonormal eigenvectors of the symmetric pencil, A_K Q = M_K Q diag(mu), Q^T M_K Q = I, and
+// the time diagonalisation TA^-1 TM = V diag(lambda) V^-1,
+//     L_T^-1 = (V (x) Q) diag_{m,j} 1 / (lambda_m + mu_j) (V^-1 TA^-1 (x) Q^T),
+// exact up to rounding: (A_K + lambda M_K)^-1 = Q diag(1 / (mu + lambda)) Q^T for every time mode.
+// A cell therefore stores one (p+1)^dim x (p+1)^dim matrix Q and (p+1)^dim eigenvalues mu instead of
+// N_t inverse planes: N_t times fewer bytes for the HBM-bound sweep, at twice the multiply-adds
+// (Q^T on the way in, Q on the way out), which the CUDA cores have to spare.
+//
+// eig_setup_kernel (FP64, one CTA per cell): local matrices, Cholesky M_K = L L^T,
+// C = L^-1 A_K L^-T, cyclic Jacobi on C (parallel round-robin ordering, rotations by Golub and
+// Van Loan's symmetric Schur decomposition) until the off-diagonal part is below 1e-15 of C,
+// Q = L^-T U.  Store per cell: Q[a][j] row-major over the local nodes a (rows and columns of
+// constrained nodes zero), NBP = NB rounded up to 4 columns, then NBP FP32 eigenvalues (1 in the
+// padding), the block padded to 16 bytes.
+//
+// eig_apply_kernel: TMA-fed like the plane smoother -- each persistent CTA walks groups of
+// consecutive cells whose blocks arrive by one bulk copy into a ring of two shared-memory stages
+// (bounded mbarrier waits); per cell and slab: modal residual (V^-1 TA^-1 in time), y = Q^T s (a
+// thread per eigenvector), z_hat = y / (lambda + mu) (complex for conjugate time modes), z = Q z_hat
+// (a thread per node), back to the time basis (V), weighted by the node's inverse cell count when the
+// weighted sum is selected, and added with atomics.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "local_mats.cuh"
+#include "tc05.cuh"
+
+namespace stmg {
+
+namespace {
+
+__host__ __device__ constexpr int eig_nbp(int nb) { return (nb + 3) / 4 * 4; }
+__host__ __device__ constexpr int64_t eig_cell_bytes_c(int nb, int esz) {
+  return ((int64_t)nb * eig_nbp(nb) * esz + (int64_t)eig_nbp(nb) * 4 + 15) / 16 * 16;
+}
+
+constexpr int kEigThreads = 256;
+constexpr int kMaxSweeps = 24;
+
+__device__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(kEigThreads)
+eig_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, unsigned char* __restrict__ out, int prec) {
+  constexpr int NB = DIM == 3 ? N * N * N : N * N;
+  constexpr int NBP = eig_nbp(NB);
+  constexpr int NPAIR = (NB + 1) / 2;
+  extern __shared__ __align__(16) double sm[];
+  double* A = sm;            // local stiffness -> C -> diagonalised C
+  double* M = A + NB * NB;   // local mass -> Cholesky factor L (lower)
+  double* U = M + NB * NB;   // scratch -> eigenvectors -> Q
+  __shared__ int s_free[NB], s_loc[NB], s_m;
+  __shared__ int s_p[NPAIR], s_q[NPAIR];
+  __shared__ double s_c[NPAIR], s_s[NPAIR];
+  __shared__ double s_red[kEigThreads / 32];
+  __shared__ int s_done;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int64_t cell = blockIdx.x;
+  const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
+  const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+  assemble_local<DIM, N>(g, geo, lt, cx, cy, cz, A, M);
+  if (tid == 0) {
+    int m = 0;
+    for (int a = 0; a < NB; ++a) {
+      const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
+      bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+      if (DIM == 3) bnd = bnd || on_boundary(cz * g.p + a / (N * N), g.nn1);
+      s_loc[a] = bnd ? -1 : m;
+      if (!bnd) s_free[m++] = a;
+    }
+    s_m = m;
+  }
+  __syncthreads();
+  const int m = s_m;
+  // compress A and M to the unconstrained nodes (row stride m)
+  for (int i = tid; i < m * m; i += nth) U[i] = A[s_free[i / m] * NB + s_free[i % m]];
+  __syncthreads();
+  for (int i = tid; i < m * m; i += nth) A[i] = U[i];
+  __syncthreads();
+  for (int i = tid; i < m * m; i += nth) U[i] = M[s_free[i / m] * NB + s_free[i % m]];
+  __syncthreads();
+  for (int i = tid; i < m * m; i += nth) M[i] = U[i];
+  __syncthreads();
+  // Cholesky M = L L^T (right-looking, lower triangle)
+  for (int k = 0; k < m; ++k) {
+    if (tid == 0) M[k * m + k] = sqrt(M[k * m + k]);
+    __syncthreads();
+    for (int i = k + 1 + tid; i < m; i += nth) M[i * m + k] /= M[k * m + k];
+    __syncthreads();
+    const int rem = m - k - 1;
+    for (int idx = tid; idx < rem * rem; idx += nth) {
+      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+      if (j <= i) M[i * m + j] -= M[i * m + k] * M[j * m + k];
+    }
+    __syncthreads();
+  }
+  // X = L^-1 A (columns in place), then C = L^-1 X^T
+  for (int c = tid; c < m; c += nth)
+    for (int i = 0; i < m; ++i) {
+      double x = A[i * m + c];
+      for (int l = 0; l < i; ++l) x -= M[i * m + l] * A[l * m + c];
+      A[i * m + c] = x / M[i * m + i];
+    }
+  __syncthreads();
+  for (int i = tid; i < m * m; i += nth) U[i] = A[(i % m) * m + i / m];
+  __syncthreads();
+  for (int c = tid; c < m; c += nth)
+    for (int i = 0; i < m; ++i) {
+      double x = U[i * m + c];
+      for (int l = 0; l < i; ++l) x -= M[i * m + l] * U[l * m + c];
+      U[i * m + c] = x / M[i * m + i];
+    }
+  __syncthreads();
+  for (int i = tid; i < m * m; i += nth) A[i] = 0.5 * (U[i] + U[(i % m) * m + i / m]);
+  __syncthreads();
+  for (int i = tid; i < m * m; i += nth) U[i] = (i / m == i % m) ? 1.0 : 0.0;
+  __syncthreads();
+  // cyclic Jacobi, round-robin pairs: position 0 fixed, the others rotate; an odd m adds a dummy
+  const int me = m + (m & 1), npairs = me / 2;
+  for (int sweep = 0; sweep < kMaxSweeps && m > 1; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = tid; i < m * m; i += nth) {
+      const double v = A[i] * A[i];
+      tot += v;
+      if (i / m != i % m) off += v;
+    }
+    off = block_sum(off, s_red);
+    tot = block_sum(tot, s_red);
+    if (tid == 0) s_done = off <= 1e-30 * tot;
+    __syncthreads();
+    if (s_done) break;
+    for (int r = 0; r < me - 1; ++r) {
+      if (tid < npairs) {
+        auto pos = [&](int k) { return k == 0 ? 0 : 1 + (k - 1 + r) % (me - 1); };
+        int p = pos(tid), q = pos(me - 1 - tid);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double app = A[p * m + p], aqq = A[q * m + q], apq = A[p * m + q];
+          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        } else {
+          p = -1;
+        }
+        s_p[tid] = p; s_q[tid] = q; s_c[tid] = c; s_s[tid] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * m; idx += nth) {  // rows p, q
+        const int pr = idx / m, k = idx % m, p = s_p[pr];
+        if (p < 0) continue;
+        const int q = s_q[pr];
+        const double c = s_c[pr], s = s_s[pr], ap = A[p * m + k], aq = A[q * m + k];
+        A[p * m + k] = c * ap - s * aq;
+        A[q * m + k] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * m; idx += nth) {  // columns p, q of A and of U
+        const int pr = idx / m, k = idx % m, p = s_p[pr];
+        if (p < 0) continue;
+        const int q = s_q[pr];
+        const double c = s_c[pr], s = s_s[pr];
+        const double ap = A[k * m + p], aq = A[k * m + q];
+        A[k * m + p] = c * ap - s * aq;
+        A[k * m + q] = s * ap + c * aq;
+        const double up = U[k * m + p], uq = U[k * m + q];
+        U[k * m + p] = c * up - s * uq;
+        U[k * m + q] = s * up + c * uq;
+      }
+      __syncthreads();
+    }
+  }
+  // Q = L^-T U (back substitution, columns in place)
+  for (int c = tid; c < m; c += nth)
+    for (int i = m - 1; i >= 0; --i) {
+      double x = U[i * m + c];
+      for (int l = i + 1; l < m; ++l) x -= M[l * m + i] * U[l * m + c];
+      U[i * m + c] = x / M[i * m + i];
+    }
+  __syncthreads();
+  const int esz = prec == 0 ? 8 : prec == 1 ? 4 : 2;
+  unsigned char* blk = out + cell * eig_cell_bytes_c(NB, esz);
+  for (int idx = tid; idx < NB * NBP; idx += nth) {
+    const int a = idx / NBP, j = idx % NBP, ia = s_loc[a];
+    const double v = (ia >= 0 && j < m) ? U[ia * m + j] : 0.0;
+    if (prec == 0) reinterpret_cast<double*>(blk)[idx] = v;
+    else if (prec == 1) reinterpret_cast<float*>(blk)[idx] = (float)v;
+    else reinterpret_cast<__nv_bfloat16*>(blk)[idx] = __float2bfloat16((float)v);
+  }
+  float* mu = reinterpret_cast<float*>(blk + (int64_t)NB * NBP * esz);
+  for (int j = tid; j < NBP; j += nth) mu[j] = j < m ? (float)A[j * m + j] : 1.0f;
+}
+
+// ---- apply ----
+template <typename TI> __device__ __forceinline__ float ld_f(const TI* p);
+template <> __device__ __forceinline__ float ld_f<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ld_f<double>(const double* p) { return (float)*p; }
+template <> __device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <typename T, typename TI> __device__ __forceinline__ T ld_t(const TI* p) { return (T)ld_f<TI>(p); }
+template <> __device__ __forceinline__ double ld_t<double, double>(const double* p) { return *p; }
+
+template <int DIM, int N, int NT, typename TI>
+struct EigCfg {
+  static constexpr int NB = DIM == 3 ? N * N * N : N * N;
+  static constexpr int NBP = eig_nbp(NB);
+  static constexpr int CELL_BYTES = (int)eig_cell_bytes_c(NB, (int)sizeof(TI));
+  static constexpr int CPG0 = 128 / NB;
+  static constexpr int CPG_MEM = 24576 / CELL_BYTES;
+  static constexpr int CPG = CPG0 < CPG_MEM ? (CPG0 > 0 ? CPG0 : 1) : (CPG_MEM > 0 ? CPG_MEM : 1);
+  static constexpr int THREADS = (CPG * NB + 31) / 32 * 32;
+  static constexpr int STAGE_BYTES = CPG * CELL_BYTES;
+  static constexpr int S = 2;
+  static constexpr size_t SMEM = (size_t)S * STAGE_BYTES;
+};
+
+template <int DIM, int N, int NT, typename T, typename TI, bool MULTI>
+__global__ void __launch_bounds__(EigCfg<DIM, N, NT, TI>::THREADS)
+eig_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const unsigned char* __restrict__ inv, GridDesc g,
+                 ModeTab<T> mt, const T* __restrict__ copy_src, T* __restrict__ copy_dst, int* status, int nslab_arg,
+                 int64_t slab_stride) {
+  const int nslab = MULTI ? nslab_arg : 1;
+  pdl_wait();
+  pdl_trigger();
+  using C = EigCfg<DIM, N, NT, TI>;
+  constexpr int NB = C::NB, NBP = C::NBP, CPG = C::CPG, S = C::S;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[S];
+  __shared__ __align__(16) T s_r[CPG][NT][NBP];  // modal residual (rows: time modes, columns: nodes)
+  __shared__ __align__(16) T s_z[CPG][NT][NBP];  // eigen-coefficients scaled by 1 / (lambda + mu)
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  const int64_t ngroups = (g.n_cells + CPG - 1) / CPG;
+  auto group_bytes = [&](int64_t grp) -> uint32_t {
+    const int64_t c0 = grp * CPG;
+    const int64_t nc = g.n_cells - c0 < CPG ? g.n_cells - c0 : CPG;
+    return (uint32_t)(nc * C::CELL_BYTES);
+  };
+  if (tid == 0) s_fail = *reinterpret_cast<const volatile int*>(status);
+  for (int i = tid; i < CPG * NT * NBP; i += blockDim.x) {
+    (&s_r[0][0][0])[i] = T(0);
+    (&s_z[0][0][0])[i] = T(0);
+  }
+  __syncthreads();
+  if (s_fail) return;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) tc::mbar_init(&bar[s], 1);
+    tc::mbar_fence_init();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  int64_t issued = 0;
+  if (tid == 0)
+    for (int s = 0; s < S; ++s) {
+      const int64_t grp = blockIdx.x + (int64_t)s * gridDim.x;
+      if (grp < ngroups)
+        tc::bulk_load(smem_raw + (size_t)s * C::STAGE_BYTES, inv + grp * CPG * (int64_t)C::CELL_BYTES, group_bytes(grp),
+                      &bar[s]);
+    }
+  for (int s = 0; s < S; ++s)
+    if (blockIdx.x + (int64_t)s * gridDim.x < ngroups) ++issued;
+  int64_t k = 0;
+  const int slot = tid / NB, a = tid - slot * NB;
+  struct Pre { int64_t node; bool active, live; T w; T rr[NT], cp[NT]; };
+  auto prefetch = [&](int64_t grp, int sl, Pre& P) {
+    const int64_t cell = grp * CPG + slot;
+    P.active = grp < ngroups && slot < CPG && cell < g.n_cells;
+    P.live = false;
+    P.node = 0;
+    P.w = T(1);
+    if (!P.active) return;
+    const int64_t so = MULTI ? (int64_t)sl * slab_stride : 0;
+    const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
+    const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+    const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
+    const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
+    bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+    if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
+    P.node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+    P.live = !bnd;
+    if (mt.weighted) P.w = node_weight<T>(gx, gy, gz, DIM, g.p);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) P.rr[t] = P.live ? r[so + t * g.n_nodes + P.node] : T(0);
+    if (copy_dst) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) P.cp[t] = copy_src[so + t * g.n_nodes + P.node];
+    }
+  };
+  Pre cur, nxt;
+  prefetch(blockIdx.x, 0, cur);
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++k) {
+    const int stage = (int)(k % S);
+    const uint32_t parity = (uint32_t)((k / S) & 1);
+    for (int sl = 0; sl < nslab; ++sl) {
+      const int64_t so = MULTI ? (int64_t)sl * slab_stride : 0;
+      if (sl + 1 < nslab) prefetch(grp, sl + 1, nxt);
+      else prefetch(grp + gridDim.x, 0, nxt);
+      const bool active = cur.active, live = cur.live;
+      const int64_t node = so + cur.node;
+      if (active) {
+        if (copy_dst) {
+#pragma unroll
+          for (int t = 0; t < NT; ++t) copy_dst[t * g.n_nodes + node] = cur.cp[t];
+        }
+#pragma unroll
+        for (int m = 0; m < NT; ++m) {
+          const bool is_real = m < mt.nreal;
+          const int mode = is_real ? m : mt.nreal + (m - mt.nreal) / 2;
+          const bool im_part = !is_real && ((m - mt.nreal) & 1);
+          T v = 0;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * cur.rr[t];
+          s_r[slot][m][a] = v;
+        }
+      }
+      if (sl == 0 && !tc::mbar_wait_bounded(&bar[stage], parity, status)) {
+        atomicExch(status, STMG_DEVICE_TIMEOUT);
+        s_fail = 1;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      const unsigned char* blk = smem_raw + (size_t)stage * C::STAGE_BYTES + (size_t)slot * C::CELL_BYTES;
+      const TI* Q = reinterpret_cast<const TI*>(blk);
+      const float* mu = reinterpret_cast<const float*>(blk + (size_t)NB * NBP * sizeof(TI));
+      if (active) {
+        // y = Q^T s for eigenvector j = a, all time modes at once; then z_hat = y / (lambda + mu_j)
+        T y[NT];
+#pragma unroll
+        for (int m = 0; m < NT; ++m) y[m] = 0;
+#pragma unroll 9
+        for (int b = 0; b < NB; ++b) {
+          const T q = ld_t<T, TI>(Q + b * NBP + a);
+#pragma unroll
+          for (int m = 0; m < NT; ++m) y[m] += q * s_r[slot][m][b];
+        }
+        const T muj = (T)mu[a];
+#pragma unroll
+        for (int m = 0; m < NT; ++m) {
+          if (m < mt.nreal) {
+            s_z[slot][m][a] = y[m] / (mt.lre[m] + muj);
+          } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+            const int mode = mt.nreal + (m - mt.nreal) / 2;
+            const T dr = mt.lre[mode] + muj, di = mt.lim[mode];
+            const T inv_den = T(1) / (dr * dr + di * di);
+            s_z[slot][m][a] = (y[m] * dr + y[m + 1] * di) * inv_den;
+            s_z[slot][m + 1][a] = (y[m + 1] * dr - y[m] * di) * inv_den;
+          }
+        }
+      }
+      __syncthreads();
+      if (active && live) {
+        // z = Q z_hat for node a (row a of Q), all modes at once
+        T z[NT];
+#pragma unroll
+        for (int m = 0; m < NT; ++m) z[m] = 0;
+#pragma unroll 9
+        for (int j = 0; j < NB; ++j) {
+          const T q = ld_t<T, TI>(Q + a * NBP + j);
+#pragma unroll
+          for (int m = 0; m < NT; ++m) z[m] += q * s_z[slot][m][j];
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          T o = 0;
+#pragma unroll
+          for (int m = 0; m < NT; ++m) {
+            if (m < mt.nreal) {
+              o += mt.Vr[t][m] * z[m];
+            } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+              const int mode = mt.nreal + (m - mt.nreal) / 2;
+              o += T(2) * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
+            }
+          }
+          atomicAdd(u + t * g.n_nodes + node, mt.omega * cur.w * o);
+        }
+      }
+      __syncthreads();  // s_r, s_z free again (and, after the last slab, the stage)
+      if (sl + 1 < nslab) cur = nxt;
+    }
+    if (s_fail) break;
+    const int64_t next = grp + (int64_t)S * gridDim.x;
+    if (next < ngroups) {
+      if (tid == 0)
+        tc::bulk_load(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * (int64_t)C::CELL_BYTES,
+                      group_bytes(next), &bar[stage]);
+      ++issued;
+    }
+    cur = nxt;
+  }
+  if (s_fail) {
+    for (int64_t q = k; q < issued; ++q) tc::mbar_wait_bounded(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
+  }
+}
+
+template <int DIM, int N>
+cudaError_t eig_setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, void* out, int prec,
+                        cudaStream_t s) {
+  constexpr int NB = DIM == 3 ? N * N * N : N * N;
+  const size_t smem = (size_t)3 * NB * NB * sizeof(double);
+  auto k = eig_setup_kernel<DIM, N>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)g.n_cells, kEigThreads, smem, s>>>(g, geo64, lt, reinterpret_cast<unsigned char*>(out), prec);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NT, typename T, typename TI, bool MULTI>
+cudaError_t eig_launch(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd,
+                       int* status, int nslab, int64_t ss, cudaStream_t s) {
+  using C = EigCfg<DIM, N, NT, TI>;
+  auto k = eig_apply_kernel<DIM, N, NT, T, TI, MULTI>;
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
+  const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+  const cudaError_t e = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), C::SMEM, s, r, u,
+                                 reinterpret_cast<const unsigned char*>(inv), g, mt, cs, cd, status, nslab, ss);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NT, typename T, typename TI>
+cudaError_t eig_apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const ModeTab<T>& mt, const T* cs, T* cd,
+                        int* status, int nslab, int64_t ss, cudaStream_t s) {
+  if (!status) return cudaErrorInvalidValue;
+  return nslab > 1 ? eig_launch<DIM, N, NT, T, TI, true>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s)
+                   : eig_launch<DIM, N, NT, T, TI, false>(r, u, inv, g, mt, cs, cd, status, 1, ss, s);
+}
+
+}  // namespace
+
+int64_t eig_cell_bytes(int dim, int n, int esz) { return eig_cell_bytes_c(dim == 3 ? n * n * n : n * n, esz); }
+
+cudaError_t launch_eig_setup(int dim, int n, const GridDesc& g, const double* geo64, const LocalTab& lt, void* out,
+                             int prec, cudaStream_t s) {
+  if (prec < 0 || prec > 2) return cudaErrorInvalidValue;
+  if (dim == 3) {
+    if (n == 2) return eig_setup_t<3, 2>(g, geo64, lt, out, prec, s);
+    if (n == 3) return eig_setup_t<3, 3>(g, geo64, lt, out, prec, s);
+    if (n == 4) return eig_setup_t<3, 4>(g, geo64, lt, out, prec, s);
+  } else {
+    if (n == 2) return eig_setup_t<2, 2>(g, geo64, lt, out, prec, s);
+    if (n == 3) return eig_setup_t<2, 3>(g, geo64, lt, out, prec, s);
+    if (n == 4) return eig_setup_t<2, 4>(g, geo64, lt, out, prec, s);
+    if (n == 5) return eig_setup_t<2, 5>(g, geo64, lt, out, prec, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+#define STMG_EIG_CASE(DIM, N, NT)                                                                            \
+  if (dim == DIM && n == N && nt == NT) {                                                                    \
+    if (prec == 0) return eig_apply_t<DIM, N, NT, T, double>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s); \
+    if (prec == 1) return eig_apply_t<DIM, N, NT, T, float>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);  \
+    return eig_apply_t<DIM, N, NT, T, __nv_bfloat16>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);         \
+  }
+
+template <typename T>
+cudaError_t launch_eig_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int prec, const GridDesc& g,
+                             const ModeTab<T>& mt, const T* cs, T* cd, int* status, int nslab, int64_t ss,
+                             cudaStream_t s) {
+  STMG_EIG_CASE(3, 2, 1) STMG_EIG_CASE(3, 2, 2) STMG_EIG_CASE(3, 2, 3) STMG_EIG_CASE(3, 2, 4)
+  STMG_EIG_CASE(3, 3, 1) STMG_EIG_CASE(3, 3, 2) STMG_EIG_CASE(3, 3, 3) STMG_EIG_CASE(3, 3, 4)
+  STMG_EIG_CASE(3, 4, 1) STMG_EIG_CASE(3, 4, 2) STMG_EIG_CASE(3, 4, 3) STMG_EIG_CASE(3, 4, 4)
+  STMG_EIG_CASE(2, 2, 1) STMG_EIG_CASE(2, 2, 2) STMG_EIG_CASE(2, 2, 3) STMG_EIG_CASE(2, 2, 4)
+  STMG_EIG_CASE(2, 3, 1) STMG_EIG_CASE(2, 3, 2) STMG_EIG_CASE(2, 3, 3) STMG_EIG_CASE(2, 3, 4)
+  STMG_EIG_CASE(2, 4, 1) STMG_EIG_CASE(2, 4, 2) STMG_EIG_CASE(2, 4, 3) STMG_EIG_CASE(2, 4, 4)
+  STMG_EIG_CASE(2, 5, 1) STMG_EIG_CASE(2, 5, 2) STMG_EIG_CASE(2, 5, 3) STMG_EIG_CASE(2, 5, 4)
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_eig_apply<float>(int, int, int, const float*, float*, const void*, int, const GridDesc&,
+                                             const ModeTab<float>&, const float*, float*, int*, int, int64_t,
+                                             cudaStream_t);
+template cudaError_t launch_eig_apply<double>(int, int, int, const double*, double*, const void*, int, const GridDesc&,
+                                              const ModeTab<double>&, const double*, double*, int*, int, int64_t,
+                                              cudaStream_t);
+
+}  // namespace stmg

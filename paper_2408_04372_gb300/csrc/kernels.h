@@ -63,6 +63,17 @@ cudaError_t launch_asm_setup(int dim, int n, int nt, const GridDesc& g, const do
                              int inv_prec, int weighted, cudaStream_t s);
 // elements per cell in the inverse store (N_t planes, padded to a 16-byte multiple)
 int64_t asm_cell_stride(int dim, int n, int nt, int esz);
+// Local solves through a per-cell generalized eigendecomposition A_K Q = M_K Q diag(mu) (eig.cu):
+// bytes per cell of the store (Q as NB x NBP entries of esz bytes, then NBP FP32 eigenvalues),
+// the set-up (prec 0 FP64, 1 FP32, 2 BF16 storage of Q) and the smoother sweep (same contract as
+// launch_asm_apply; the weighted sum's factors are applied by the kernel).
+int64_t eig_cell_bytes(int dim, int n, int esz);
+cudaError_t launch_eig_setup(int dim, int n, const GridDesc& g, const double* geo64, const LocalTab& lt, void* out,
+                             int prec, cudaStream_t s);
+template <typename T>
+cudaError_t launch_eig_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int prec, const GridDesc& g,
+                             const ModeTab<T>& mt, const T* cs, T* cd, int* status, int nslab, int64_t ss,
+                             cudaStream_t s);
 // copy_src/copy_dst (may be NULL): side job for the V-cycle, copy_dst := copy_src on every node of every cell.
 // status (device int, may be NULL): with it the inverses arrive by bulk copies (TMA) into shared memory and
 // a timed-out wait stores STMG_DEVICE_TIMEOUT there; without it each thread streams its rows itself.

@@ -42,6 +42,7 @@ struct Level {
   void* inv = nullptr;
   int inv_prec = 1;
   bool fd = false;             // fast diagonalisation instead of stored inverses
+  bool eig = false;            // stored per-cell eigendecompositions (Q, mu) instead of inverse planes
   FDTab<double> fd64{};
   FDTab<float> fd32{};
   double* rho_cell64 = nullptr;
@@ -327,6 +328,12 @@ stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega, cons
   mt.omega = (T)omega;
   // block diagonal over the slabs: every space-time cell lies in one slab (same local inverses)
   const int64_t ss = L.slab_size();
+  if (L.eig) {
+    ctx->launches += 1;
+    CK(launch_eig_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->status, L.nc,
+                           ss, ctx->stream));
+    return STMG_OK;
+  }
   if (!L.fd) {
     ctx->launches += 1;
     CK(launch_asm_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->status, L.nc,
@@ -690,6 +697,23 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     CK(cudaMemcpy(L.rho_cell32, rcf.data(), sizeof(float) * rcf.size(), cudaMemcpyHostToDevice));
     return STMG_OK;
   }
+  if (L.eig) {
+    if (L.dim == 3 && L.n > 4) {
+      ctx->err = "the eigendecomposition smoother supports p <= 3 in 3D";
+      return STMG_ERR_UNSUPPORTED;
+    }
+    const int prec = L.inv_prec == 0 ? 0 : L.inv_prec == 1 ? 1 : 2;
+    L.inv_prec = prec;
+    const size_t bytes = (size_t)L.g.n_cells * eig_cell_bytes(L.dim, L.n, prec == 0 ? 8 : prec == 1 ? 4 : 2);
+    void* store = nullptr;
+    cudaError_t e = cudaMalloc(&store, bytes);
+    if (e != cudaSuccess) { ctx->err = std::string("cudaMalloc eigen store: ") + cudaGetErrorString(e); return STMG_ERR_OOM; }
+    ctx->allocations.push_back(store);
+    L.inv = store;
+    CK(launch_eig_setup(L.dim, L.n, L.g, L.geo64, L.lt, L.inv, prec, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return STMG_OK;
+  }
   const int NB = L.dim == 3 ? L.n * L.n * L.n : L.n * L.n;
   if (L.dim == 3 && L.n > 4) {
     ctx->err = "dense additive Schwarz setup supports p <= 3 in 3D";
@@ -1015,6 +1039,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
       }
     }
   }
+  if (o.smoother_kind < STMG_SMOOTHER_AUTO || o.smoother_kind > STMG_SMOOTHER_EIG)
+    return invalid(ctx, "smoother_kind must be AUTO, DENSE, FD or EIG");
   if (o.smoother_kind == STMG_SMOOTHER_FD && (dim != 3 || !cartesian))
     return invalid(ctx, "fast diagonalisation needs a 3D Cartesian grid");
   for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
@@ -1033,8 +1059,9 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
       }
     }
     if (o.smoother_kind == STMG_SMOOTHER_FD) L.fd = true;
-    else if (o.smoother_kind == STMG_SMOOTHER_DENSE) L.fd = false;
+    else if (o.smoother_kind == STMG_SMOOTHER_DENSE || o.smoother_kind == STMG_SMOOTHER_EIG) L.fd = false;
     else L.fd = dim == 3 && cartesian && (patch_const || L.n > 4);
+    L.eig = o.smoother_kind == STMG_SMOOTHER_EIG;
   }
   for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
     CKS(setup_smoother(ctx, ctx->levels[li]));
@@ -1840,6 +1867,11 @@ stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int
   d.ny = L0.g.nn1;
   d.nz = L0.dim == 3 ? L0.g.nn1 : 1;
   d.V = L0.g.n_nodes;
+  d.nxp = d.nx + 2;
+  d.nyp = d.ny + 2;
+  d.nzp = d.nz + 2;
+  d.Vp = (int64_t)d.nxp * d.nyp * d.nzp;
+  d.status = ctx->status;
   d.su = (float)scales[0];
   d.sf = (float)scales[1];
   d.so = (float)scales[2];
@@ -1875,11 +1907,15 @@ stmg_status stmg_net_create(stmg_net** out, stmg_ctx* ctx, int layers, const int
   }
   for (int l = 0; l <= layers; ++l) {
     stmg_status st;
-    if (l < layers && (st = net_alloc(net, (void**)&d.act[l], (size_t)d.V * d.cp[l] * 2)) != STMG_OK) return fail(st);
-    if (l >= 1 && (st = net_alloc(net, (void**)&d.grad[l], (size_t)d.V * d.cp[l] * 2)) != STMG_OK) return fail(st);
+    if (l < layers && (st = net_alloc(net, (void**)&d.act[l], (size_t)d.Vp * d.cp[l] * 2)) != STMG_OK) return fail(st);
+    if (l >= 1 && (st = net_alloc(net, (void**)&d.grad[l], (size_t)d.Vp * d.cp[l] * 2)) != STMG_OK) return fail(st);
   }
   stmg_status st;
-  if ((st = net_alloc(net, (void**)&d.out, (size_t)d.V * d.cp[layers] * 4)) != STMG_OK) return fail(st);
+  if ((st = net_alloc(net, (void**)&d.out, (size_t)d.Vp * d.cp[layers] * 4)) != STMG_OK) return fail(st);
+  if (net_make_tmaps(d) != cudaSuccess) {
+    ctx->err = "tensor maps of the network's convolutions could not be encoded";
+    return fail(STMG_ERR_CUDA);
+  }
   if ((st = net_alloc(net, (void**)&d.loss, 8)) != STMG_OK) return fail(st);
   if (net_refresh_bf16(d, ctx->stream) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
     return fail(STMG_ERR_CUDA);
@@ -1945,10 +1981,10 @@ stmg_status stmg_net_gradients(stmg_net* net, const double* u_prev, const double
   }
   if (out_host) {
     const int cpl = d.cp[d.L];
-    std::vector<float> o((size_t)d.V * cpl);
+    std::vector<float> o((size_t)d.Vp * cpl);
     CK(cudaMemcpy(o.data(), d.out, o.size() * 4, cudaMemcpyDeviceToHost));
     for (int c = 0; c < d.ch[d.L]; ++c)
-      for (int64_t v = 0; v < d.V; ++v) out_host[(size_t)c * d.V + v] = o[(size_t)v * cpl + c];
+      for (int64_t v = 0; v < d.V; ++v) out_host[(size_t)c * d.V + v] = o[(size_t)net_row(d, v) * cpl + c];
   }
   return STMG_OK;
 }
