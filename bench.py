@@ -202,7 +202,7 @@ def run_kernel_only(args):
     torch.cuda.set_device(0)
     wl = workload(args.n_cells)
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
-                       vcycle_precision=stmg.FP32, omega=[0.2] * 16,
+                       vcycle_precision=stmg.FP32, omega=[0.2] * 16, smoother_kind=smoother_kind(stmg, args),
                        inverse_precision={"fp32": stmg.FP32, "bf16": stmg.BF16, "fp64": stmg.FP64,
                                           "fp8": stmg.FP8}[args.inverse])
     kind, prec = {"apply64": (stmg.KERNEL_APPLY, stmg.FP64), "apply32": (stmg.KERNEL_APPLY, stmg.FP32),
@@ -242,7 +242,7 @@ def run_ours(args):
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                        vcycle_precision=vprec, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
                        coarse_max_dofs=args.coarse_max_dofs, asm_weighting=args.asm_weighting,
-                       outer_relax=args.outer_relax if not args.plain else 0)
+                       outer_relax=args.outer_relax if not args.plain else 0, smoother_kind=smoother_kind(stmg, args))
     nt, nn = ctx.nt, ctx.n_nodes
     n = nt * nn
     X = ctx.node_coords()
@@ -443,9 +443,14 @@ def run_ours(args):
                      "peak_source": "FP64 1.25 TFLOP/s nominal (GB300 table; no measured FP64 peak)",
                      "avg_launch_ms": apply_ms}
         nb = nq ** 3
+        eig = args.smoother == "eig"
         asm_roof = smoother_roofline(args.inverse, cells, nt, nb, n, asm_ms, peaks,
-                                     f"asm_apply_tma_kernel<3,3,3,float,{args.inverse}> (finest-level additive Schwarz, "
-                                     "TMA-fed)", traffic_key=f"asm_{args.inverse}" if args.inverse in ("bf16", "fp8") else None)
+                                     (f"eig_apply_kernel<3,3,3,float,{args.inverse}> (finest-level additive Schwarz, "
+                                      "per-cell eigendecompositions, TMA-fed)") if eig else
+                                     (f"asm_apply_tma_kernel<3,3,3,float,{args.inverse}> (finest-level additive Schwarz, "
+                                      "TMA-fed)"),
+                                     traffic_key=(f"eig_{args.inverse}" if eig else f"asm_{args.inverse}")
+                                     if args.inverse in ("bf16", "fp8") else None, eig=eig)
         if args.plain:
             roof = roof_fp64
             extra["asm_finest"] = asm_roof
@@ -633,6 +638,44 @@ def run_learned_c5(args):
         ms = ev0.elapsed_time(ev1)
         arms[name] = {"value": dofs * (n_slabs - n_train) / (ms / 1e3), "unit": UNIT, "ms_per_slab": ms / (n_slabs - n_train),
                       "fgmres_iterations_mean": float(np.mean(its)), "guess_taken": int(sum(taken))}
+    # the plain FP64 solver (FP64 V-cycle, FP64 operator apply) on the first held-out slabs, previous-slab guess
+    ctx64 = stmg.Context(3, N, p, k, tau, vcycle_precision=stmg.FP64, rtol=1e-8, restart=30, max_it=200,
+                         asm_weighting=args.asm_weighting)
+    sols.copy_(ref_sols)
+    n64 = min(16, n_slabs - n_train)
+    its64 = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for s_ in range(n_train, n_train + n64):
+        prev_end = sols[s_][(nt - 1) * nn:]
+        ctx64.rhs(F[s_], rhs, u0=prev_end)
+        ctx64.guess_previous(prev_end, u)
+        st = ctx64.solve(rhs, u)
+        assert st["converged"], st
+        sols[s_ + 1].copy_(u)
+        its64.append(st["iterations"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    arms["plain_fp64_previous_slab"] = {"value": dofs * n64 / (ms64 / 1e3), "unit": UNIT, "ms_per_slab": ms64 / n64,
+                                        "fgmres_iterations_mean": float(np.mean(its64)),
+                                        "slabs": f"{n_train}..{n_train + n64 - 1}"}
+    ctx64.close()
+    pred_ms = []
+    for _ in range(10):
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record()
+        net.predict(sols[n_train], F[n_train], cand)
+        b_.record()
+        torch.cuda.synchronize()
+        pred_ms.append(a_.elapsed_time(b_))
+    voxels = (N * p + 1) ** 3
+    conv_flops = 2 * 27 * voxels * sum(channels[l] * channels[l + 1] for l in range(len(channels) - 1))
+    inference = {"median_ms": float(np.median(pred_ms)), "flops": conv_flops,
+                 "tflops": conv_flops / (float(np.median(pred_ms)) * 1e-3) / 1e12,
+                 "frac_of_bf16_burst": conv_flops / (float(np.median(pred_ms)) * 1e-3) / 1e12 /
+                 read_peaks()["bf16_tflops"]}
     line = {"metric": "space-time DoFs/s solved to 1e-8, learned vs previous-slab initial guess (held-out slabs)",
             "value": arms["learned"]["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f64+f32+bf16", "data": "synthetic",
@@ -642,7 +685,7 @@ def run_learned_c5(args):
             "training": {"data_solve_s": t_data, "train_s": t_train, "steps": len(losses),
                          "loss_first_epoch": float(np.mean(losses[:n_train - 1])),
                          "loss_last_epoch": float(np.mean(losses[-(n_train - 1):]))},
-            "arms": arms}
+            "inference": inference, "arms": arms}
     print(json.dumps(line), flush=True)
     net.close()
     ctx.close()
@@ -732,7 +775,7 @@ def run_c3(args):
     ctx = stmg.Context(3, N, p, k, tau, pde=stmg.WAVE, scheme=stmg.CGP, vertices=V, coeff=rho,
                        vcycle_precision=stmg.FP32, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
                        coarse_max_dofs=args.coarse_max_dofs, asm_weighting=args.asm_weighting,
-                       outer_relax=args.outer_relax)
+                       outer_relax=args.outer_relax, smoother_kind=smoother_kind(stmg, args))
     setup_s = time.perf_counter() - t0
     nt, nn = ctx.nt, ctx.n_nodes
     n = nt * nn
@@ -782,7 +825,8 @@ def run_c3(args):
     asm_ms = ctx.time_kernel(stmg.KERNEL_ASM, 0, stmg.FP32, reps=20)
     cells, nq = N ** 3, p + 1
     roof = smoother_roofline(args.inverse, cells, nt, nq ** 3, n, asm_ms, peaks,
-                             f"asm_apply_tma_kernel<3,4,2,float,{args.inverse}> (finest-level additive Schwarz)")
+                             f"{'eig_apply_kernel' if args.smoother == 'eig' else 'asm_apply_tma_kernel'}"
+                             f"<3,4,2,float,{args.inverse}> (finest-level additive Schwarz)", eig=args.smoother == "eig")
     ga = apply_gdofs(stmg, ctx, dofs)
     flops = (12 * nq ** 4 + (16 + 8 * nt) * nq ** 3) * cells * nt
     df_peak = 152 * 128 * 2.07e9 / 15 * 2
@@ -887,16 +931,29 @@ def run_shm(args):
     return 0
 
 
-def smoother_roofline(inverse, cells, nt, nb, n, asm_ms, peaks, kernel_name, traffic_key=None):
+def smoother_kind(stmg, args):
+    return {"auto": stmg.SMOOTHER_AUTO, "dense": stmg.SMOOTHER_DENSE, "eig": stmg.SMOOTHER_EIG}[args.smoother]
+
+
+def smoother_roofline(inverse, cells, nt, nb, n, asm_ms, peaks, kernel_name, traffic_key=None, eig=False):
     """Finest-level Schwarz sweep against the measured copy bandwidth.  Algorithmic bytes: the
-    inverse entries themselves, n_b^2 per time plane and cell (no padding), plus two FP32 vectors
-    (residual in, correction out); the stored block with its padding is reported apart."""
+    stored local solver without padding -- n_b^2 inverse entries per time plane and cell, or with the
+    eigendecomposition smoother the n_b^2 entries of Q and n_b FP32 eigenvalues per cell -- plus two
+    FP32 vectors (residual in, correction out); the stored block with its padding is reported apart."""
     inv_bytes = {"fp32": 4, "bf16": 2, "fp64": 8, "fp8": 1}[inverse]
-    alg = cells * nt * nb * nb * inv_bytes + 2 * 4 * n
-    plane_entries = nt * nb * ((nb + 3) // 4 * 4)
-    cell_bytes = ((plane_entries + 4 * nt + 15) // 16 * 16 if inv_bytes == 1 else
-                  (plane_entries + 7) // 8 * 8 * inv_bytes)
-    stored = cells * cell_bytes + 2 * 4 * n
+    nbp = (nb + 3) // 4 * 4
+    if eig:
+        inv_bytes = 2 if inverse == "fp8" else inv_bytes  # FP8 requests store Q in BF16
+        mu_bytes = 8 if inv_bytes == 8 else 4
+        nbq = nbp if (nbp // 4) % 2 == 1 else nbp + 4  # Q's row stride (odd number of 4-entry chunks)
+        alg = cells * (nb * nb * inv_bytes + mu_bytes * nb) + 2 * 4 * n
+        stored = cells * ((nb * nbq * inv_bytes + mu_bytes * nbq + 15) // 16 * 16) + 2 * 4 * n
+    else:
+        alg = cells * nt * nb * nb * inv_bytes + 2 * 4 * n
+        plane_entries = nt * nb * nbp
+        cell_bytes = ((plane_entries + 4 * nt + 15) // 16 * 16 if inv_bytes == 1 else
+                      (plane_entries + 7) // 8 * 8 * inv_bytes)
+        stored = cells * cell_bytes + 2 * 4 * n
     gbs = alg / (asm_ms * 1e-3) / 1e9
     return {"kernel": kernel_name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / peaks["hbm_gbs"],
@@ -1052,6 +1109,9 @@ def main():
     ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64", "fp8"],
                     help="storage of the Schwarz inverses in the mixed solver")
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--smoother", default="dense", choices=["auto", "dense", "eig"],
+                    help="local solver of the Schwarz smoother: stored inverse planes (dense) or per-cell "
+                         "eigendecompositions (eig)")
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")

@@ -15,8 +15,9 @@
 // C = L^-1 A_K L^-T, cyclic Jacobi on C (parallel round-robin ordering, rotations by Golub and
 // Van Loan's symmetric Schur decomposition) until the off-diagonal part is below 1e-15 of C,
 // Q = L^-T U.  Store per cell: Q[a][j] row-major over the local nodes a (rows and columns of
-// constrained nodes zero), NBP = NB rounded up to 4 columns, then NBP FP32 eigenvalues (1 in the
-// padding), the block padded to 16 bytes.
+// constrained nodes zero) with row stride NBP (NB rounded up to whole 4-entry chunks, an odd number
+// of them), then NBP eigenvalues (FP64 next to an FP64 Q, else FP32; 1 in the padding), the block
+// padded to 16 bytes.
 //
 // eig_apply_kernel: TMA-fed like the plane smoother -- each persistent CTA walks groups of
 // consecutive cells whose blocks arrive by one bulk copy into a ring of two shared-memory stages
@@ -36,9 +37,13 @@ namespace stmg {
 
 namespace {
 
-__host__ __device__ constexpr int eig_nbp(int nb) { return (nb + 3) / 4 * 4; }
+// Row stride of Q: NB rounded up to a multiple of 4 entries with an odd number of 4-entry chunks, so
+// that the threads of a warp, each reading its own row four entries at a time, hit distinct banks.
+__host__ __device__ constexpr int eig_nbp(int nb) { return ((nb + 3) / 4) % 2 == 1 ? (nb + 3) / 4 * 4 : (nb + 3) / 4 * 4 + 4; }
+// eigenvalues in FP64 next to an FP64 Q, in FP32 otherwise
+__host__ __device__ constexpr int eig_mu_bytes(int esz) { return esz == 8 ? 8 : 4; }
 __host__ __device__ constexpr int64_t eig_cell_bytes_c(int nb, int esz) {
-  return ((int64_t)nb * eig_nbp(nb) * esz + (int64_t)eig_nbp(nb) * 4 + 15) / 16 * 16;
+  return ((int64_t)nb * eig_nbp(nb) * esz + (int64_t)eig_nbp(nb) * eig_mu_bytes(esz) + 15) / 16 * 16;
 }
 
 constexpr int kEigThreads = 256;
@@ -206,8 +211,12 @@ eig_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, unsign
     else if (prec == 1) reinterpret_cast<float*>(blk)[idx] = (float)v;
     else reinterpret_cast<__nv_bfloat16*>(blk)[idx] = __float2bfloat16((float)v);
   }
-  float* mu = reinterpret_cast<float*>(blk + (int64_t)NB * NBP * esz);
-  for (int j = tid; j < NBP; j += nth) mu[j] = j < m ? (float)A[j * m + j] : 1.0f;
+  unsigned char* mu = blk + (int64_t)NB * NBP * esz;
+  for (int j = tid; j < NBP; j += nth) {
+    const double v = j < m ? A[j * m + j] : 1.0;
+    if (prec == 0) reinterpret_cast<double*>(mu)[j] = v;
+    else reinterpret_cast<float*>(mu)[j] = (float)v;
+  }
 }
 
 // ---- apply ----
@@ -217,6 +226,14 @@ template <> __device__ __forceinline__ float ld_f<double>(const double* p) { ret
 template <> __device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 template <typename T, typename TI> __device__ __forceinline__ T ld_t(const TI* p) { return (T)ld_f<TI>(p); }
 template <> __device__ __forceinline__ double ld_t<double, double>(const double* p) { return *p; }
+
+// four consecutive entries of a row (8-byte aligned for BF16, 16 for FP32, 32 for FP64)
+__device__ __forceinline__ float4 row4(const __nv_bfloat16* p) {
+  const uint2 w = *reinterpret_cast<const uint2*>(p);
+  return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xffff0000u), __uint_as_float(w.y << 16),
+                     __uint_as_float(w.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 row4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 template <int DIM, int N, int NT, typename TI>
 struct EigCfg {
@@ -339,7 +356,8 @@ eig_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const unsigned char
       if (s_fail) break;
       const unsigned char* blk = smem_raw + (size_t)stage * C::STAGE_BYTES + (size_t)slot * C::CELL_BYTES;
       const TI* Q = reinterpret_cast<const TI*>(blk);
-      const float* mu = reinterpret_cast<const float*>(blk + (size_t)NB * NBP * sizeof(TI));
+      using MuT = typename std::conditional<sizeof(TI) == 8, double, float>::type;
+      const MuT* mu = reinterpret_cast<const MuT*>(blk + (size_t)NB * NBP * sizeof(TI));
       if (active) {
         // y = Q^T s for eigenvector j = a, all time modes at once; then z_hat = y / (lambda + mu_j)
         T y[NT];
@@ -371,11 +389,24 @@ eig_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const unsigned char
         T z[NT];
 #pragma unroll
         for (int m = 0; m < NT; ++m) z[m] = 0;
-#pragma unroll 9
-        for (int j = 0; j < NB; ++j) {
-          const T q = ld_t<T, TI>(Q + a * NBP + j);
+        if constexpr (std::is_same<T, float>::value && !std::is_same<TI, double>::value) {
+          // row a four entries at a time (padding entries of Q and of s_z are zero)
+#pragma unroll 4
+          for (int j = 0; j < NBP; j += 4) {
+            const float4 q = row4(Q + a * NBP + j);
 #pragma unroll
-          for (int m = 0; m < NT; ++m) z[m] += q * s_z[slot][m][j];
+            for (int m = 0; m < NT; ++m) {
+              const float4 v = *reinterpret_cast<const float4*>(&s_z[slot][m][j]);
+              z[m] += q.x * v.x + q.y * v.y + q.z * v.z + q.w * v.w;
+            }
+          }
+        } else {
+#pragma unroll 9
+          for (int j = 0; j < NB; ++j) {
+            const T q = ld_t<T, TI>(Q + a * NBP + j);
+#pragma unroll
+            for (int m = 0; m < NT; ++m) z[m] += q * s_z[slot][m][j];
+          }
         }
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
