@@ -66,6 +66,40 @@ def test_network_output_loss_and_gradients_match_oracle(env):
     ctx.close()
 
 
+def test_network_matches_oracle_on_a_larger_grid(env):
+    """Q2 on 8^3 cells (17^3 nodes: 54 row blocks of the tensor-core kernels, several CTAs per tap set in
+    the weight gradient), three layers 4 -> 24 -> 24 -> 2 (padded to 16 / 64 / 64 / 16 channels)."""
+    torch, stmg = env
+    N, ch = 8, (4, 24, 24, 2)
+    ctx = stmg.Context(3, N, 2, 1, 0.05, omega=[0.2] * 8)
+    nn1 = 2 * N + 1
+    W, b = synth.conv_net_init(ch, seed=6, last_scale=1.0)
+    b = [np.random.default_rng(40 + l).standard_normal(len(x)) * 0.05 for l, x in enumerate(b)]
+    rng = np.random.default_rng(3)
+    u_prev, f, u_t = (rng.standard_normal((2, ctx.n_nodes)) for _ in range(3))
+    scales = (0.9, 1.1, 1.5)
+    net = stmg.Net(ctx, ch, W, b, scales)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+    loss, gW, gb, out = net.gradients(d(u_prev), d(f), d(u_t))
+    onet = conv.Net([_bf16(w) for w in W], [np.asarray(x, np.float64) for x in b])
+    shape = (nn1, nn1, nn1)
+    x0 = np.concatenate([u_prev * scales[0], f * scales[1]]).reshape((4,) + shape)
+    target = ((u_t - u_prev[-1][None, :]) * scales[2]).reshape((2,) + shape)
+    mask = np.zeros(shape, bool)
+    mask[1:-1, 1:-1, 1:-1] = True
+    ref_out, _ = onet.forward(x0)
+    ref_loss, rW, rb = onet.loss_and_grads(x0, target, mask)
+    assert np.abs(out.reshape(ref_out.shape) - ref_out).max() < 3e-2 * np.abs(ref_out).max()
+    assert abs(loss - ref_loss) < 3e-2 * ref_loss
+    for l in range(len(W)):
+        for g, r in ((gW[l], rW[l]), (gb[l], rb[l])):
+            rel = np.linalg.norm(g - r) / np.linalg.norm(r)
+            cos = float(np.dot(g.ravel(), r.ravel()) / (np.linalg.norm(g) * np.linalg.norm(r)))
+            assert rel < 5e-2 and cos > 0.998, (l, rel, cos)
+    net.close()
+    ctx.close()
+
+
 def test_adam_step_matches_definition(env):
     torch, stmg = env
     ctx, nn1, W, b, u_prev, f, u_t = _setup(stmg, torch)
