@@ -443,14 +443,18 @@ def run_ours(args):
                      "peak_source": "FP64 1.25 TFLOP/s nominal (GB300 table; no measured FP64 peak)",
                      "avg_launch_ms": apply_ms}
         nb = nq ** 3
-        eig = args.smoother == "eig"
+        eig = args.smoother in ("eig", "eig_tc")
         asm_roof = smoother_roofline(args.inverse, cells, nt, nb, n, asm_ms, peaks,
+                                     ("eig_tc_kernel<3,3,3,1> (finest-level additive Schwarz, per-cell "
+                                      "eigendecompositions, both products on the tensor cores)")
+                                     if args.smoother == "eig_tc" else
                                      (f"eig_apply_kernel<3,3,3,float,{args.inverse}> (finest-level additive Schwarz, "
                                       "per-cell eigendecompositions, TMA-fed)") if eig else
                                      (f"asm_apply_tma_kernel<3,3,3,float,{args.inverse}> (finest-level additive Schwarz, "
                                       "TMA-fed)"),
-                                     traffic_key=(f"eig_{args.inverse}" if eig else f"asm_{args.inverse}")
-                                     if args.inverse in ("bf16", "fp8") else None, eig=eig)
+                                     traffic_key=(f"{args.smoother}_{args.inverse}" if eig else f"asm_{args.inverse}")
+                                     if args.inverse in ("bf16", "fp8") else None, eig=eig,
+                                     tc=args.smoother == "eig_tc")
         if args.plain:
             roof = roof_fp64
             extra["asm_finest"] = asm_roof
@@ -532,7 +536,7 @@ def at_once_arm(args, stmg, wl, F, sols, dofs_per_step, nt, nn, inv_prec, dev):
     n = nt * nn
     ctxb = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                         vcycle_precision=stmg.FP32, inverse_precision=inv_prec, rtol=1e-8, restart=30, max_it=200,
-                        n_slabs=nc, asm_weighting=args.asm_weighting)
+                        n_slabs=nc, asm_weighting=args.asm_weighting, smoother_kind=smoother_kind(stmg, args))
     rb = torch.empty(nc * n, dtype=torch.float64, device=dev)
     ub = torch.empty_like(rb)
     prev_end = sols[0][(nt - 1) * nn:]
@@ -826,7 +830,8 @@ def run_c3(args):
     cells, nq = N ** 3, p + 1
     roof = smoother_roofline(args.inverse, cells, nt, nq ** 3, n, asm_ms, peaks,
                              f"{'eig_apply_kernel' if args.smoother == 'eig' else 'asm_apply_tma_kernel'}"
-                             f"<3,4,2,float,{args.inverse}> (finest-level additive Schwarz)", eig=args.smoother == "eig")
+                             f"<3,4,2,float,{args.inverse}> (finest-level additive Schwarz)",
+                             eig=args.smoother in ("eig", "eig_tc"), tc=args.smoother == "eig_tc")
     ga = apply_gdofs(stmg, ctx, dofs)
     flops = (12 * nq ** 4 + (16 + 8 * nt) * nq ** 3) * cells * nt
     df_peak = 152 * 128 * 2.07e9 / 15 * 2
@@ -932,17 +937,22 @@ def run_shm(args):
 
 
 def smoother_kind(stmg, args):
-    return {"auto": stmg.SMOOTHER_AUTO, "dense": stmg.SMOOTHER_DENSE, "eig": stmg.SMOOTHER_EIG}[args.smoother]
+    return {"auto": stmg.SMOOTHER_AUTO, "dense": stmg.SMOOTHER_DENSE, "eig": stmg.SMOOTHER_EIG,
+            "eig_tc": stmg.SMOOTHER_EIG_TC}[args.smoother]
 
 
-def smoother_roofline(inverse, cells, nt, nb, n, asm_ms, peaks, kernel_name, traffic_key=None, eig=False):
+def smoother_roofline(inverse, cells, nt, nb, n, asm_ms, peaks, kernel_name, traffic_key=None, eig=False, tc=False):
     """Finest-level Schwarz sweep against the measured copy bandwidth.  Algorithmic bytes: the
     stored local solver without padding -- n_b^2 inverse entries per time plane and cell, or with the
     eigendecomposition smoother the n_b^2 entries of Q and n_b FP32 eigenvalues per cell -- plus two
     FP32 vectors (residual in, correction out); the stored block with its padding is reported apart."""
     inv_bytes = {"fp32": 4, "bf16": 2, "fp64": 8, "fp8": 1}[inverse]
     nbp = (nb + 3) // 4 * 4
-    if eig:
+    if tc:
+        nq = 16 if nb <= 16 else 32 if nb <= 32 else 64  # BF16 operand images padded to nq x nq
+        alg = cells * (nb * nb * 2 + 4 * nb) + 2 * 4 * n
+        stored = cells * (nq * nq * 2 + 4 * nq) + 2 * 4 * n
+    elif eig:
         inv_bytes = 2 if inverse == "fp8" else inv_bytes  # FP8 requests store Q in BF16
         mu_bytes = 8 if inv_bytes == 8 else 4
         nbq = nbp if (nbp // 4) % 2 == 1 else nbp + 4  # Q's row stride (odd number of 4-entry chunks)
@@ -1109,7 +1119,7 @@ def main():
     ap.add_argument("--inverse", default="bf16", choices=["fp32", "bf16", "fp64", "fp8"],
                     help="storage of the Schwarz inverses in the mixed solver")
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--smoother", default="dense", choices=["auto", "dense", "eig"],
+    ap.add_argument("--smoother", default="dense", choices=["auto", "dense", "eig", "eig_tc"],
                     help="local solver of the Schwarz smoother: stored inverse planes (dense) or per-cell "
                          "eigendecompositions (eig)")
     ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],

@@ -70,8 +70,13 @@ enum { STMG_FP64 = 1, STMG_FP32 = 2, STMG_BF16 = 3, STMG_DF32 = 4, STMG_FP8 = 5 
  *          (A_K + lambda_m M_K)^-1 = Q diag(1 / (mu + lambda_m)) Q^T for every time mode: one matrix Q
  *          and (p+1)^dim eigenvalues per cell instead of N_t planes (inverse_precision FP64, FP32 or
  *          BF16 for Q; FP8 stores BF16); any grid, p <= 3 in 3D, p <= 4 in 2D.
+ *   EIG_TC: EIG with Q in BF16 and both products Q^T s and Q z_hat on the tensor cores (tcgen05, FP32
+ *          accumulation; right-hand sides split into two BF16 parts); FP32 V-cycle only,
+ *          (p+1)^dim <= 64, at most 8 slabs per system; stmg_smooth with FP64 vectors returns
+ *          STMG_ERR_UNSUPPORTED.
  *   AUTO:  FD on 3D Cartesian grids where it is exact (or p = 4), DENSE elsewhere. */
-enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2, STMG_SMOOTHER_EIG = 3 };
+enum { STMG_SMOOTHER_AUTO = 0, STMG_SMOOTHER_DENSE = 1, STMG_SMOOTHER_FD = 2, STMG_SMOOTHER_EIG = 3,
+       STMG_SMOOTHER_EIG_TC = 4 };
 
 /* Structured grid of n_cells^dim cells.  vertices: HOST array of
  * (n_cells+1)^dim x dim coordinates (lexicographic, x fastest), copied at
@@ -117,7 +122,7 @@ typedef struct {
   int nu_post;             /* post-smoothing sweeps nu_2 [1] */
   int vcycle_precision;    /* STMG_FP32 (mixed) or STMG_FP64 (plain) [FP32] */
   int inverse_precision;   /* storage of dense local inverses: FP64/FP32/BF16/FP8 [same as V-cycle] */
-  int smoother_kind;       /* AUTO, DENSE, FD or EIG (see above) [AUTO] */
+  int smoother_kind;       /* AUTO, DENSE, FD, EIG or EIG_TC (see above) [AUTO] */
   const double* omega;     /* host, may be NULL */
   int fgmres_restart;      /* [30] */
   double rtol;             /* relative residual target of stmg_solve [1e-8] */

@@ -18,7 +18,7 @@ HEAT, WAVE = 0, 1
 DG, CGP = 0, 1
 COEFF_PER_CELL, COEFF_PER_QPOINT = 0, 1
 FP64, FP32, BF16, DF32, FP8 = 1, 2, 3, 4, 5
-SMOOTHER_AUTO, SMOOTHER_DENSE, SMOOTHER_FD, SMOOTHER_EIG = 0, 1, 2, 3
+SMOOTHER_AUTO, SMOOTHER_DENSE, SMOOTHER_FD, SMOOTHER_EIG, SMOOTHER_EIG_TC = 0, 1, 2, 3, 4
 COARSEN_P_THEN_H, COARSEN_H = 0, 1
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN",

@@ -46,6 +46,9 @@ __host__ __device__ constexpr int64_t eig_cell_bytes_c(int nb, int esz) {
   return ((int64_t)nb * eig_nbp(nb) * esz + (int64_t)eig_nbp(nb) * eig_mu_bytes(esz) + 15) / 16 * 16;
 }
 
+// tensor-core variant: Q padded to NQ x NQ (16, 32 or 64 rows of 32, 64 or 128 bytes)
+__host__ __device__ constexpr int eig_tc_nq(int nb) { return nb <= 16 ? 16 : nb <= 32 ? 32 : 64; }
+
 constexpr int kEigThreads = 256;
 constexpr int kMaxSweeps = 24;
 
@@ -202,6 +205,24 @@ eig_setup_kernel(GridDesc g, const double* __restrict__ geo, LocalTab lt, unsign
       U[i * m + c] = x / M[i * m + i];
     }
   __syncthreads();
+  if (prec == 3) {
+    // tensor-core operand image: Q padded to NQ x NQ, rows of NQ BF16, the 16-byte chunks of each row
+    // permuted by the swizzle of the row width (the pattern TMA and the tensor core use), eigenvalues apart
+    constexpr int NQ = eig_tc_nq(NB);
+    constexpr uint32_t mask = NQ == 16 ? 1u : NQ == 32 ? 3u : 7u;
+    unsigned char* img = out + cell * (int64_t)NQ * NQ * 2;
+    for (int idx = tid; idx < NQ * NQ; idx += nth) {
+      const int a = idx / NQ, j = idx % NQ;
+      const int ia = a < NB ? s_loc[a] : -1;
+      const double v = (ia >= 0 && j < m) ? U[ia * m + j] : 0.0;
+      const uint32_t o = (uint32_t)(a * NQ * 2 + 2 * j);
+      const uint32_t sw = o ^ (((o >> 7) & mask) << 4);
+      *reinterpret_cast<__nv_bfloat16*>(img + sw) = __float2bfloat16((float)v);
+    }
+    float* mu = reinterpret_cast<float*>(out + (int64_t)g.n_cells * NQ * NQ * 2) + cell * NQ;
+    for (int j = tid; j < NQ; j += nth) mu[j] = j < m ? (float)A[j * m + j] : 1.0f;
+    return;
+  }
   const int esz = prec == 0 ? 8 : prec == 1 ? 4 : 2;
   unsigned char* blk = out + cell * eig_cell_bytes_c(NB, esz);
   for (int idx = tid; idx < NB * NBP; idx += nth) {
@@ -441,6 +462,331 @@ eig_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const unsigned char
   }
 }
 
+// ---- tensor-core sweep ----
+// A CTA of 128 threads owns tiles of CPT = 128 / NQ consecutive cells; thread t is accumulator row t =
+// (cell c = t / NQ, local node or eigenvector index a = t % NQ).  Per tile the Q images of its cells arrive
+// by one bulk copy (two stages); per round (all slabs of the system at once when they fit, NSL <= 8):
+//   1. threads write the modal residual of their node, split into BF16 high and low parts, into the
+//      right-hand-side operand B_c of their cell (rows = (part, slab, time mode), K = node);
+//   2. one thread issues, per cell c, D_c = Q_stack^T B_c^T on the tensor cores: A = the tile's Q images
+//      read M-major (M = (cell, eigenvector index), each cell one swizzle column), so the rows of cell c
+//      hold Q_c^T s_c (the other cells' rows are not read);
+//   3. threads read their row of D_c from tensor memory, add the two parts, divide by lambda_m + mu_j and
+//      write z_hat (again as two BF16 parts) into B_c;
+//   4. per cell, D_c = Q_stack B_c^T with A read K-major (rows (cell, node), K = eigenvector index);
+//   5. threads read their row (node a of cell c), add the parts, transform back to the time basis and
+//      add omega w_a times it to u with atomics.
+template <int DIM, int N, int NT, int NSL>
+struct EigTcCfg {
+  static constexpr int NB = DIM == 3 ? N * N * N : N * N;
+  static constexpr int NQ = eig_tc_nq(NB);
+  static constexpr int CPT = 128 / NQ;
+  static constexpr int RB = NQ * 2;
+  static constexpr uint32_t ATOM = 8 * RB;
+  static constexpr tc::Swizzle SW = NQ == 16 ? tc::kSw32 : NQ == 32 ? tc::kSw64 : tc::kSw128;
+  static constexpr uint32_t SWMASK = NQ == 16 ? 1u : NQ == 32 ? 3u : 7u;
+  static constexpr int CELL_Q = NQ * NQ * 2;
+  static constexpr int TILE_Q = CPT * CELL_Q;
+  static constexpr int NR = 2 * NT * NSL;                 // operand rows: two parts x slabs x modes
+  static constexpr int NP = (NR + 15) / 16 * 16;          // N of the MMAs
+  static constexpr int B_CELL = NP * RB;
+  static constexpr int B_BYTES = CPT * B_CELL;
+  static constexpr int S = 2;
+  static constexpr size_t SMEM = (size_t)S * TILE_Q + B_BYTES + 1024;
+  static constexpr uint32_t TMEM_COLS = CPT * NP <= 32 ? 32 : CPT * NP <= 64 ? 64 : CPT * NP <= 128 ? 128 : 256;
+};
+
+// This thread's accumulator row (TMEM lane = thread index) in the column block of its cell c.  The load
+// is warp-collective: a warp that spans several cells (NQ = 16) loads every cell's block and keeps its own.
+template <int NP, int NQ>
+__device__ __forceinline__ void load_row(uint32_t tmem, int warp, int c, float (&v)[NP]) {
+  constexpr int CPW = NQ >= 32 ? 1 : 32 / NQ;
+#pragma unroll
+  for (int i = 0; i < CPW; ++i) {
+    const int cw = (32 * warp) / NQ + i;
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      float t16[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cw * NP + c0), t16);
+      if (cw == c) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[c0 + j] = t16[j];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void store_bf16_swz(unsigned char* base, uint32_t o, uint32_t mask, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + (o ^ (((o >> 7) & mask) << 4))) = __float2bfloat16(v);
+}
+
+template <int DIM, int N, int NT, int NSL>
+__global__ void __launch_bounds__(128)
+eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned char* __restrict__ qimg,
+              const float* __restrict__ mu_all, GridDesc g, ModeTab<float> mt, const float* __restrict__ copy_src,
+              float* __restrict__ copy_dst, int* status, int nslab, int64_t slab_stride) {
+  pdl_wait();
+  pdl_trigger();
+  using C = EigTcCfg<DIM, N, NT, NSL>;
+  constexpr int NB = C::NB, NQ = C::NQ, CPT = C::CPT, S = C::S;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[S], mma_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* bops = ring + (size_t)S * C::TILE_Q;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int c = tid / NQ, a = tid % NQ;
+  const int64_t ntiles = (g.n_cells + CPT - 1) / CPT;
+  auto tile_bytes = [&](int64_t tl) -> uint32_t {
+    const int64_t c0 = tl * CPT;
+    const int64_t nc = g.n_cells - c0 < CPT ? g.n_cells - c0 : CPT;
+    return (uint32_t)(nc * C::CELL_Q);
+  };
+  if (tid == 0) {
+    s_fail = *reinterpret_cast<const volatile int*>(status);
+    for (int s = 0; s < S; ++s) tc::mbar_init(&bar[s], 1);
+    tc::mbar_init(&mma_bar, 1);
+    tc::mbar_fence_init();
+  }
+  for (int i = tid; i < C::B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(bops)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, C::TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const bool skip = s_fail != 0;
+  int64_t issued = 0, k = 0;
+  uint32_t mma_phase = 0;
+  int pending = -1;  // parity of an MMA round whose completion a wait gave up on
+  if (!skip) {
+    if (tid == 0)
+      for (int s = 0; s < S; ++s) {
+        const int64_t tl = blockIdx.x + (int64_t)s * gridDim.x;
+        if (tl < ntiles) tc::bulk_load(ring + (size_t)s * C::TILE_Q, qimg + tl * (int64_t)C::TILE_Q, tile_bytes(tl), &bar[s]);
+      }
+    for (int s = 0; s < S; ++s)
+      if (blockIdx.x + (int64_t)s * gridDim.x < ntiles) ++issued;
+  }
+  unsigned char* Bc = bops + (size_t)c * C::B_CELL;
+  constexpr uint32_t idesc_t = tc::idesc_bf16_f32(128, C::NP) | (1u << 15);  // A read M-major (Q^T)
+  constexpr uint32_t idesc_n = tc::idesc_bf16_f32(128, C::NP);               // A read K-major (Q)
+  const int nsl = NSL > 1 ? nslab : 1;
+  for (int64_t tl = blockIdx.x; tl < ntiles && !skip; tl += gridDim.x, ++k) {
+    const int stage = (int)(k % S);
+    const uint32_t parity = (uint32_t)((k / S) & 1);
+    const int64_t cell = tl * CPT + c;
+    const int ncells = (int)(g.n_cells - tl * CPT < CPT ? g.n_cells - tl * CPT : CPT);
+    const bool active = cell < g.n_cells && a < NB;
+    bool live = false;
+    int64_t node = 0;
+    float w = 1.f, muj = 1.f;
+    if (active) {
+      const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
+      const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+      const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
+      const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
+      bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+      if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
+      node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+      live = !bnd;
+      if (mt.weighted) w = node_weight<float>(gx, gy, gz, DIM, g.p);
+    }
+    if (cell < g.n_cells) muj = __ldg(mu_all + cell * NQ + a);
+    // 1. modal residual of every slab (as two BF16 parts) into B_c; side job copy
+#pragma unroll 1
+    for (int sl = 0; sl < nsl; ++sl) {
+      const int64_t so = (int64_t)sl * slab_stride;
+      float rr[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) rr[t] = live ? r[so + t * g.n_nodes + node] : 0.f;
+      if (copy_dst && active) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) copy_dst[so + t * g.n_nodes + node] = copy_src[so + t * g.n_nodes + node];
+      }
+#pragma unroll
+      for (int m = 0; m < NT; ++m) {
+        const bool is_real = m < mt.nreal;
+        const int mode = is_real ? m : mt.nreal + (m - mt.nreal) / 2;
+        const bool im_part = !is_real && ((m - mt.nreal) & 1);
+        float v = 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[t];
+        const float hi = __bfloat162float(__float2bfloat16(v));
+        store_bf16_swz(Bc, (uint32_t)((sl * NT + m) * C::RB + 2 * a), C::SWMASK, hi);
+        store_bf16_swz(Bc, (uint32_t)((NT * NSL + sl * NT + m) * C::RB + 2 * a), C::SWMASK, v - hi);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0 && !tc::mbar_wait_bounded(&bar[stage], parity, status)) {
+      atomicExch(status, STMG_DEVICE_TIMEOUT);
+      s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const uint32_t qa = tc::smem_addr(ring + (size_t)stage * C::TILE_Q);
+    const uint32_t ba = tc::smem_addr(bops);
+    // 2. y = Q^T s per cell
+    if (tid == 0) {
+      tc::fence_after_sync();
+      for (int cc = 0; cc < ncells; ++cc)
+#pragma unroll
+        for (int ks = 0; ks < NQ / 16; ++ks) {
+          const uint64_t ad = tc::smem_desc(qa + ks * 2 * C::ATOM, C::CELL_Q, C::ATOM, C::SW);
+          const uint64_t bd = tc::smem_desc(ba + cc * C::B_CELL + ks * 32, 16, C::ATOM, C::SW);
+          tc::mma_bf16(tmem + (uint32_t)(cc * C::NP), ad, bd, idesc_t, ks > 0 ? 1u : 0u);
+        }
+      tc::mma_commit(&mma_bar);
+    }
+    bool ok = tc::mbar_wait_bounded(&mma_bar, mma_phase, status);
+    if (!ok) pending = (int)mma_phase;
+    mma_phase ^= 1u;
+    __syncwarp();
+    tc::fence_after_sync();
+    // 3. z_hat = y / (lambda + mu_a) into B_c
+    {
+      float v[C::NP];
+      load_row<C::NP, NQ>(tmem, warp, c, v);
+#pragma unroll 1
+      for (int sl = 0; sl < nsl; ++sl) {
+        float y[NT];
+#pragma unroll
+        for (int m = 0; m < NT; ++m) y[m] = v[sl * NT + m] + v[NT * NSL + sl * NT + m];
+        float zh[NT];
+#pragma unroll
+        for (int m = 0; m < NT; ++m) {
+          if (m < mt.nreal) {
+            zh[m] = y[m] / (mt.lre[m] + muj);
+          } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+            const int mode = mt.nreal + (m - mt.nreal) / 2;
+            const float dr = mt.lre[mode] + muj, di = mt.lim[mode];
+            const float inv_den = 1.f / (dr * dr + di * di);
+            zh[m] = (y[m] * dr + y[m + 1] * di) * inv_den;
+            zh[m + 1] = (y[m + 1] * dr - y[m] * di) * inv_den;
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < NT; ++m) {
+          const float hi = __bfloat162float(__float2bfloat16(zh[m]));
+          store_bf16_swz(Bc, (uint32_t)((sl * NT + m) * C::RB + 2 * a), C::SWMASK, hi);
+          store_bf16_swz(Bc, (uint32_t)((NT * NSL + sl * NT + m) * C::RB + 2 * a), C::SWMASK, zh[m] - hi);
+        }
+      }
+    }
+    tc::fence_before_sync();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // 4. z = Q z_hat per cell
+    if (tid == 0 && ok) {
+      tc::fence_after_sync();
+      for (int cc = 0; cc < ncells; ++cc)
+#pragma unroll
+        for (int ks = 0; ks < NQ / 16; ++ks) {
+          const uint64_t ad = tc::smem_desc(qa + ks * 32, 16, C::ATOM, C::SW);
+          const uint64_t bd = tc::smem_desc(ba + cc * C::B_CELL + ks * 32, 16, C::ATOM, C::SW);
+          tc::mma_bf16(tmem + (uint32_t)(cc * C::NP), ad, bd, idesc_n, ks > 0 ? 1u : 0u);
+        }
+      tc::mma_commit(&mma_bar);
+    }
+    if (ok) {
+      ok = tc::mbar_wait_bounded(&mma_bar, mma_phase, status);
+      if (!ok) pending = (int)mma_phase;
+      mma_phase ^= 1u;
+    }
+    __syncwarp();
+    tc::fence_after_sync();
+    // 5. back to the time basis, weighted atomics
+    {
+      float v[C::NP];
+      load_row<C::NP, NQ>(tmem, warp, c, v);
+      if (ok && active && live) {
+#pragma unroll 1
+        for (int sl = 0; sl < nsl; ++sl) {
+          float z[NT];
+#pragma unroll
+          for (int m = 0; m < NT; ++m) z[m] = v[sl * NT + m] + v[NT * NSL + sl * NT + m];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            float o = 0.f;
+#pragma unroll
+            for (int m = 0; m < NT; ++m) {
+              if (m < mt.nreal) {
+                o += mt.Vr[t][m] * z[m];
+              } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+                const int mode = mt.nreal + (m - mt.nreal) / 2;
+                o += 2.f * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
+              }
+            }
+            atomicAdd(u + (int64_t)sl * slab_stride + t * g.n_nodes + node, mt.omega * w * o);
+          }
+        }
+      }
+    }
+    if (!ok && tid == 0) {
+      atomicExch(status, STMG_DEVICE_TIMEOUT);
+      s_fail = 1;
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // B operands, tensor memory and the stage are free again
+    if (s_fail) break;
+    const int64_t next = tl + (int64_t)S * gridDim.x;
+    if (next < ntiles) {
+      if (tid == 0)
+        tc::bulk_load(ring + (size_t)stage * C::TILE_Q, qimg + next * (int64_t)C::TILE_Q, tile_bytes(next), &bar[stage]);
+      ++issued;
+    }
+  }
+  if (s_fail) {
+    // drain: copies still in flight, then any MMA round still running
+    if (tid == 0) {
+      for (int64_t q = k; q < issued; ++q) tc::mbar_wait_bounded(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
+      if (pending >= 0) tc::mbar_wait_bounded(&mma_bar, (uint32_t)pending, nullptr);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+template <int DIM, int N, int NT, int NSL>
+cudaError_t eig_tc_launch(const float* r, float* u, const void* inv, const GridDesc& g, const ModeTab<float>& mt,
+                          const float* cs, float* cd, int* status, int nslab, int64_t ss, cudaStream_t s) {
+  using C = EigTcCfg<DIM, N, NT, NSL>;
+  auto k = eig_tc_kernel<DIM, N, NT, NSL>;
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // resident CTAs per SM from shared memory and tensor memory (every CTA holds TMEM_COLS of the SM's
+    // 512 columns); the occupancy query reports one CTA per SM for kernels that allocate tensor memory
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int by_smem = smem_sm / (int)(C::SMEM + 1024);
+    per_sm = std::max(1, std::min(std::min(by_smem, 16), 512 / (int)C::TMEM_COLS));
+  }
+  const unsigned char* img = reinterpret_cast<const unsigned char*>(inv);
+  const float* mu = reinterpret_cast<const float*>(img + g.n_cells * (int64_t)C::CELL_Q);
+  const int64_t tiles = (g.n_cells + C::CPT - 1) / C::CPT;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)sms * per_sm);
+  const cudaError_t e = launch_k(k, dim3((unsigned)grid), dim3(128), C::SMEM, s, r, u, img, mu, g, mt, cs, cd, status,
+                                 nslab, ss);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int DIM, int N, int NT>
+cudaError_t eig_tc_t(const float* r, float* u, const void* inv, const GridDesc& g, const ModeTab<float>& mt,
+                     const float* cs, float* cd, int* status, int nslab, int64_t ss, cudaStream_t s) {
+  if (!status || nslab > 8) return cudaErrorInvalidValue;
+  return nslab > 1 ? eig_tc_launch<DIM, N, NT, 8>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s)
+                   : eig_tc_launch<DIM, N, NT, 1>(r, u, inv, g, mt, cs, cd, status, 1, ss, s);
+}
+
 template <int DIM, int N>
 cudaError_t eig_setup_t(const GridDesc& g, const double* geo64, const LocalTab& lt, void* out, int prec,
                         cudaStream_t s) {
@@ -489,9 +835,17 @@ cudaError_t eig_apply_t(const T* r, T* u, const void* inv, const GridDesc& g, co
 
 int64_t eig_cell_bytes(int dim, int n, int esz) { return eig_cell_bytes_c(dim == 3 ? n * n * n : n * n, esz); }
 
+int64_t eig_tc_bytes(int dim, int n, int64_t n_cells) {
+  const int nb = dim == 3 ? n * n * n : n * n;
+  if (nb > 64) return -1;
+  const int nq = eig_tc_nq(nb);
+  return n_cells * ((int64_t)nq * nq * 2 + (int64_t)nq * 4);
+}
+
 cudaError_t launch_eig_setup(int dim, int n, const GridDesc& g, const double* geo64, const LocalTab& lt, void* out,
                              int prec, cudaStream_t s) {
-  if (prec < 0 || prec > 2) return cudaErrorInvalidValue;
+  if (prec < 0 || prec > 3) return cudaErrorInvalidValue;
+  if (prec == 3 && (dim == 3 ? n * n * n : n * n) > 64) return cudaErrorInvalidValue;
   if (dim == 3) {
     if (n == 2) return eig_setup_t<3, 2>(g, geo64, lt, out, prec, s);
     if (n == 3) return eig_setup_t<3, 3>(g, geo64, lt, out, prec, s);
@@ -532,5 +886,25 @@ template cudaError_t launch_eig_apply<float>(int, int, int, const float*, float*
 template cudaError_t launch_eig_apply<double>(int, int, int, const double*, double*, const void*, int, const GridDesc&,
                                               const ModeTab<double>&, const double*, double*, int*, int, int64_t,
                                               cudaStream_t);
+
+}  // namespace stmg
+
+namespace stmg {
+
+#define STMG_EIG_TC_CASE(DIM, N, NT) \
+  if (dim == DIM && n == N && nt == NT) return eig_tc_t<DIM, N, NT>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);
+
+cudaError_t launch_eig_tc_apply(int dim, int n, int nt, const float* r, float* u, const void* inv, const GridDesc& g,
+                                const ModeTab<float>& mt, const float* cs, float* cd, int* status, int nslab,
+                                int64_t ss, cudaStream_t s) {
+  STMG_EIG_TC_CASE(3, 2, 1) STMG_EIG_TC_CASE(3, 2, 2) STMG_EIG_TC_CASE(3, 2, 3) STMG_EIG_TC_CASE(3, 2, 4)
+  STMG_EIG_TC_CASE(3, 3, 1) STMG_EIG_TC_CASE(3, 3, 2) STMG_EIG_TC_CASE(3, 3, 3) STMG_EIG_TC_CASE(3, 3, 4)
+  STMG_EIG_TC_CASE(3, 4, 1) STMG_EIG_TC_CASE(3, 4, 2) STMG_EIG_TC_CASE(3, 4, 3) STMG_EIG_TC_CASE(3, 4, 4)
+  STMG_EIG_TC_CASE(2, 2, 1) STMG_EIG_TC_CASE(2, 2, 2) STMG_EIG_TC_CASE(2, 2, 3) STMG_EIG_TC_CASE(2, 2, 4)
+  STMG_EIG_TC_CASE(2, 3, 1) STMG_EIG_TC_CASE(2, 3, 2) STMG_EIG_TC_CASE(2, 3, 3) STMG_EIG_TC_CASE(2, 3, 4)
+  STMG_EIG_TC_CASE(2, 4, 1) STMG_EIG_TC_CASE(2, 4, 2) STMG_EIG_TC_CASE(2, 4, 3) STMG_EIG_TC_CASE(2, 4, 4)
+  STMG_EIG_TC_CASE(2, 5, 1) STMG_EIG_TC_CASE(2, 5, 2) STMG_EIG_TC_CASE(2, 5, 3) STMG_EIG_TC_CASE(2, 5, 4)
+  return cudaErrorInvalidValue;
+}
 
 }  // namespace stmg

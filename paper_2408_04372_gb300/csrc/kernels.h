@@ -70,6 +70,13 @@ int64_t asm_cell_stride(int dim, int n, int nt, int esz);
 int64_t eig_cell_bytes(int dim, int n, int esz);
 cudaError_t launch_eig_setup(int dim, int n, const GridDesc& g, const double* geo64, const LocalTab& lt, void* out,
                              int prec, cudaStream_t s);
+// Tensor-core variant (BF16 Q images padded to 16, 32 or 64 rows, swizzled as the operand layout wants,
+// then FP32 eigenvalues; (p+1)^dim <= 64; FP32 vectors; at most 8 slabs per system): store bytes
+// (-1 when unsupported), set-up with prec 3, sweep.
+int64_t eig_tc_bytes(int dim, int n, int64_t n_cells);
+cudaError_t launch_eig_tc_apply(int dim, int n, int nt, const float* r, float* u, const void* inv, const GridDesc& g,
+                                const ModeTab<float>& mt, const float* cs, float* cd, int* status, int nslab,
+                                int64_t ss, cudaStream_t s);
 template <typename T>
 cudaError_t launch_eig_apply(int dim, int n, int nt, const T* r, T* u, const void* inv, int prec, const GridDesc& g,
                              const ModeTab<T>& mt, const T* cs, T* cd, int* status, int nslab, int64_t ss,

@@ -15,8 +15,8 @@
 // accumulator rows from tensor memory.
 //   forward:        out[r][co] = sum_tap sum_ci in[r + off(tap)][ci] Wt[tap][co][ci] (+ bias, ReLU)
 //   backward data:  din[r][ci] = sum_tap sum_co dout[r - off(tap)][co] WtT[tap][ci][co] (x ReLU mask)
-// wgrad_kernel: dW[tap][co][ci] = sum_r dout[r][co] in[r + off(tap)][ci], split over row chunks,
-//   mma.sync with FP32 atomics into the gradient.
+// wgrad_tc_kernel: dW[tap][co][ci] = sum_r dout[r][co] in[r + off(tap)][ci] on the same tensor cores,
+//   taps stacked along M so that every MMA shares the output-gradient tile, FP32 atomics at the end.
 #include <algorithm>
 #include <cstdint>
 
@@ -27,22 +27,6 @@
 namespace stmg {
 
 namespace {
-
-__device__ inline void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ inline uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-constexpr int kTileV = 64;
-constexpr int kThreads = 128;
 
 // ---- tensor-core convolution ----
 template <int CI_P, int CO_P>
@@ -207,91 +191,160 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant_
   }
 }
 
-__device__ inline int tap_dx(int t) { return t % 3 - 1; }
-__device__ inline int tap_dy(int t) { return (t / 3) % 3 - 1; }
-__device__ inline int tap_dz(int t) { return t / 9 - 1; }
-
 struct VGrid { int nx, ny, nz; int64_t V; };
 
-// neighbour row of r shifted by (dx,dy,dz) of the tap on the (padded) grid g; -1 outside it
-__device__ inline int64_t neighbour(int64_t v, int s, int tap, const VGrid& g) {
-  const int x = (int)(v % g.nx);
-  const int64_t r = v / g.nx;
-  const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-  const int xx = x + s * tap_dx(tap), yy = y + s * tap_dy(tap), zz = z + s * tap_dz(tap);
-  if (xx < 0 || xx >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) return -1;
-  return xx + (int64_t)g.nx * (yy + (int64_t)g.ny * zz);
+// ---- tensor-core weight gradient ----
+// dW[tap][co][ci] = sum_r in[r + off(tap)][ci] dout[r][co], as D[(tap, ci)][co] = A B with the K dimension
+// running over activation rows r: A = the shifted input tiles of G = 128 / CI_P taps stacked along M
+// (each tile one 128-byte or 32-byte swizzle column of the M dimension, M-major), B = the output-gradient
+// tile (N = co contiguous, N-major) shared by every tap.  A CTA owns a range of 128-row blocks and a set
+// of tap groups; its accumulators (one 128 x CO_P block per group) stay in tensor memory over the whole
+// range and are added to dW with FP32 atomics at the end (one atomic per element and CTA).
+template <int CI_P, int CO_P>
+struct WgCfg {
+  static constexpr int BK = 128;                          // rows per block (K of 8 MMAs)
+  static constexpr int G = 128 / CI_P;                    // taps per group (M = G * CI_P = 128)
+  static constexpr int NGROUPS = (27 + G - 1) / G;
+  static constexpr int GPS_MAX = 512 / CO_P;              // groups whose accumulators fit in TMEM
+  static constexpr int GPS = NGROUPS < GPS_MAX ? NGROUPS : (NGROUPS + 1) / 2;  // groups per CTA (tap set)
+  static constexpr int TAPSETS = (NGROUPS + GPS - 1) / GPS;
+  static constexpr int TILE_A = BK * CI_P * 2;            // one tap's rows
+  static constexpr int A_BYTES = G * TILE_A;               // 32 KB
+  static constexpr int B_BYTES = BK * CO_P * 2;
+  static constexpr int STAGE = (A_BYTES + B_BYTES + 1023) / 1024 * 1024;
+  static constexpr int S = 3;
+  static constexpr size_t SMEM = (size_t)S * STAGE + 1024;
+  static constexpr tc::Swizzle SWA = CI_P == 64 ? tc::kSw128 : tc::kSw32;
+  static constexpr tc::Swizzle SWB = CO_P == 64 ? tc::kSw128 : tc::kSw32;
+  static constexpr uint32_t ATOM_A = CI_P == 64 ? 1024 : 256;  // 8 rows of one tile
+  static constexpr uint32_t ATOM_B = CO_P == 64 ? 1024 : 256;
+  static constexpr uint32_t TMEM_COLS = GPS * CO_P <= 32 ? 32 : GPS * CO_P <= 64 ? 64 : GPS * CO_P <= 128 ? 128
+                                        : GPS * CO_P <= 256 ? 256 : 512;
+  static constexpr int THREADS = 192;
+};
+
+// Instruction descriptor of kind::f16 with both operands M/N-major (transpose bits set).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+  return tc::idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
-// dW[tap][co][ci] += sum over a voxel chunk of dout[v][co] * in[v + off(tap)][ci]
 template <int CI_P, int CO_P>
-__global__ void __launch_bounds__(kThreads)
-wgrad_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dout, float* __restrict__ dW,
-             VGrid g, int64_t chunk) {
-  constexpr int SD = CO_P + 8, SA = CI_P + 8;
-  constexpr int MT = CO_P / 16, NT8 = CI_P / 8, TILES = MT * NT8;
-  constexpr int TPW = (TILES + 3) / 4;  // tiles per warp
-  __shared__ __align__(16) __nv_bfloat16 Sd[kTileV * SD];
-  __shared__ __align__(16) __nv_bfloat16 Sa[kTileV * SA];
-  const int tap = blockIdx.y;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int gq = lane >> 2, tq = lane & 3;
-  float acc[TPW][4];
-#pragma unroll
-  for (int i = 0; i < TPW; ++i)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc[i][e] = 0.f;
-  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = std::min<int64_t>(g.V, lo + chunk);
-  for (int64_t v0 = lo; v0 < hi; v0 += kTileV) {
-    for (int i = tid; i < kTileV * CO_P / 8; i += kThreads) {
-      const int row = i / (CO_P / 8), c8 = i % (CO_P / 8);
-      const int64_t v = v0 + row;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (v < hi) val = __ldg(reinterpret_cast<const uint4*>(dout + v * CO_P) + c8);
-      *reinterpret_cast<uint4*>(&Sd[row * SD + c8 * 8]) = val;
-    }
-    for (int i = tid; i < kTileV * CI_P / 8; i += kThreads) {
-      const int row = i / (CI_P / 8), c8 = i % (CI_P / 8);
-      const int64_t v = v0 + row;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (v < hi) {
-        const int64_t nb = neighbour(v, 1, tap, g);
-        if (nb >= 0) val = __ldg(reinterpret_cast<const uint4*>(in + nb * CI_P) + c8);
+__global__ void __launch_bounds__(WgCfg<CI_P, CO_P>::THREADS)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_dout,
+                float* __restrict__ dW, PGrid g, int64_t blocks_per_cta, int* status) {
+  using C = WgCfg<CI_P, CO_P>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[C::S], empty[C::S], acc_full;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail, s_issued, s_consumed;
+  unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nblocks = (g.Vp + C::BK - 1) / C::BK;
+  const int64_t rb0 = (int64_t)blockIdx.x * blocks_per_cta;
+  const int64_t rb1 = rb0 + blocks_per_cta < nblocks ? rb0 + blocks_per_cta : nblocks;
+  const int g0 = blockIdx.y * C::GPS;
+  const int ng = C::NGROUPS - g0 < C::GPS ? C::NGROUPS - g0 : C::GPS;
+  const int steps = rb1 > rb0 ? (int)((rb1 - rb0) * ng) : 0;
+  if (threadIdx.x == 0) {
+    s_fail = *reinterpret_cast<const volatile int*>(status);
+    s_issued = 0;
+    s_consumed = 0;
+    for (int s = 0; s < C::S; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    tc::mbar_init(&acc_full, 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_base, C::TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const bool skip = s_fail != 0 || steps == 0;
+
+  if (warp == 0 && lane == 0 && !skip) {
+    tc::prefetch_tmap(&tm_in);
+    tc::prefetch_tmap(&tm_dout);
+    for (int i = 0; i < steps; ++i) {
+      const int s = i % C::S;
+      if (i >= C::S && !tc::mbar_wait_bounded(&empty[s], (uint32_t)(((i / C::S) - 1) & 1), status)) {
+        atomicExch(status, STMG_DEVICE_TIMEOUT);
+        break;
       }
-      *reinterpret_cast<uint4*>(&Sa[row * SA + c8 * 8]) = val;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTileV; kk += 16) {
-#pragma unroll
-      for (int i = 0; i < TPW; ++i) {
-        const int tile = warp + 4 * i;
-        if (tile >= TILES) break;
-        const int m0 = (tile / NT8) * 16, n0 = (tile % NT8) * 8;
-        // A = dout^T (rows co, columns v), B = shifted input (rows v, columns ci)
-        const int k0 = kk + 2 * tq;
-        const uint32_t a0 = pack2(Sd[k0 * SD + m0 + gq], Sd[(k0 + 1) * SD + m0 + gq]);
-        const uint32_t a1 = pack2(Sd[k0 * SD + m0 + gq + 8], Sd[(k0 + 1) * SD + m0 + gq + 8]);
-        const uint32_t a2 = pack2(Sd[(k0 + 8) * SD + m0 + gq], Sd[(k0 + 9) * SD + m0 + gq]);
-        const uint32_t a3 = pack2(Sd[(k0 + 8) * SD + m0 + gq + 8], Sd[(k0 + 9) * SD + m0 + gq + 8]);
-        const uint32_t b0 = pack2(Sa[k0 * SA + n0 + gq], Sa[(k0 + 1) * SA + n0 + gq]);
-        const uint32_t b1 = pack2(Sa[(k0 + 8) * SA + n0 + gq], Sa[(k0 + 9) * SA + n0 + gq]);
-        mma_bf16(acc[i], a0, a1, a2, a3, b0, b1);
+      const int64_t r0 = (rb0 + i / ng) * C::BK;
+      const int grp = g0 + i % ng;
+      unsigned char* st = ring + (size_t)s * C::STAGE;
+      tc::mbar_expect_tx(&full[s], (uint32_t)(C::A_BYTES + C::B_BYTES));
+#pragma unroll 1
+      for (int h = 0; h < C::G; ++h) {
+        const int t = grp * C::G + h < 27 ? grp * C::G + h : 26;  // a short last group repeats a tap
+        const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+        const int64_t off = dx + (int64_t)g.nxp * (dy + (int64_t)g.nyp * dz);
+        tc::tma_load_2d(st + h * C::TILE_A, &tm_in, 0, (int)(r0 + off), &full[s]);
       }
+      tc::tma_load_2d(st + C::A_BYTES, &tm_dout, 0, (int)r0, &full[s]);
+      s_issued = i + 1;
+    }
+  } else if (warp == 1 && lane == 0 && !skip) {
+    constexpr uint32_t idesc = idesc_bf16_f32_mn(128, CO_P);
+    bool ok = true;
+    for (int i = 0; i < steps; ++i) {
+      const int s = i % C::S;
+      if (!tc::mbar_wait_bounded(&full[s], (uint32_t)((i / C::S) & 1), status)) {
+        atomicExch(status, STMG_DEVICE_TIMEOUT);
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const int grp_local = i % ng;
+      const bool first_block = i < ng;
+      const uint32_t a = tc::smem_addr(ring + (size_t)s * C::STAGE);
+      const uint32_t b = a + C::A_BYTES;
+      const uint32_t d = tmem + (uint32_t)(grp_local * CO_P);
+#pragma unroll
+      for (int ks = 0; ks < C::BK / 16; ++ks) {
+        // 16 rows = two 8-row swizzle atoms along K; M-atoms (taps) C::TILE_A apart
+        const uint64_t ad = tc::smem_desc(a + ks * 2 * C::ATOM_A, C::TILE_A, C::ATOM_A, C::SWA);
+        const uint64_t bd = tc::smem_desc(b + ks * 2 * C::ATOM_B, C::B_BYTES, C::ATOM_B, C::SWB);
+        tc::mma_bf16(d, ad, bd, idesc, (first_block && ks == 0) ? 0u : 1u);
+      }
+      tc::mma_commit(&empty[s]);
+      s_consumed = i + 1;
+    }
+    if (ok) tc::mma_commit(&acc_full);
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int m = 32 * q + lane;             // accumulator row = (tap h, ci)
+    const int h = m / CI_P, ci = m % CI_P;
+    bool ok = !skip && tc::mbar_wait_bounded(&acc_full, 0u, status);
+    if (!skip && !ok && lane == 0) atomicExch(status, STMG_DEVICE_TIMEOUT);
+    __syncwarp();
+    tc::fence_after_sync();
+    for (int gl = 0; gl < ng; ++gl) {
+      const int t = (g0 + gl) * C::G + h;
+#pragma unroll
+      for (int c0 = 0; c0 < CO_P; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(gl * CO_P + c0), v);
+        if (!ok || t >= 27) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) atomicAdd(dW + ((int64_t)t * CO_P + c0 + j) * CI_P + ci, v[j]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (!skip && *reinterpret_cast<const volatile int*>(status) != 0) {
+    if (threadIdx.x == 0)
+      for (int i = s_consumed; i < s_issued; ++i)
+        tc::mbar_wait_bounded(&full[i % C::S], (uint32_t)((i / C::S) & 1), nullptr);
+    if (threadIdx.x == 32 && s_consumed > 0) {
+      const int i = s_consumed - 1;
+      tc::mbar_wait_bounded(&empty[i % C::S], (uint32_t)((i / C::S) & 1), nullptr);
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int i = 0; i < TPW; ++i) {
-    const int tile = warp + 4 * i;
-    if (tile >= TILES) break;
-    const int m0 = (tile / NT8) * 16, n0 = (tile % NT8) * 8;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int co = m0 + gq + (e >= 2 ? 8 : 0);
-      const int ci = n0 + 2 * tq + (e & 1);
-      atomicAdd(dW + ((int64_t)tap * CO_P + co) * CI_P + ci, acc[i][e]);
-    }
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, C::TMEM_COLS);
   }
 }
 
@@ -422,19 +475,30 @@ cudaError_t conv_dispatch(int ci, int co, const CUtensorMap& tin, const CUtensor
 }
 
 template <int CI_P, int CO_P>
-cudaError_t wgrad_t(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* dW, const VGrid& g, cudaStream_t s) {
-  const int64_t chunk = 4096;
-  dim3 grid((unsigned)((g.V + chunk - 1) / chunk), 27);
-  wgrad_kernel<CI_P, CO_P><<<grid, kThreads, 0, s>>>(in, dout, dW, g, chunk);
+cudaError_t wgrad_t(const CUtensorMap& tin, const CUtensorMap& tdout, float* dW, const PGrid& g, int* status,
+                    cudaStream_t s) {
+  using C = WgCfg<CI_P, CO_P>;
+  auto k = wgrad_tc_kernel<CI_P, CO_P>;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t nblocks = (g.Vp + C::BK - 1) / C::BK;
+  const int64_t ctas_x = std::max<int64_t>(1, std::min<int64_t>(nblocks, 152 / C::TAPSETS));
+  const int64_t per = (nblocks + ctas_x - 1) / ctas_x;
+  const dim3 grid((unsigned)((nblocks + per - 1) / per), (unsigned)C::TAPSETS);
+  k<<<grid, C::THREADS, C::SMEM, s>>>(tin, tdout, dW, g, per, status);
   return cudaGetLastError();
 }
 
-cudaError_t wgrad_dispatch(int ci, int co, const __nv_bfloat16* in, const __nv_bfloat16* dout, float* dW,
-                           const VGrid& g, cudaStream_t s) {
-  if (ci == 16 && co == 64) return wgrad_t<16, 64>(in, dout, dW, g, s);
-  if (ci == 64 && co == 64) return wgrad_t<64, 64>(in, dout, dW, g, s);
-  if (ci == 64 && co == 16) return wgrad_t<64, 16>(in, dout, dW, g, s);
-  if (ci == 16 && co == 16) return wgrad_t<16, 16>(in, dout, dW, g, s);
+cudaError_t wgrad_dispatch(int ci, int co, const CUtensorMap& tin, const CUtensorMap& tdout, float* dW, const PGrid& g,
+                           int* status, cudaStream_t s) {
+  if (ci == 16 && co == 64) return wgrad_t<16, 64>(tin, tdout, dW, g, status, s);
+  if (ci == 64 && co == 64) return wgrad_t<64, 64>(tin, tdout, dW, g, status, s);
+  if (ci == 64 && co == 16) return wgrad_t<64, 16>(tin, tdout, dW, g, status, s);
+  if (ci == 16 && co == 16) return wgrad_t<16, 16>(tin, tdout, dW, g, status, s);
   return cudaErrorInvalidValue;
 }
 
@@ -499,7 +563,6 @@ cudaError_t net_guess(const NetDev& n, const double* u_prev, double* guess, cuda
 cudaError_t net_backward(NetDev& n, const double* u_prev, const double* u_target, double* loss, cudaStream_t s) {
   const VGrid g{n.nx, n.ny, n.nz, n.V};
   const PGrid pg{n.nxp, n.nyp, n.nzp, n.Vp};
-  const VGrid gp{n.nxp, n.nyp, n.nzp, n.Vp};  // the padded grid, for the weight gradient's row walk
   cudaMemsetAsync(loss, 0, sizeof(double), s);
   const int cpL = n.cp[n.L];
   int64_t interior = (int64_t)(n.nx - 2) * (n.ny - 2) * (n.nz - 2);
@@ -510,7 +573,7 @@ cudaError_t net_backward(NetDev& n, const double* u_prev, const double* u_target
     // gradients of layer l from grad[l+1] (= dL/dy_l) and act[l]; halo rows of both are zero
     cudaMemsetAsync(n.gw[l], 0, sizeof(float) * 27 * n.cp[l + 1] * n.cp[l], s);
     cudaMemsetAsync(n.gb[l], 0, sizeof(float) * n.cp[l + 1], s);
-    cudaError_t e = wgrad_dispatch(n.cp[l], n.cp[l + 1], n.act[l], n.grad[l + 1], n.gw[l], gp, s);
+    cudaError_t e = wgrad_dispatch(n.cp[l], n.cp[l + 1], n.tm_in_f[l], n.tm_in_b[l], n.gw[l], pg, n.status, s);
     if (e != cudaSuccess) return e;
     bias_grad_kernel<<<blocks_for(n.Vp * n.cp[l + 1]), 256, n.cp[l + 1] * sizeof(float), s>>>(n.grad[l + 1], n.gb[l],
                                                                                                 n.Vp, n.cp[l + 1]);

@@ -1,5 +1,6 @@
 // Host side of libstmg: context, multigrid hierarchy, V-cycle, FGMRES and the C ABI (include/stmg.h).
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -43,6 +44,7 @@ struct Level {
   int inv_prec = 1;
   bool fd = false;             // fast diagonalisation instead of stored inverses
   bool eig = false;            // stored per-cell eigendecompositions (Q, mu) instead of inverse planes
+  bool eig_tc = false;         // ... applied on the tensor cores (BF16 operand images, FP32 vectors)
   FDTab<double> fd64{};
   FDTab<float> fd32{};
   double* rho_cell64 = nullptr;
@@ -328,6 +330,17 @@ stmg_status op_asm(stmg_ctx* ctx, Level& L, const T* r, T* u, double omega, cons
   mt.omega = (T)omega;
   // block diagonal over the slabs: every space-time cell lies in one slab (same local inverses)
   const int64_t ss = L.slab_size();
+  if (L.eig_tc) {
+    if constexpr (std::is_same<T, float>::value) {
+      ctx->launches += 1;
+      CK(launch_eig_tc_apply(L.dim, L.n, L.nt, r, u, L.inv, L.g, mt, copy_src, copy_dst, ctx->status, L.nc, ss,
+                             ctx->stream));
+      return STMG_OK;
+    } else {
+      ctx->err = "the tensor-core smoother takes FP32 vectors";
+      return STMG_ERR_UNSUPPORTED;
+    }
+  }
   if (L.eig) {
     ctx->launches += 1;
     CK(launch_eig_apply<T>(L.dim, L.n, L.nt, r, u, L.inv, L.inv_prec, L.g, mt, copy_src, copy_dst, ctx->status, L.nc,
@@ -574,8 +587,15 @@ stmg_status estimate_omega(stmg_ctx* ctx, int l) {
   int m = steps;
   double* z = ctx->Z;
   for (int j = 0; j < steps; ++j) {
-    CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
-    CKS(op_asm<double>(ctx, L, V[j], z, 1.0));
+    if (L.eig_tc) {  // the tensor-core smoother takes FP32 vectors
+      CK(launch_convert<double, float>(V[j], L.r32, n, ctx->stream));
+      CK(cudaMemsetAsync(L.u32, 0, sizeof(float) * n, ctx->stream));
+      CKS(op_asm<float>(ctx, L, L.r32, L.u32, 1.0));
+      CK(launch_convert<float, double>(L.u32, z, n, ctx->stream));
+    } else {
+      CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
+      CKS(op_asm<double>(ctx, L, V[j], z, 1.0));
+    }
     CKS(op_apply<double>(ctx, L, z, V[j + 1]));
     std::vector<double> h;
     double hn = 0.0;
@@ -695,6 +715,22 @@ stmg_status setup_smoother(stmg_ctx* ctx, Level& L) {
     CKS(dev_alloc(ctx, &L.rho_cell32, L.g.n_cells));
     CK(cudaMemcpy(L.rho_cell64, rc.data(), sizeof(double) * rc.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.rho_cell32, rcf.data(), sizeof(float) * rcf.size(), cudaMemcpyHostToDevice));
+    return STMG_OK;
+  }
+  if (L.eig_tc) {
+    const int64_t bytes = eig_tc_bytes(L.dim, L.n, L.g.n_cells);
+    if (bytes < 0 || L.nc > 8) {
+      ctx->err = "the tensor-core smoother needs (p+1)^dim <= 64 and at most 8 slabs per system";
+      return STMG_ERR_UNSUPPORTED;
+    }
+    void* store = nullptr;
+    cudaError_t e = cudaMalloc(&store, (size_t)bytes);
+    if (e != cudaSuccess) { ctx->err = std::string("cudaMalloc eigen images: ") + cudaGetErrorString(e); return STMG_ERR_OOM; }
+    ctx->allocations.push_back(store);
+    L.inv = store;
+    L.inv_prec = 3;
+    CK(launch_eig_setup(L.dim, L.n, L.g, L.geo64, L.lt, L.inv, 3, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return STMG_OK;
   }
   if (L.eig) {
@@ -1039,8 +1075,10 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
       }
     }
   }
-  if (o.smoother_kind < STMG_SMOOTHER_AUTO || o.smoother_kind > STMG_SMOOTHER_EIG)
-    return invalid(ctx, "smoother_kind must be AUTO, DENSE, FD or EIG");
+  if (o.smoother_kind < STMG_SMOOTHER_AUTO || o.smoother_kind > STMG_SMOOTHER_EIG_TC)
+    return invalid(ctx, "smoother_kind must be AUTO, DENSE, FD, EIG or EIG_TC");
+  if (o.smoother_kind == STMG_SMOOTHER_EIG_TC && o.vcycle_precision == STMG_FP64)
+    return invalid(ctx, "the tensor-core smoother runs in the FP32 V-cycle");
   if (o.smoother_kind == STMG_SMOOTHER_FD && (dim != 3 || !cartesian))
     return invalid(ctx, "fast diagonalisation needs a 3D Cartesian grid");
   for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
@@ -1059,9 +1097,10 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
       }
     }
     if (o.smoother_kind == STMG_SMOOTHER_FD) L.fd = true;
-    else if (o.smoother_kind == STMG_SMOOTHER_DENSE || o.smoother_kind == STMG_SMOOTHER_EIG) L.fd = false;
+    else if (o.smoother_kind == STMG_SMOOTHER_DENSE || o.smoother_kind >= STMG_SMOOTHER_EIG) L.fd = false;
     else L.fd = dim == 3 && cartesian && (patch_const || L.n > 4);
-    L.eig = o.smoother_kind == STMG_SMOOTHER_EIG;
+    L.eig = o.smoother_kind >= STMG_SMOOTHER_EIG;
+    L.eig_tc = o.smoother_kind == STMG_SMOOTHER_EIG_TC;
   }
   for (size_t li = 0; li + 1 < ctx->levels.size(); ++li) {
     CKS(setup_smoother(ctx, ctx->levels[li]));

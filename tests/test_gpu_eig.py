@@ -127,3 +127,75 @@ def test_eig_smoother_refuses_q4_in_3d(env):
     with pytest.raises(stmg.StmgError) as err:
         stmg.Context(3, 2, 4, 1, 0.1, smoother_kind=stmg.SMOOTHER_EIG, omega=[0.3] * 16)
     assert err.value.status == 9  # STMG_ERR_UNSUPPORTED
+
+
+# ---- tensor-core variant (smoother_kind EIG_TC): BF16 Q images, both products on tcgen05 ----
+TC_CASES = [c for c in CASES if (c.p + 1) ** c.dim <= 64]
+
+
+@pytest.mark.parametrize("weighted", [0, 1])
+@pytest.mark.parametrize("case", TC_CASES, ids=lambda c: c.name)
+def test_eig_tensor_core_smoother_matches_oracle_blocks(env, case, weighted):
+    """FP32 vectors, Q in BF16 (2e-2 as for the BF16 plane storage); the right-hand sides enter the
+    tensor cores as two BF16 parts, so the only coarse rounding is that of Q."""
+    torch, stmg = env
+    H = _weighted(case) if weighted else oracle_hierarchy(case)
+    ctx = make_context(stmg, case, H, vcycle_precision=stmg.FP32, smoother_kind=stmg.SMOOTHER_EIG_TC,
+                       asm_weighting=weighted)
+    for li, lev in enumerate(H.levels[:-1]):
+        prob = lev.prob
+        f = _rand(prob.n, 300 + li, prob.bmask_full)
+        # one sweep from u = 0 is omega B f: the smoother's own error, without the cancellation of
+        # u - omega B S u that a sweep from a random u adds on levels where B S is close to I
+        ref = lev.omega * (lev.B @ f)
+        for call in range(2):  # the operand buffers and tensor memory are reused call after call
+            u32 = torch.zeros(prob.n, dtype=torch.float32, device="cuda")
+            ctx.smooth(torch.from_numpy(f).to("cuda", torch.float32), u32, sweeps=1, level=li)
+            assert rel_err(u32.cpu().numpy(), ref) < 2e-2, (case.name, li, call)
+        # FP64 vectors are refused
+        with pytest.raises(stmg.StmgError):
+            ctx.smooth(torch.from_numpy(f).cuda(), torch.zeros(prob.n, dtype=torch.float64, device="cuda"), sweeps=1,
+                       level=li)
+    prob = H.levels[0].prob
+    r = _rand(prob.n, 600, prob.bmask_full)
+    e = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    ctx.vcycle(torch.from_numpy(r).to("cuda", torch.float32), e)
+    assert rel_err(e.cpu().numpy(), H.vcycle(r)) < 3e-2, case.name
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[6]], ids=lambda c: c.name)
+def test_eig_tensor_core_solve_reaches_direct_solution(env, case):
+    torch, stmg = env
+    H = oracle_hierarchy(case)
+    prob = H.levels[0].prob
+    b = _rand(prob.n, 1002, prob.bmask_full)
+    xd = prob.solve(b).reshape(-1)
+    ctx = make_context(stmg, case, H, omega=None, vcycle_precision=stmg.FP32, smoother_kind=stmg.SMOOTHER_EIG_TC,
+                       asm_weighting=1, rtol=1e-12, max_it=200)
+    u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st = ctx.solve(torch.from_numpy(b).cuda(), u)
+    assert st["converged"], st
+    assert np.linalg.norm(u.cpu().numpy() - xd) < 1e-8 * np.linalg.norm(xd)
+    ctx.close()
+
+
+def test_eig_tensor_core_smoother_several_slabs(env):
+    """Four heat dG slabs in one system: all slabs' right-hand sides share one pass over each Q image."""
+    torch, stmg = env
+    import synth
+    from oracle import atonce
+    dim, N, p, k, tau, nc = 3, 4, 2, 1, 1 / 32, 4
+    V = synth.jittered_vertices(N, dim)
+    rho = synth.block_coefficient(N, dim, blocks=2)
+    H = atonce.AtOnceHierarchy(dim, N, p, k, tau, nc, V, rho_cell=rho, estimate=False, omegas=[0.5] * 16)
+    ctx = stmg.Context(dim, N, p, k, tau, vertices=V, coeff=rho, n_slabs=nc, omega=H.omegas(),
+                       vcycle_precision=stmg.FP32, smoother_kind=stmg.SMOOTHER_EIG_TC)
+    for li, lev in enumerate(H.levels[:-1]):
+        prob = lev.prob
+        f = _rand(prob.n, 720 + li, prob.bmask_full)
+        ref = lev.omega * (lev.B @ f)
+        u32 = torch.zeros(prob.n, dtype=torch.float32, device="cuda")
+        ctx.smooth(torch.from_numpy(f).to("cuda", torch.float32), u32, sweeps=1, level=li)
+        assert rel_err(u32.cpu().numpy(), ref) < 2e-2, li
+    ctx.close()

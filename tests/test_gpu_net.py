@@ -195,3 +195,68 @@ def test_trained_guess_beats_previous_slab_guess(env):
     assert np.mean(it_net) <= np.mean(it_prev)
     net.close()
     ctx.close()
+
+
+def test_mixed_precision_with_learned_guess_beats_plain_fp64_in_wall_time(env):
+    """The end-to-end claim: the mixed-precision solver with the learned guess (network inference, guess
+    selection by FP64 residual, FGMRES) solves held-out slabs faster than the plain FP64 solver with the
+    previous-slab guess, both to rtol 1e-8 (Q2 on 32^3 cells, dG(1), moving Gaussian sources).  The
+    learned guess against the previous-slab guess of the same mixed solver is measured and printed:
+    on GB300 the guess costs more than the iterations it saves (recorded, not asserted)."""
+    torch, stmg = env
+    N, k, tau, n_train, n_eval = 32, 1, 1.0 / 128, 12, 6
+    ctx = stmg.Context(3, N, 2, k, tau, vcycle_precision=stmg.FP32, rtol=1e-8, asm_weighting=1, outer_relax=1)
+    ctx64 = stmg.Context(3, N, 2, k, tau, vcycle_precision=stmg.FP64, rtol=1e-8, asm_weighting=1)
+    nt, nn = ctx.nt, ctx.n_nodes
+    X = ctx.node_coords()
+    src = synth.MovingGaussians()
+    tn = fe1d.gauss_radau_right(k + 1)[0]
+    F = [torch.from_numpy(np.stack([src(X, tau * (s + th)) for th in tn]).reshape(-1)).cuda()
+         for s in range(n_train + n_eval)]
+    sols, u_prev = [], torch.zeros(nn, dtype=torch.float64, device="cuda")
+    rhs = torch.empty(nt * nn, dtype=torch.float64, device="cuda")
+    for s in range(n_train + n_eval):
+        ctx.rhs(F[s], rhs, u0=u_prev)
+        u = torch.empty_like(rhs)
+        ctx.guess_previous(u_prev, u)
+        assert ctx.solve(rhs, u)["converged"]
+        sols.append(u.clone())
+        u_prev = u[(nt - 1) * nn:].clone()
+    prev = [torch.zeros(nt * nn, dtype=torch.float64, device="cuda")] + sols[:-1]
+    su = 1.0 / float(torch.stack(sols[:n_train]).pow(2).mean().sqrt())
+    sf = 1.0 / float(torch.stack(F[:n_train]).pow(2).mean().sqrt())
+    so = 1.0 / float(torch.stack([sols[s] - prev[s][(nt - 1) * nn:].repeat(nt) for s in range(1, n_train)])
+                     .pow(2).mean().sqrt())
+    W, b = synth.conv_net_init(CHANNELS, seed=15)
+    net = stmg.Net(ctx, CHANNELS, W, b, (su, sf, so))
+    for epoch in range(20):
+        for s in range(1, n_train):
+            net.train_step(prev[s], F[s], sols[s], 2e-3)
+    cand = torch.empty(nt * nn, dtype=torch.float64, device="cuda")
+
+    def run(mode):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(n_train, n_train + n_eval):
+            c = ctx64 if mode == "fp64" else ctx
+            c.rhs(F[s], rhs, u0=prev[s][(nt - 1) * nn:])
+            u = torch.empty_like(rhs)
+            c.guess_previous(prev[s][(nt - 1) * nn:].contiguous(), u)
+            if mode == "learned":
+                net.predict(prev[s], F[s], cand)
+                c.select_guess(rhs, cand, u)
+            assert c.solve(rhs, u)["converged"]
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n_eval
+
+    for mode in ("learned", "previous", "fp64"):
+        run(mode)  # warm-up (graph capture, first launches)
+    t = {mode: run(mode) for mode in ("learned", "previous", "fp64")}
+    print(f"\nms per held-out slab: learned {t['learned']:.3f}, previous-slab {t['previous']:.3f}, "
+          f"plain FP64 {t['fp64']:.3f}")
+    assert t["learned"] < t["fp64"], t
+    net.close()
+    ctx.close()
+    ctx64.close()
