@@ -194,12 +194,50 @@ def run_oracle_full(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_net_only(args):
+    """Profiling helper for the learned guess's tensor-core kernels: the learned-guess workload's grid
+    (Q2 on 48^3 cells, dG(1): 97^3 nodes), the 4-60-60-60-2 network with seeded weights, `steps`
+    inferences and training steps on seeded inputs; prints the mean times."""
+    import torch
+    import paper_2408_04372_gb300 as stmg
+    torch.cuda.set_device(0)
+    N = args.n_cells if args.n_cells != 32 else 48
+    ctx = stmg.Context(3, N, 2, 1, 1.0 / 256, omega=[0.2] * 8, vcycle_precision=stmg.FP32)
+    nt, nn = ctx.nt, ctx.n_nodes
+    channels = (2 * nt, NET_CHANNELS_HIDDEN, NET_CHANNELS_HIDDEN, NET_CHANNELS_HIDDEN, nt)
+    W, b = synth.conv_net_init(channels, seed=15)
+    net = stmg.Net(ctx, channels, W, b, (1.0, 1.0, 1.0))
+    up = torch.from_numpy(synth.random_vector(nt * nn, seed=31)).cuda()
+    f = torch.from_numpy(synth.random_vector(nt * nn, seed=32)).cuda()
+    g = torch.empty_like(up)
+    times = {}
+    for name, fn in (("predict", lambda: net.predict(up, f, g)), ("train_step", lambda: net.train_step(up, f, up, 1e-4))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+    voxels = (N * 2 + 1) ** 3
+    flops = 2 * 27 * voxels * sum(channels[l] * channels[l + 1] for l in range(len(channels) - 1))
+    times["inference_tflops"] = flops / (times["predict_ms"] * 1e-3) / 1e12
+    print(json.dumps({"workload": f"heat3d_q2_dg1_{N}cubed learned guess network", "channels": list(channels), **times}))
+    net.close()
+    ctx.close()
+    return 0
+
+
 def run_kernel_only(args):
     """Profiling helper: builds the workload's hierarchy with fixed relaxation weights (no Arnoldi)
     and launches one kernel a few times; used for ncu captures of a single kernel."""
     import torch
     import paper_2408_04372_gb300 as stmg
     torch.cuda.set_device(0)
+    if args.only_kernel == "net":
+        return run_net_only(args)
     wl = workload(args.n_cells)
     ctx = stmg.Context(3, wl["N"], wl["p"], wl["k"], wl["tau"], vertices=wl["vertices"], coeff=wl["rho"],
                        vcycle_precision=stmg.FP32, omega=[0.2] * 16, smoother_kind=smoother_kind(stmg, args),
@@ -1122,7 +1160,8 @@ def main():
     ap.add_argument("--smoother", default="dense", choices=["auto", "dense", "eig", "eig_tc"],
                     help="local solver of the Schwarz smoother: stored inverse planes (dense) or per-cell "
                          "eigendecompositions (eig)")
-    ap.add_argument("--only-kernel", default=None, choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64"],
+    ap.add_argument("--only-kernel", default=None,
+                    choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64", "net"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
     ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")
     ap.add_argument("--asm-weighting", type=int, default=1, choices=[0, 1],

@@ -487,13 +487,20 @@ struct EigTcCfg {
   static constexpr uint32_t SWMASK = NQ == 16 ? 1u : NQ == 32 ? 3u : 7u;
   static constexpr int CELL_Q = NQ * NQ * 2;
   static constexpr int TILE_Q = CPT * CELL_Q;
-  static constexpr int NR = 2 * NT * NSL;                 // operand rows: two parts x slabs x modes
-  static constexpr int NP = (NR + 15) / 16 * 16;          // N of the MMAs
+  // right-hand sides of one cell: slabs x time modes, each as a high and a low BF16 part for one slab
+  // (16 rows either way), the high part alone for several slabs (precision of Q itself, 8 bits)
+  static constexpr int PARTS = NSL == 1 ? 2 : 1;
+  static constexpr int NR = PARTS * NT * NSL;
+  // N of the MMAs and the column stride of the cells' accumulators in tensor memory: a power of two
+  // (16, 32 or 64), so that every accumulator starts on a multiple of its own width
+  static constexpr int NP = NR <= 16 ? 16 : NR <= 32 ? 32 : 64;
   static constexpr int B_CELL = NP * RB;
   static constexpr int B_BYTES = CPT * B_CELL;
   static constexpr int S = 2;
   static constexpr size_t SMEM = (size_t)S * TILE_Q + B_BYTES + 1024;
-  static constexpr uint32_t TMEM_COLS = CPT * NP <= 32 ? 32 : CPT * NP <= 64 ? 64 : CPT * NP <= 128 ? 128 : 256;
+  static constexpr uint32_t TMEM_COLS = CPT * NP <= 32 ? 32 : CPT * NP <= 64 ? 64 : CPT * NP <= 128 ? 128
+                                        : CPT * NP <= 256 ? 256 : 512;
+  static_assert(NR <= 64, "at most 64 right-hand-side rows per cell");
 };
 
 // This thread's accumulator row (TMEM lane = thread index) in the column block of its cell c.  The load
@@ -532,7 +539,7 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[S], mma_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ int s_fail, s_ok;
   unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* bops = ring + (size_t)S * C::TILE_Q;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -593,17 +600,23 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
       if (mt.weighted) w = node_weight<float>(gx, gy, gz, DIM, g.p);
     }
     if (cell < g.n_cells) muj = __ldg(mu_all + cell * NQ + a);
-    // 1. modal residual of every slab (as two BF16 parts) into B_c; side job copy
+    // 1. modal residual of every slab into B_c (all slabs' loads issued before the first use); side job
+    float rr[NSL][NT];
+#pragma unroll
+    for (int sl = 0; sl < NSL; ++sl)
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        rr[sl][t] = (sl < nsl && live) ? r[(int64_t)sl * slab_stride + t * g.n_nodes + node] : 0.f;
+    if (copy_dst && active) {
 #pragma unroll 1
-    for (int sl = 0; sl < nsl; ++sl) {
-      const int64_t so = (int64_t)sl * slab_stride;
-      float rr[NT];
+      for (int sl = 0; sl < nsl; ++sl)
 #pragma unroll
-      for (int t = 0; t < NT; ++t) rr[t] = live ? r[so + t * g.n_nodes + node] : 0.f;
-      if (copy_dst && active) {
+        for (int t = 0; t < NT; ++t)
+          copy_dst[(int64_t)sl * slab_stride + t * g.n_nodes + node] = copy_src[(int64_t)sl * slab_stride + t * g.n_nodes + node];
+    }
 #pragma unroll
-        for (int t = 0; t < NT; ++t) copy_dst[so + t * g.n_nodes + node] = copy_src[so + t * g.n_nodes + node];
-      }
+    for (int sl = 0; sl < NSL; ++sl) {
+      if (sl >= nsl) break;
 #pragma unroll
       for (int m = 0; m < NT; ++m) {
         const bool is_real = m < mt.nreal;
@@ -611,10 +624,10 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
         const bool im_part = !is_real && ((m - mt.nreal) & 1);
         float v = 0.f;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[t];
+        for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[sl][t];
         const float hi = __bfloat162float(__float2bfloat16(v));
         store_bf16_swz(Bc, (uint32_t)((sl * NT + m) * C::RB + 2 * a), C::SWMASK, hi);
-        store_bf16_swz(Bc, (uint32_t)((NT * NSL + sl * NT + m) * C::RB + 2 * a), C::SWMASK, v - hi);
+        if (C::PARTS == 2) store_bf16_swz(Bc, (uint32_t)((NT * NSL + sl * NT + m) * C::RB + 2 * a), C::SWMASK, v - hi);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -638,20 +651,23 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
         }
       tc::mma_commit(&mma_bar);
     }
-    bool ok = tc::mbar_wait_bounded(&mma_bar, mma_phase, status);
+    // one thread waits for the MMA round (the others sleep at the barrier instead of polling)
+    if (tid == 0) s_ok = tc::mbar_wait_bounded(&mma_bar, mma_phase, status) ? 1 : 0;
+    __syncthreads();
+    bool ok = s_ok != 0;
     if (!ok) pending = (int)mma_phase;
     mma_phase ^= 1u;
-    __syncwarp();
     tc::fence_after_sync();
     // 3. z_hat = y / (lambda + mu_a) into B_c
     {
       float v[C::NP];
       load_row<C::NP, NQ>(tmem, warp, c, v);
-#pragma unroll 1
-      for (int sl = 0; sl < nsl; ++sl) {
+#pragma unroll
+      for (int sl = 0; sl < NSL; ++sl) {
+        if (sl >= nsl) break;
         float y[NT];
 #pragma unroll
-        for (int m = 0; m < NT; ++m) y[m] = v[sl * NT + m] + v[NT * NSL + sl * NT + m];
+        for (int m = 0; m < NT; ++m) y[m] = v[sl * NT + m] + (C::PARTS == 2 ? v[NT * NSL + sl * NT + m] : 0.f);
         float zh[NT];
 #pragma unroll
         for (int m = 0; m < NT; ++m) {
@@ -669,7 +685,8 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
         for (int m = 0; m < NT; ++m) {
           const float hi = __bfloat162float(__float2bfloat16(zh[m]));
           store_bf16_swz(Bc, (uint32_t)((sl * NT + m) * C::RB + 2 * a), C::SWMASK, hi);
-          store_bf16_swz(Bc, (uint32_t)((NT * NSL + sl * NT + m) * C::RB + 2 * a), C::SWMASK, zh[m] - hi);
+          if (C::PARTS == 2)
+            store_bf16_swz(Bc, (uint32_t)((NT * NSL + sl * NT + m) * C::RB + 2 * a), C::SWMASK, zh[m] - hi);
         }
       }
     }
@@ -689,22 +706,24 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
       tc::mma_commit(&mma_bar);
     }
     if (ok) {
-      ok = tc::mbar_wait_bounded(&mma_bar, mma_phase, status);
+      if (tid == 0) s_ok = tc::mbar_wait_bounded(&mma_bar, mma_phase, status) ? 1 : 0;
+      __syncthreads();
+      ok = s_ok != 0;
       if (!ok) pending = (int)mma_phase;
       mma_phase ^= 1u;
     }
-    __syncwarp();
     tc::fence_after_sync();
     // 5. back to the time basis, weighted atomics
     {
       float v[C::NP];
       load_row<C::NP, NQ>(tmem, warp, c, v);
       if (ok && active && live) {
-#pragma unroll 1
-        for (int sl = 0; sl < nsl; ++sl) {
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) {
+          if (sl >= nsl) break;
           float z[NT];
 #pragma unroll
-          for (int m = 0; m < NT; ++m) z[m] = v[sl * NT + m] + v[NT * NSL + sl * NT + m];
+          for (int m = 0; m < NT; ++m) z[m] = v[sl * NT + m] + (C::PARTS == 2 ? v[NT * NSL + sl * NT + m] : 0.f);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
             float o = 0.f;

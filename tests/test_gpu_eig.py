@@ -180,12 +180,14 @@ def test_eig_tensor_core_solve_reaches_direct_solution(env, case):
     ctx.close()
 
 
-def test_eig_tensor_core_smoother_several_slabs(env):
-    """Four heat dG slabs in one system: all slabs' right-hand sides share one pass over each Q image."""
+@pytest.mark.parametrize("k,nc", [(1, 4), (2, 8)])
+def test_eig_tensor_core_smoother_several_slabs(env, k, nc):
+    """Heat dG slabs in one system (4 slabs of dG(1), 8 of dG(2): 16 and 48 right-hand-side rows per cell):
+    all slabs' right-hand sides share one pass over each Q image."""
     torch, stmg = env
     import synth
     from oracle import atonce
-    dim, N, p, k, tau, nc = 3, 4, 2, 1, 1 / 32, 4
+    dim, N, p, tau = 3, 4, 2, 1 / 32
     V = synth.jittered_vertices(N, dim)
     rho = synth.block_coefficient(N, dim, blocks=2)
     H = atonce.AtOnceHierarchy(dim, N, p, k, tau, nc, V, rho_cell=rho, estimate=False, omegas=[0.5] * 16)
