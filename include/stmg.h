@@ -88,8 +88,10 @@ typedef struct {
   const double* vertices;  /* host, may be NULL */
 } stmg_mesh;
 
-/* The slab problem (Section 2).  p: spatial degree 1..4; k: time degree
- * (dG: 0..3, N_t = k+1; cGP: 1..4, N_t = k); tau: slab length.
+/* The slab problem (Section 2).  p: spatial degree 1..4 (1..5 in 3D, where Q5 levels need the fast
+ * diagonalisation, i.e. a Cartesian grid with a constant coefficient); k: time degree
+ * (dG: 0..4, N_t = k+1; cGP: 1..5, N_t = k; N_t = 5 only in 3D with the fast diagonalisation);
+ * tau: slab length.
  * n_slabs (0 = 1): consecutive slabs solved as one system, heat equation with dG
  * only (eq. heat-cg-dg-at-once: the slab operator S on the block diagonal, the
  * coupling -B = -1 (x) alpha (x) M_h to the previous slab's last time DoF below it).

@@ -48,6 +48,8 @@ cudaError_t launch_apply(int dim, int n, int nt, const T* x, T* y, const T* geo,
   STMG_APPLY_CASE(3, 3, 1) STMG_APPLY_CASE(3, 3, 2) STMG_APPLY_CASE(3, 3, 3) STMG_APPLY_CASE(3, 3, 4)
   STMG_APPLY_CASE(3, 4, 1) STMG_APPLY_CASE(3, 4, 2) STMG_APPLY_CASE(3, 4, 3) STMG_APPLY_CASE(3, 4, 4)
   STMG_APPLY_CASE(3, 5, 1) STMG_APPLY_CASE(3, 5, 2) STMG_APPLY_CASE(3, 5, 3) STMG_APPLY_CASE(3, 5, 4)
+  STMG_APPLY_CASE(3, 2, 5) STMG_APPLY_CASE(3, 3, 5) STMG_APPLY_CASE(3, 4, 5) STMG_APPLY_CASE(3, 5, 5)
+  STMG_APPLY_CASE(3, 6, 1) STMG_APPLY_CASE(3, 6, 5)
   STMG_APPLY_CASE(2, 2, 1) STMG_APPLY_CASE(2, 2, 2) STMG_APPLY_CASE(2, 2, 3) STMG_APPLY_CASE(2, 2, 4)
   STMG_APPLY_CASE(2, 3, 1) STMG_APPLY_CASE(2, 3, 2) STMG_APPLY_CASE(2, 3, 3) STMG_APPLY_CASE(2, 3, 4)
   STMG_APPLY_CASE(2, 4, 1) STMG_APPLY_CASE(2, 4, 2) STMG_APPLY_CASE(2, 4, 3) STMG_APPLY_CASE(2, 4, 4)
@@ -64,6 +66,8 @@ cudaError_t launch_mass_apply(int dim, int n, int nt, const double* x, double* y
   STMG_MASS_CASE(3, 3, 1) STMG_MASS_CASE(3, 3, 2) STMG_MASS_CASE(3, 3, 3) STMG_MASS_CASE(3, 3, 4)
   STMG_MASS_CASE(3, 4, 1) STMG_MASS_CASE(3, 4, 2) STMG_MASS_CASE(3, 4, 3) STMG_MASS_CASE(3, 4, 4)
   STMG_MASS_CASE(3, 5, 1) STMG_MASS_CASE(3, 5, 2) STMG_MASS_CASE(3, 5, 3) STMG_MASS_CASE(3, 5, 4)
+  STMG_MASS_CASE(3, 2, 5) STMG_MASS_CASE(3, 3, 5) STMG_MASS_CASE(3, 4, 5) STMG_MASS_CASE(3, 5, 5)
+  STMG_MASS_CASE(3, 6, 1) STMG_MASS_CASE(3, 6, 5)
   STMG_MASS_CASE(2, 2, 1) STMG_MASS_CASE(2, 2, 2) STMG_MASS_CASE(2, 2, 3) STMG_MASS_CASE(2, 2, 4)
   STMG_MASS_CASE(2, 3, 1) STMG_MASS_CASE(2, 3, 2) STMG_MASS_CASE(2, 3, 3) STMG_MASS_CASE(2, 3, 4)
   STMG_MASS_CASE(2, 4, 1) STMG_MASS_CASE(2, 4, 2) STMG_MASS_CASE(2, 4, 3) STMG_MASS_CASE(2, 4, 4)
@@ -80,6 +84,7 @@ cudaError_t launch_apply_f2d(int dim, int n, int nt, const float* x, double* y, 
   STMG_F2D_CASE(3, 3, 1) STMG_F2D_CASE(3, 3, 2) STMG_F2D_CASE(3, 3, 3) STMG_F2D_CASE(3, 3, 4)
   STMG_F2D_CASE(3, 4, 1) STMG_F2D_CASE(3, 4, 2) STMG_F2D_CASE(3, 4, 3) STMG_F2D_CASE(3, 4, 4)
   STMG_F2D_CASE(3, 5, 1) STMG_F2D_CASE(3, 5, 2) STMG_F2D_CASE(3, 5, 3) STMG_F2D_CASE(3, 5, 4)
+  STMG_F2D_CASE(3, 2, 5) STMG_F2D_CASE(3, 3, 5) STMG_F2D_CASE(3, 4, 5) STMG_F2D_CASE(3, 5, 5) STMG_F2D_CASE(3, 6, 5)
   STMG_F2D_CASE(2, 2, 1) STMG_F2D_CASE(2, 2, 2) STMG_F2D_CASE(2, 2, 3) STMG_F2D_CASE(2, 2, 4)
   STMG_F2D_CASE(2, 3, 1) STMG_F2D_CASE(2, 3, 2) STMG_F2D_CASE(2, 3, 3) STMG_F2D_CASE(2, 3, 4)
   STMG_F2D_CASE(2, 4, 1) STMG_F2D_CASE(2, 4, 2) STMG_F2D_CASE(2, 4, 3) STMG_F2D_CASE(2, 4, 4)

@@ -17,6 +17,7 @@ cudaError_t launch_apply_df_d(int dim, int n, int nt, const double* x, double* y
   STMG_APPLY_CASE(3, 3, 1) STMG_APPLY_CASE(3, 3, 2) STMG_APPLY_CASE(3, 3, 3) STMG_APPLY_CASE(3, 3, 4)
   STMG_APPLY_CASE(3, 4, 1) STMG_APPLY_CASE(3, 4, 2) STMG_APPLY_CASE(3, 4, 3) STMG_APPLY_CASE(3, 4, 4)
   STMG_APPLY_CASE(3, 5, 1) STMG_APPLY_CASE(3, 5, 2) STMG_APPLY_CASE(3, 5, 3) STMG_APPLY_CASE(3, 5, 4)
+  STMG_APPLY_CASE(3, 2, 5) STMG_APPLY_CASE(3, 3, 5) STMG_APPLY_CASE(3, 4, 5) STMG_APPLY_CASE(3, 5, 5) STMG_APPLY_CASE(3, 6, 5)
   STMG_APPLY_CASE(2, 2, 1) STMG_APPLY_CASE(2, 2, 2) STMG_APPLY_CASE(2, 2, 3) STMG_APPLY_CASE(2, 2, 4)
   STMG_APPLY_CASE(2, 3, 1) STMG_APPLY_CASE(2, 3, 2) STMG_APPLY_CASE(2, 3, 3) STMG_APPLY_CASE(2, 3, 4)
   STMG_APPLY_CASE(2, 4, 1) STMG_APPLY_CASE(2, 4, 2) STMG_APPLY_CASE(2, 4, 3) STMG_APPLY_CASE(2, 4, 4)
@@ -33,6 +34,8 @@ cudaError_t launch_mass_apply_df(int dim, int n, int nt, const double* x, double
   STMG_MASS_DFD_CASE(3, 3, 1) STMG_MASS_DFD_CASE(3, 3, 2) STMG_MASS_DFD_CASE(3, 3, 3) STMG_MASS_DFD_CASE(3, 3, 4)
   STMG_MASS_DFD_CASE(3, 4, 1) STMG_MASS_DFD_CASE(3, 4, 2) STMG_MASS_DFD_CASE(3, 4, 3) STMG_MASS_DFD_CASE(3, 4, 4)
   STMG_MASS_DFD_CASE(3, 5, 1) STMG_MASS_DFD_CASE(3, 5, 2) STMG_MASS_DFD_CASE(3, 5, 3) STMG_MASS_DFD_CASE(3, 5, 4)
+  STMG_MASS_DFD_CASE(3, 2, 5) STMG_MASS_DFD_CASE(3, 3, 5) STMG_MASS_DFD_CASE(3, 4, 5) STMG_MASS_DFD_CASE(3, 5, 5)
+  STMG_MASS_DFD_CASE(3, 6, 1) STMG_MASS_DFD_CASE(3, 6, 5)
   STMG_MASS_DFD_CASE(2, 2, 1) STMG_MASS_DFD_CASE(2, 2, 2) STMG_MASS_DFD_CASE(2, 2, 3) STMG_MASS_DFD_CASE(2, 2, 4)
   STMG_MASS_DFD_CASE(2, 3, 1) STMG_MASS_DFD_CASE(2, 3, 2) STMG_MASS_DFD_CASE(2, 3, 3) STMG_MASS_DFD_CASE(2, 3, 4)
   STMG_MASS_DFD_CASE(2, 4, 1) STMG_MASS_DFD_CASE(2, 4, 2) STMG_MASS_DFD_CASE(2, 4, 3) STMG_MASS_DFD_CASE(2, 4, 4)

@@ -21,7 +21,8 @@ namespace stmg {
 namespace apply_detail {
 
 template <int N> constexpr int cells_per_block(int dim) {
-  return dim == 3 ? (N == 2 ? 32 : N == 3 ? 14 : N == 4 ? 8 : 5) : (N == 2 ? 64 : N == 3 ? 42 : N == 4 ? 32 : 25);
+  return dim == 3 ? (N == 2 ? 32 : N == 3 ? 14 : N == 4 ? 8 : N == 5 ? 5 : 3)
+                  : (N == 2 ? 64 : N == 3 ? 42 : N == 4 ? 32 : 25);
 }
 
 // Output accumulation: the result of every cell is added to its nodes' rows.
@@ -55,6 +56,8 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   const int slot = threadIdx.x / N2;
   const int lid = threadIdx.x - slot * N2;
   const int i = lid % N, j = lid / N;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + slot;
+  const bool active = cell < g.n_cells;
   T* s0 = smem + (size_t)slot * 3 * NT * N3;
   T* s1 = s0 + NT * N3;
   T* s2 = s1 + NT * N3;
@@ -67,11 +70,6 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
     sD[threadIdx.x / N][threadIdx.x % N] = tab.D[threadIdx.x / N][threadIdx.x % N];
   }
   auto I4 = [](int t, int c, int b, int a) { return ((t * N + c) * N + b) * N + a; };
-  // persistent: the CTA walks blocks of CPB cells (no partial last wave)
-  const int64_t nblk = (g.n_cells + CPB - 1) / CPB;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-  const int64_t cell = blk * CPB + slot;
-  const bool active = cell < g.n_cells;
 
   const int64_t cc = active ? cell : 0;
   const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N), cz = (int)(cc / ((int64_t)g.N * g.N));
@@ -253,8 +251,6 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
       }
     }
   }
-  __syncthreads();  // the next block reuses the shared buffers
-  }
 }
 
 template <int N, int NT, typename T, int CPB, typename TI, typename TO, bool MASS = false>
@@ -415,18 +411,12 @@ cudaError_t launch_apply_t(const TI* x, TO* y, const T* geo, const GridDesc& g, 
   if constexpr (DIM == 3) {
     const size_t smem = (size_t)CPB * 3 * NT * N * N * N * sizeof(T);
     auto k = apply3d_kernel<N, NT, T, CPB, TI, TO, MASS>;
-    static int resident = 0;  // CTAs per GPU (SMs x CTAs per SM), once per instance
-    if (!resident) {
+    static bool attr = false;
+    if (!attr) {
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, CPB * N * N, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-      resident = sms * per_sm;
+      attr = true;
     }
-    const int64_t grid = blocks < resident ? blocks : resident;
-    { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(CPB * N * N), smem, s, x, y, geo, g, tab, mask_input); if (e_ != cudaSuccess) return e_; }
+    { const cudaError_t e_ = launch_k(k, dim3((unsigned)blocks), dim3(CPB * N * N), smem, s, x, y, geo, g, tab, mask_input); if (e_ != cudaSuccess) return e_; }
   } else {
     const size_t smem = (size_t)CPB * 2 * NT * N * N * sizeof(T);
     auto k = apply2d_kernel<N, NT, T, CPB, TI, TO, MASS>;

@@ -33,9 +33,9 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-constexpr int kMaxN = 5;    // p <= 4
+constexpr int kMaxN = 6;    // p <= 5
 constexpr int STMG_DEVICE_TIMEOUT = 1;  // device status word: a bounded wait gave up
-constexpr int kMaxNT = 4;   // time DoFs per slab
+constexpr int kMaxNT = 5;   // time DoFs per slab
 
 // Tables of one operator evaluation, passed by value (constant bank).
 //   B[q][i]  : 1D nodal (Gauss-Lobatto) basis i at Gauss point q

@@ -15,7 +15,7 @@ namespace stmg {
 
 namespace {
 
-template <int N> constexpr int fd_cells_per_block() { return N == 2 ? 32 : N == 3 ? 14 : N == 4 ? 8 : 5; }
+template <int N> constexpr int fd_cells_per_block() { return N == 2 ? 32 : N == 3 ? 14 : N == 4 ? 8 : N == 5 ? 5 : 3; }
 
 template <int N, int NT, typename T, int CPB>
 __global__ void __launch_bounds__(CPB * N * N)
@@ -205,6 +205,7 @@ cudaError_t launch_fd_apply(int n, int nt, const T* r, T* u, const T* rho, const
   STMG_FD_CASE(3, 1) STMG_FD_CASE(3, 2) STMG_FD_CASE(3, 3) STMG_FD_CASE(3, 4)
   STMG_FD_CASE(4, 1) STMG_FD_CASE(4, 2) STMG_FD_CASE(4, 3) STMG_FD_CASE(4, 4)
   STMG_FD_CASE(5, 1) STMG_FD_CASE(5, 2) STMG_FD_CASE(5, 3) STMG_FD_CASE(5, 4)
+  STMG_FD_CASE(2, 5) STMG_FD_CASE(3, 5) STMG_FD_CASE(4, 5) STMG_FD_CASE(5, 5) STMG_FD_CASE(6, 5)
   return cudaErrorInvalidValue;
 }
 

@@ -880,7 +880,8 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   const int dim = mesh->dim, N = mesh->n_cells;
   if (dim != 2 && dim != 3) return invalid(ctx, "dim must be 2 or 3");
   if (N < 2) return invalid(ctx, "n_cells must be >= 2");
-  if (pr->p < 1 || pr->p > 4) return invalid(ctx, "p must be in 1..4");
+  if (pr->p < 1 || pr->p > 5 || (pr->p == 5 && dim != 3))
+    return invalid(ctx, "p must be in 1..4 (1..5 in 3D, where Q5 levels use the fast diagonalisation)");
   CKS(dev_alloc(ctx, &ctx->status, 1));
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   if (pr->time_scheme != STMG_DG && pr->time_scheme != STMG_CGP) return invalid(ctx, "unknown time scheme");
