@@ -510,11 +510,18 @@ def run_ours(args):
             extra["apply_fp64_finest"] = roof_fp64
             f32_ms = ctx.time_kernel(stmg.KERNEL_APPLY, 0, stmg.FP32, reps=20)
             f32_peak = 152 * 128 * 2 * 2.07e9  # FP32 FMA lanes x 2 flop x max SM clock
+            # bytes: x read, y read and written (atomics), the stored FP32 geometry (chunked, 32 B per Gauss point)
+            f32_bytes = n * 4 * 3 + cells * nq ** 3 * 32
             extra["apply_fp32_finest"] = {
-                "kernel": "apply3d_kernel<N=3,NT=3,float> (finest level, V-cycle residuals)", "bound": "shared memory",
+                "kernel": "apply3d_reg_kernel<3,3,float,float,0> (finest level, V-cycle residuals; one thread per "
+                          "cell and time DoF, sum factorisation in registers)", "bound": "alu",
                 "achieved": flops / (f32_ms * 1e-3) / 1e12, "peak": f32_peak / 1e12, "unit": "TFLOP/s",
                 "frac": flops / (f32_ms * 1e-3) / f32_peak, "avg_launch_ms": f32_ms,
-                "note": "fraction of the FP32-pipe peak; the kernel is bound by its shared-memory transposes"}
+                "stored_bytes": f32_bytes, "hbm_frac": f32_bytes / (f32_ms * 1e-3) / (peaks["hbm_gbs"] * 1e9),
+                "traffic": read_traffic("apply_fp32"),
+                "note": "frac: of the FP32-pipe peak (algorithmic flop count); hbm_frac: the bytes it must move "
+                        "(vectors and the stored geometry) over the measured copy bandwidth; latency-bound "
+                        "(long-scoreboard stalls, 16 warps per SM)"}
         extra["vcycle_ms"] = vc_ms
         extra["apply_gdofs"] = apply_gdofs(stmg, ctx, dofs_per_step, df=not args.plain)
         if not args.skip_compare and not args.plain:

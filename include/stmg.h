@@ -98,6 +98,8 @@ typedef struct {
  * Vectors of such a system are [slab][N_t][n_nodes]; the hierarchy adds
  * tau-levels (pairs of slabs merged, tau -> 2 tau, while their number is even)
  * between the space and the k levels (Algorithm mg-sequence).  1..64.
+ * Size limit: 2 n_slabs N_t (p n_cells + 1)^dim < 2^31 (the kernels index in 32-bit arithmetic);
+ * larger problems are refused with STMG_ERR_INVALID_ARG.
  * coeff (HOST, copied at create): rho of eq. space-matrices, either one value
  * per finest cell (PER_CELL) or one per finest-level Gauss point
  * ([cell][(p+1)^dim points, x fastest], PER_QPOINT); NULL means rho = 1.

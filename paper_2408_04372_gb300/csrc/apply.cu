@@ -18,16 +18,11 @@ __global__ void init_rows_kernel(T* __restrict__ y, const T* __restrict__ f, con
   const int64_t total = g.n_nodes * nt;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t node = idx % g.n_nodes;
-    const int gx = (int)(node % g.nn1);
-    const int64_t rest = node / g.nn1;
-    bool bnd = on_boundary(gx, g.nn1);
-    if (g.dim == 3) {
-      const int gy = (int)(rest % g.nn1), gz = (int)(rest / g.nn1);
-      bnd = bnd || on_boundary(gy, g.nn1) || on_boundary(gz, g.nn1);
-    } else {
-      bnd = bnd || on_boundary((int)rest, g.nn1);
-    }
+    const uint32_t node = (uint32_t)idx % (uint32_t)g.n_nodes;
+    int gx, gy, gz;
+    node_xyz(node, g.nn1, gx, gy, gz);
+    bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+    if (g.dim == 3) bnd = bnd || on_boundary(gz, g.nn1);
     T v;
     if (mode == 0) v = bnd ? (T)x[idx] : T(0);
     else if (mode == 1) v = bnd ? f[idx] - (T)x[idx] : f[idx];

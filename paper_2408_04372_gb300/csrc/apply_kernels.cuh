@@ -2,8 +2,10 @@
 // TA must be diagonal: it is M_tau, diagonal for the Lagrange time bases at quadrature
 // nodes of dG(k) and cGP(k) (the host checks this at set-up).
 //
-// One group of n^(dim-1) threads per cell ("pencil" threads, one per (x,y) node
-// column in 3D, one per x node line in 2D), several cells per CTA.  Per cell and
+// Two kernels.  3D with n = p + 1 <= 3 nodes per direction in FP32 arithmetic:
+// apply3d_reg_kernel, one thread per cell and time DoF, everything in registers (described below).
+// Otherwise (FP64 arithmetic, higher degrees, 2D): one group of n^(dim-1) threads per cell ("pencil"
+// threads, one per (x,y) node column in 3D, one per x node line in 2D), several cells per CTA.  Per cell and
 // time DoF the pencil threads do the sum-factorised interpolation to the Gauss
 // points (B), collocation derivatives there (D), the space-time mixing with the
 // two N_t x N_t time matrices and the metric (rho w |J| J^-1 J^-T) at each point,
@@ -13,9 +15,12 @@
 // constrained rows, 0 or the right-hand side elsewhere).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "df64.cuh"
 #include "kernels.h"
+#include "apply_reg.cuh"
 
 namespace stmg {
 namespace apply_detail {
@@ -72,7 +77,8 @@ apply3d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   auto I4 = [](int t, int c, int b, int a) { return ((t * N + c) * N + b) * N + a; };
 
   const int64_t cc = active ? cell : 0;
-  const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N), cz = (int)(cc / ((int64_t)g.N * g.N));
+  int cx, cy, cz;
+  cell_xyz(cc, g, cx, cy, cz);
   const int gx = cx * g.p + i, gy = cy * g.p + j;
   const bool bxy = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
   // FP32: the metric of this thread's column of Gauss points is loaded first, so that its latency
@@ -276,7 +282,8 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
   }
   auto I3 = [](int t, int b, int a) { return (t * N + b) * N + a; };
   const int64_t cc = active ? cell : 0;
-  const int cx = (int)(cc % g.N), cy = (int)(cc / g.N);
+  int cx, cy, cz_unused;
+  cell_xyz(cc, g, cx, cy, cz_unused);
   const int gx = cx * g.p + i;
   const bool bx = on_boundary(gx, g.nn1);
   {
@@ -406,6 +413,9 @@ apply2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, const T* __restrict
 template <int DIM, int N, int NT, typename T, typename TI, typename TO, bool MASS = false>
 cudaError_t launch_apply_t(const TI* x, TO* y, const T* geo, const GridDesc& g, const OpTab<T>& tab,
                            int mask_input, cudaStream_t s) {
+  if constexpr (DIM == 3 && geo_chunked(3, N) && std::is_same<T, float>::value) {
+    return launch_apply_reg<N, NT, TI, TO, MASS>(x, y, geo, g, tab, mask_input, s);
+  } else {
   constexpr int CPB = cells_per_block<N>(DIM);
   const int64_t blocks = (g.n_cells + CPB - 1) / CPB;
   if constexpr (DIM == 3) {
@@ -421,6 +431,7 @@ cudaError_t launch_apply_t(const TI* x, TO* y, const T* geo, const GridDesc& g, 
     const size_t smem = (size_t)CPB * 2 * NT * N * N * sizeof(T);
     auto k = apply2d_kernel<N, NT, T, CPB, TI, TO, MASS>;
     { const cudaError_t e_ = launch_k(k, dim3((unsigned)blocks), dim3(CPB * N), smem, s, x, y, geo, g, tab, mask_input); if (e_ != cudaSuccess) return e_; }
+  }
   }
   return cudaGetLastError();
 }

@@ -237,8 +237,8 @@ asm_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __restric
   const int64_t cell = (int64_t)blockIdx.x * CPB + slot;
   const bool active = cell < g.n_cells && a < NB;
   const int64_t cc = cell < g.n_cells ? cell : 0;
-  const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N);
-  const int cz = DIM == 3 ? (int)(cc / ((int64_t)g.N * g.N)) : 0;
+  int cx, cy, cz;
+  cell_xyz(cc, g, cx, cy, cz);
   const int aa = a < NB ? a : 0;
   const int gx = cx * g.p + aa % N, gy = cy * g.p + (aa / N) % N;
   const int gz = DIM == 3 ? cz * g.p + aa / (N * N) : 0;
@@ -469,8 +469,8 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     P.node = 0;
     if (!P.active) return;
     const int64_t so = MULTI ? (int64_t)sl * slab_stride : 0;
-    const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
-    const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+    int cx, cy, cz;
+    cell_xyz(cell, g, cx, cy, cz);
     const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
     const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
     bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);

@@ -62,6 +62,34 @@ struct GridDesc {
 
 __host__ __device__ inline bool on_boundary(int g, int nn1) { return g == 0 || g == nn1 - 1; }
 
+// Coordinates of a cell or node index, in 32-bit unsigned division: every index of a level is below
+// 2^31 (checked when a context is created), and 32-bit division costs a fraction of 64-bit division.
+__device__ __forceinline__ void cell_xyz(int64_t cell, const GridDesc& g, int& cx, int& cy, int& cz) {
+  const uint32_t c = (uint32_t)cell, n = (uint32_t)g.N;
+  const uint32_t r = c / n;
+  cx = (int)(c - r * n);
+  cy = (int)(r % n);
+  cz = (int)(r / n);
+}
+__device__ __forceinline__ void node_xyz(int64_t node, int nn1, int& gx, int& gy, int& gz) {
+  const uint32_t c = (uint32_t)node, n = (uint32_t)nn1;
+  const uint32_t r = c / n;
+  gx = (int)(c - r * n);
+  gy = (int)(r % n);
+  gz = (int)(r / n);
+}
+
+// Geometry layout.  The FP32 geometry of 3D levels with at most three nodes per direction is read
+// by the register-resident operator kernel (one thread per cell and time DoF), whose warps read
+// consecutive cells with 16-byte loads: it is stored in chunks of kGeoChunk cells,
+// [cell / 32][Gauss point][part][cell % 32][4], part 0 = (G00, G01, G02, G11), part 1 = (G12, G22, m, 0).
+// Every other geometry array is [cell][component][point].
+constexpr int kGeoChunk = 32;
+__host__ __device__ constexpr bool geo_chunked(int dim, int n) { return dim == 3 && n <= 3; }
+__host__ __device__ inline int64_t geo_chunk_cells(int64_t n_cells) {
+  return (n_cells + kGeoChunk - 1) / kGeoChunk * kGeoChunk;
+}
+
 // Time diagonalisation of the local space-time matrices for the additive
 // Schwarz smoother: modes m = 0..nreal-1 are real, then ncplx complex modes
 // (one representative per conjugate pair).  W = V^-1 TA^-1 (rows = modes),

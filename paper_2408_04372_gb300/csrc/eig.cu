@@ -326,8 +326,8 @@ eig_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const unsigned char
     P.w = T(1);
     if (!P.active) return;
     const int64_t so = MULTI ? (int64_t)sl * slab_stride : 0;
-    const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
-    const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+    int cx, cy, cz;
+    cell_xyz(cell, g, cx, cy, cz);
     const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
     const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
     bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
@@ -589,8 +589,8 @@ eig_tc_kernel(const float* __restrict__ r, float* __restrict__ u, const unsigned
     int64_t node = 0;
     float w = 1.f, muj = 1.f;
     if (active) {
-      const int cx = (int)(cell % g.N), cy = (int)((cell / g.N) % g.N);
-      const int cz = DIM == 3 ? (int)(cell / ((int64_t)g.N * g.N)) : 0;
+      int cx, cy, cz;
+      cell_xyz(cell, g, cx, cy, cz);
       const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
       const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
       bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);

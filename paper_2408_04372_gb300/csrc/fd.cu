@@ -35,7 +35,8 @@ fd_apply_kernel(const T* __restrict__ r, T* __restrict__ u, const T* __restrict_
   T* s1 = s0 + NT * N3;
   auto I4 = [](int t, int c, int b, int a) { return ((t * N + c) * N + b) * N + a; };
   const int64_t cc = active ? cell : 0;
-  const int cx = (int)(cc % g.N), cy = (int)((cc / g.N) % g.N), cz = (int)(cc / ((int64_t)g.N * g.N));
+  int cx, cy, cz;
+  cell_xyz(cc, g, cx, cy, cz);
   const int tx = cx == 0 ? 0 : (cx == g.N - 1 ? 2 : 1);
   const int ty = cy == 0 ? 0 : (cy == g.N - 1 ? 2 : 1);
   const int tz = cz == 0 ? 0 : (cz == g.N - 1 ? 2 : 1);

@@ -46,7 +46,8 @@ cudaError_t launch_init_rows(T* y, const T* f, const T* x, const GridDesc& g, in
 
 // ---- geometry (setup.cu) ----
 // geo64 [cell][7 or 4][nq^dim]: rho w |J| J^-1 J^-T (upper triangle) and w |J|; geo32 the same in
-// FP32, geodf (may be NULL) as double-float pairs
+// FP32, geodf (may be NULL) as double-float pairs.  geo32 uses the chunked layout where
+// geo_chunked(dim, nq) holds (common.cuh) and then holds geo_chunk_cells(n_cells) cells x 8 components.
 cudaError_t launch_geometry(const GridDesc& g, const double* vertices, const double* rho_qp, const double* xq,
                             const double* wq, double* geo64, float* geo32, df64* geodf, cudaStream_t s);
 
@@ -147,7 +148,8 @@ cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64
 // stride, the vectors arrive by bulk copies (TMA) and a timed-out wait is recorded there.
 cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                            double* out, cudaStream_t s, int* status = nullptr);
+                            double* out, cudaStream_t s, int* status = nullptr, const double* nrm2 = nullptr,
+                            float* copy32 = nullptr);
 int cgs_blocks();
 // w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride; V in FP64 or FP32)
 template <typename TV>

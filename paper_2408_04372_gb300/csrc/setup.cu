@@ -79,15 +79,19 @@ __global__ void geometry_kernel(GridDesc g, const double* __restrict__ vert, con
       out[2] = (Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1]) * jw * rho;
       out[3] = jw;
     }
+    const bool chunked = geo_chunked(dim, nq);
     for (int c = 0; c < ncomp; ++c) {
       const int64_t o = (cell * ncomp + c) * nqd + q;
+      const int64_t oc =
+          chunked ? (((cell / kGeoChunk * nqd + q) * 2 + c / 4) * kGeoChunk + cell % kGeoChunk) * 4 + c % 4 : o;
       geo64[o] = out[c];
-      geo32[o] = (float)out[c];
+      geo32[oc] = (float)out[c];
       if (geodf) {
         const float h = (float)out[c];
         geodf[o] = df64(h, (float)(out[c] - (double)h));
       }
     }
+    if (chunked) geo32[(((cell / kGeoChunk * nqd + q) * 2 + 1) * kGeoChunk + cell % kGeoChunk) * 4 + 3] = 0.0f;
   }
 }
 

@@ -68,10 +68,14 @@ struct Level {
 
 }  // namespace
 
+// pinned host staging: Arnoldi columns (up to 66 values) of even iterations at 0, of odd ones here
+constexpr int kColSlot = 192;
+
 struct stmg_ctx {
   cudaStream_t stream = nullptr;       // private stream (graph capture needs a non-legacy stream)
   cudaStream_t user_stream = nullptr;  // caller's stream; every call is ordered after and before it
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_iter[2] = {nullptr, nullptr};  // end of FGMRES iteration j (slot j % 2): its column is on the host
   int dim = 3, pde = 0, scheme = 0;
   double tau = 1.0;
   stmg_options opt{};
@@ -89,7 +93,7 @@ struct stmg_ctx {
   unsigned int* counter = nullptr;  // arrival counter of those passes (zero between launches)
   int* status = nullptr;            // device status word: nonzero after a bounded device wait gave up
   double* dsm = nullptr;  // device scalars [0..nvec+8) h1, [128..) h2, [256..) outputs
-  double* hsm = nullptr;  // pinned host mirror
+  double* hsm = nullptr;  // pinned host mirror: [0..) and [kColSlot..) Arnoldi columns of even / odd iterations
   double* tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* rhs_buf = nullptr;
   double* u_buf = nullptr;
@@ -528,20 +532,23 @@ stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
 }
 
 // enqueue part: no host synchronisation (capturable).  Classical Gram-Schmidt twice in three
-// fused passes over the basis: h1 = V^T w ; w -= V h1, h2 = V^T w ; w -= V h2, ||w|| and the
-// column h1 + h2 ; then w /= ||w|| (and, with copy32, its FP32 copy: the next V-cycle's input).
+// fused passes over the basis: h1 = V^T w ; w -= V h1, h2 = V^T w, |w|^2 ; w = (w - V h2) / hn with
+// hn^2 = |w|^2 - |h2|^2 (orthonormal basis), the column h1 + h2 and hn (with copy32, also the FP32
+// copy of the normalised w: the next V-cycle's input).
 stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, int nv, double* w, int64_t n,
-                                  float* copy32 = nullptr) {
+                                  float* copy32 = nullptr, double* hdst = nullptr) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
   double* d_out = ctx->dsm + 384;
   int* st = ctx->status;
   CK(launch_cgs_pass(V0, ld, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream, st));
-  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st));
-  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 1, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream, st));
-  ctx->launches += 4;
-  CK(launch_scale_by_device(w, d_out + nv + 1, n, ctx->stream, copy32));
-  CK(cudaMemcpyAsync(ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
+  // the second pass also reduces |w|^2 (into d_h2[nv]), from which the third pass knows the norm of
+  // its result and normalises it (and writes the FP32 copy) as it subtracts
+  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 1, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st));
+  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 0, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream, st,
+                     d_h2 + nv, copy32));
+  ctx->launches += 3;
+  CK(cudaMemcpyAsync(hdst ? hdst : ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
   return STMG_OK;
 }
 
@@ -893,6 +900,11 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
   if (nslabs < 1 || nslabs > 64) return invalid(ctx, "n_slabs must be in 1..64");
   if (nslabs > 1 && (pr->pde != STMG_HEAT || pr->time_scheme != STMG_DG))
     return invalid(ctx, "several slabs in one system: heat equation with dG in time only");
+  {  // the kernels index vectors and cells in 32-bit arithmetic
+    const double nn1 = (double)pr->p * N + 1.0;
+    if (std::pow(nn1, dim) * nt * nslabs * 2.0 >= 2147483648.0)
+      return invalid(ctx, "problem too large: a level's vectors must hold fewer than 2^30 entries");
+  }
   ctx->dim = dim; ctx->pde = pr->pde; ctx->scheme = pr->time_scheme; ctx->tau = pr->tau;
   stmg_options o{};
   if (op) o = *op;
@@ -1037,7 +1049,9 @@ stmg_status create_impl(stmg_ctx* ctx, const stmg_mesh* mesh, const stmg_problem
     CK(cudaMemcpy(dwq, wq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice));
     const int ncomp = dim == 3 ? 7 : 4;
     CKS(dev_alloc(ctx, &L.geo64, (size_t)L.g.n_cells * ncomp * nqd));
-    CKS(dev_alloc(ctx, &L.geo32, (size_t)L.g.n_cells * ncomp * nqd));
+    const bool chunked = geo_chunked(dim, nq);
+    CKS(dev_alloc(ctx, &L.geo32, chunked ? (size_t)geo_chunk_cells(L.g.n_cells) * 8 * nqd
+                                         : (size_t)L.g.n_cells * ncomp * nqd));
     if (li == 0 && ctx->outer_df) CKS(dev_alloc(ctx, &L.geodf, (size_t)L.g.n_cells * ncomp * nqd));
     CK(launch_geometry(L.g, dvert, drho, dxq, dwq, L.geo64, L.geo32, L.geodf, ctx->stream));
     const int64_t sz = L.size();
@@ -1146,7 +1160,8 @@ stmg_status op_apply_f2d(stmg_ctx* ctx, Level& L, const float* x, double* y) {
   return STMG_OK;
 }
 
-// z_j = B v_j, v_{j+1} = S z_j, CGS2 against v_0..v_j, Hessenberg column to the host buffer.
+// z_j = B v_j, v_{j+1} = S z_j, CGS2 against v_0..v_j, Hessenberg column to the host buffer of
+// parity j (hsm + (j % 2) * kColSlot).
 // low: the operator apply in FP32 arithmetic (relaxed FGMRES), else double-float / FP64.
 stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool low = false) {
   Level& L = ctx->levels[0];
@@ -1172,7 +1187,8 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool
     CK(cudaMemsetAsync(w, 0, sizeof(double) * n, ctx->stream));
     if (low) CKS(op_apply_f2d(ctx, L, z32, w));
     else CKS(op_apply_df(ctx, L, z32, w, false));
-    return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n, j + 1 < ctx->m ? L.f32 : nullptr);
+    return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n, j + 1 < ctx->m ? L.f32 : nullptr,
+                                 ctx->hsm + (j & 1) * kColSlot);
   }
   if (ctx->opt.vcycle_precision == STMG_FP32) {
     CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
@@ -1188,7 +1204,7 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool
     CK(cudaMemcpyAsync(z, L.u64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     CKS(op_apply<double>(ctx, L, z, w));
   }
-  return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n);
+  return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n, nullptr, ctx->hsm + (j & 1) * kColSlot);
 }
 
 stmg_status fgmres_iteration(stmg_ctx* ctx, int j, bool low = false) {
@@ -1275,13 +1291,34 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), cs(m, 0.0), sn(m, 0.0);
     g[0] = beta;
     int jend = 0;
-    bool low = false;  // relaxed apply: only after the residual estimate has fallen far enough
+    // Iterations are pipelined: iteration j + 1 only needs v_{j+1}, which iteration j leaves on the
+    // device, so it is enqueued before the host reads iteration j's Arnoldi column and the GPU does
+    // not wait for the host round trip.  The host's decisions for it are taken from the residual
+    // estimate extrapolated by the last contraction factor: whether the cycle goes on (not
+    // speculated when the estimate is within kSpecMargin of the target, so that normally no
+    // iteration is wasted; one that is wasted is simply not used) and the relaxed (FP32) apply.
+    constexpr double kSpecMargin = 10.0;
+    std::vector<char> lowv(m, 0);
+    int enq = 0;          // iterations of this cycle enqueued so far
+    double ratio = 1.0;   // last contraction |g_{j+1}| / |g_j|
+    auto relax_ok = [&](double gest) { return ctx->opt.outer_relax && ctx->outer_df && gest <= target / kRelaxDelta; };
+    auto enqueue = [&](int jj, bool lw) -> stmg_status {
+      CKS(fgmres_iteration(ctx, jj, lw));
+      CK(cudaEventRecord(ctx->ev_iter[jj & 1], ctx->stream));
+      lowv[jj] = lw;
+      enq = jj + 1;
+      return STMG_OK;
+    };
+    CKS(enqueue(0, false));
     for (int j = 0; j < m; ++j) {
-      CKS(fgmres_iteration(ctx, j, low));
-      if (low) s.relaxed_iterations++;
-      std::vector<double> h;
-      double hn = 0.0;
-      CKS(orthogonalise_read(ctx, j + 1, h, hn));
+      if (enq == j + 1 && j + 1 < m && its + 1 < ctx->opt.max_it) {
+        const double gpred = std::fabs(g[j]) * ratio;  // extrapolated |g_{j+1}|
+        if (gpred > kSpecMargin * target) CKS(enqueue(j + 1, relax_ok(gpred)));
+      }
+      CK(cudaEventSynchronize(ctx->ev_iter[j & 1]));
+      const double* col = ctx->hsm + (j & 1) * kColSlot;
+      std::vector<double> h(col, col + j + 1);
+      const double hn = col[j + 1];
       for (int i = 0; i <= j; ++i) {
         if (!std::isfinite(h[i])) { ctx->err = "preconditioned vector is not finite"; return STMG_ERR_NONFINITE; }
         H[(size_t)i * m + j] = h[i];
@@ -1300,11 +1337,13 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
       H[(size_t)(j + 1) * m + j] = 0.0;
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
+      ratio = std::fabs(sn[j]);  // |g_{j+1}| / |g_j|
       ++its;
       jend = j + 1;
-      low = ctx->opt.outer_relax && ctx->outer_df && std::fabs(g[j + 1]) <= target / kRelaxDelta;
+      if (lowv[j]) s.relaxed_iterations++;
       if (hn == 0.0) break;  // breakdown: the Krylov space is invariant, the update below is exact
       if (std::fabs(g[j + 1]) <= target || its >= ctx->opt.max_it) break;
+      if (enq == j + 1 && j + 1 < m) CKS(enqueue(j + 1, relax_ok(std::fabs(g[j + 1]))));
     }
     std::vector<double> y(jend, 0.0);
     for (int i = jend - 1; i >= 0; --i) {
@@ -1477,6 +1516,7 @@ stmg_status stmg_create(stmg_ctx** out, const stmg_mesh* mesh, const stmg_proble
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->ev_iter[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     ctx->err = std::string("stream set-up: ") + cudaGetErrorString(e);
     *out = ctx;
@@ -1509,6 +1549,8 @@ stmg_status stmg_destroy(stmg_ctx* ctx) {
   if (ctx->hsm) cudaFreeHost(ctx->hsm);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  for (auto ev : ctx->ev_iter)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return STMG_OK;

@@ -50,11 +50,11 @@ __global__ void gather_axis_kernel(const T* __restrict__ in, T* __restrict__ out
   const int64_t total = (int64_t)nt * o2 * o1 * o0;
   const int64_t sin_ = axis == 0 ? 1 : (axis == 1 ? d0 : (int64_t)d0 * d1);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = e;
-    const int x0 = (int)(r % o0); r /= o0;
-    const int x1 = (int)(r % o1); r /= o1;
-    const int x2 = (int)(r % o2);
-    const int t = (int)(r / o2);
+    uint32_t r = (uint32_t)e;  // every index of a level is below 2^31
+    const int x0 = (int)(r % (uint32_t)o0); r /= (uint32_t)o0;
+    const int x1 = (int)(r % (uint32_t)o1); r /= (uint32_t)o1;
+    const int x2 = (int)(r % (uint32_t)o2);
+    const int t = (int)(r / (uint32_t)o2);
     const int i = axis == 0 ? x0 : (axis == 1 ? x1 : x2);
     const int64_t base = (((int64_t)t * d2 + (axis == 2 ? 0 : x2)) * d1 + (axis == 1 ? 0 : x1)) * d0 + (axis == 0 ? 0 : x0);
     T acc = 0;
@@ -89,12 +89,14 @@ __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ ou
   const int64_t per_in = DIM == 3 ? (int64_t)nin * nin * nin : (int64_t)nin * nin;
   const int64_t total = per * nt;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(e / per);
-    int64_t r = e - (int64_t)t * per;
-    const int x = (int)(r % nout);
-    r /= nout;
-    const int y = DIM == 3 ? (int)(r % nout) : (int)r;
-    const int z = DIM == 3 ? (int)(r / nout) : 0;
+    // 32-bit index arithmetic (every index of a level is below 2^31)
+    const uint32_t e32 = (uint32_t)e, per32 = (uint32_t)per, no = (uint32_t)nout;
+    const int t = (int)(e32 / per32);
+    uint32_t r = e32 - (uint32_t)t * per32;
+    const uint32_t ry = r / no;
+    const int x = (int)(r - ry * no);
+    const int y = DIM == 3 ? (int)(ry % no) : (int)ry;
+    const int z = DIM == 3 ? (int)(ry / no) : 0;
     int jx[R], jy[R], jz[R];
     T wx[R], wy[R], wz[R];
 #pragma unroll
@@ -172,11 +174,9 @@ cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, c
 }
 
 __device__ inline bool node_on_boundary(int64_t node, const GridDesc& g) {
-  const int gx = (int)(node % g.nn1);
-  const int64_t rest = node / g.nn1;
-  if (on_boundary(gx, g.nn1)) return true;
-  if (g.dim == 3) return on_boundary((int)(rest % g.nn1), g.nn1) || on_boundary((int)(rest / g.nn1), g.nn1);
-  return on_boundary((int)rest, g.nn1);
+  int gx, gy, gz;
+  node_xyz(node, g.nn1, gx, gy, gz);
+  return on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1) || (g.dim == 3 && on_boundary(gz, g.nn1));
 }
 
 template <typename T>
@@ -186,7 +186,7 @@ __global__ void prolong_time_add_kernel(T* __restrict__ uf, const T* __restrict_
   pdl_trigger();
   const int64_t nn = g.n_nodes;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn * tt.nb; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / nn, node = e - b * nn;
+    const int64_t b = (uint32_t)e / (uint32_t)nn, node = e - b * nn;
     T* ub = uf + b * tt.ntf * nn;
     const T* eb = ec + b * tt.ntc * nn;
     for (int i = 0; i < tt.ntf; ++i) side.run(b * tt.ntf * nn + i * nn + node);
@@ -208,7 +208,7 @@ __global__ void restrict_time_kernel(T* __restrict__ rc, const T* __restrict__ r
   pdl_trigger();
   const int64_t nn = g.n_nodes;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn * tt.nb; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / nn, node = e - b * nn;
+    const int64_t b = (uint32_t)e / (uint32_t)nn, node = e - b * nn;
     T* cb = rc + b * tt.ntc * nn;
     const T* fb = rf + b * tt.ntf * nn;
     for (int j = 0; j < tt.ntc; ++j) side.run(b * tt.ntc * nn + j * nn + node);

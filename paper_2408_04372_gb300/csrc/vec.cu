@@ -55,13 +55,27 @@ __global__ void scale_by_device_kernel(double* __restrict__ x, const double* __r
 // partials in block order, so the results do not depend on scheduling.  It then writes
 //   fin 0: out[j] = s_j (j < nv) and out[nv] = s_nv when norm is set;
 //   fin 1: the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = sqrt(s_nv), out[nv+1] = 1/out[nv].
+// nrm2 (fin 1 only, norm unset): the pass also normalises.  nrm2[0] is |w|^2 before this pass's
+// subtraction (from the previous pass); with an orthonormal basis the subtracted vector has
+// |w - V c|^2 = nrm2[0] - |c|^2, so every block knows the norm hn before it starts, scales its
+// elements by 1 / hn and, with copy32, writes their FP32 copy; out[nv] = hn.  One pass over w and
+// one launch fewer than a separate normalisation.
 // One thread keeps the K values V_j[i] of its element in registers between the subtraction and
 // the dot products, so every basis vector is read once per pass.
+// sqrt(|w|^2 - |c|^2) (0 when the difference is not positive: w lies in the span of the basis)
+__device__ __forceinline__ double fused_norm(double w2, const double* cs, int nv) {
+  double c2 = 0.0;
+  for (int j = 0; j < nv; ++j) c2 += cs[j] * cs[j];
+  const double d = w2 - c2;
+  return d > 0.0 ? sqrt(d) : 0.0;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kCgsThreads)
 cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
                 const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev, int fin,
-                double* __restrict__ partial, unsigned int* __restrict__ counter, double* __restrict__ out) {
+                double* __restrict__ partial, unsigned int* __restrict__ counter, double* __restrict__ out,
+                const double* __restrict__ nrm2, float* __restrict__ copy32) {
   pdl_wait();
   pdl_trigger();
   __shared__ double red[kCgsThreads / 32][K + 1];
@@ -70,6 +84,8 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (sub && j < nv) ? c[j] : 0.0;
   __syncthreads();
+  const double hn_fused = nrm2 ? fused_norm(nrm2[0], cs, nv) : 0.0;
+  const double inv = hn_fused > 0.0 ? 1.0 / hn_fused : 0.0;
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
   double acc[K + 1];
@@ -85,6 +101,10 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
 #pragma unroll
       for (int j = 0; j < K; ++j) sv += cs[j] * v[j];
       wi -= sv;
+      if (nrm2) {
+        wi *= inv;
+        if (copy32) copy32[i] = (float)wi;
+      }
       w[i] = wi;
     }
     if (dot) {
@@ -135,7 +155,7 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
   } else {
     for (int j = threadIdx.x; j < nv; j += blockDim.x) out[j] = h_prev[j] + cs[j];
     if (threadIdx.x == 0) {
-      const double hn = sqrt(fmax(tot[K], 0.0));
+      const double hn = nrm2 ? hn_fused : sqrt(fmax(tot[K], 0.0));
       out[nv] = hn;
       out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     }
@@ -184,7 +204,8 @@ __global__ void __launch_bounds__(kCgsThreads)
 cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
                     const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev,
                     int fin, double* __restrict__ partial, unsigned int* __restrict__ counter,
-                    double* __restrict__ out, int* status) {
+                    double* __restrict__ out, int* status, const double* __restrict__ nrm2,
+                    float* __restrict__ copy32) {
   pdl_wait();
   pdl_trigger();
   constexpr int E = CgsTma<K>::E, S = CgsTma<K>::S;
@@ -206,6 +227,8 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
+  const double hn_fused = nrm2 ? fused_norm(nrm2[0], cs, nv) : 0.0;
+  const double inv = hn_fused > 0.0 ? 1.0 / hn_fused : 0.0;
   auto main_bytes = [&](int64_t ch) -> uint32_t {
     const int64_t ne = n - ch * E < E ? n - ch * E : E;
     return (uint32_t)((ne * (int64_t)sizeof(double)) / 16 * 16);
@@ -258,6 +281,10 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
           for (int j = 0; j < K; ++j)
             if (j < nv) sv += cs[j] * vj(j);
           wi -= sv;
+          if (nrm2) {
+            wi *= inv;
+            if (copy32) copy32[e0 + e] = (float)wi;
+          }
           w[e0 + e] = wi;
         }
         if (dot) {
@@ -265,7 +292,7 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
           for (int j = 0; j < K; ++j)
             if (j < nv) acc[j] += vj(j) * wi;
         }
-        acc[K] += wi * wi;
+        if (norm) acc[K] += wi * wi;
       }
       __syncthreads();  // stage free again
       const int64_t nx = ch + (int64_t)S * gridDim.x;
@@ -322,7 +349,7 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   } else {
     for (int j = tid; j < nv; j += blockDim.x) out[j] = h_prev[j] + cs[j];
     if (tid == 0) {
-      const double hn = sqrt(fmax(tot[K], 0.0));
+      const double hn = nrm2 ? hn_fused : sqrt(fmax(tot[K], 0.0));
       out[nv] = hn;
       out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     }
@@ -411,11 +438,10 @@ __global__ void zero_constrained_kernel(double* __restrict__ y, GridDesc g, int 
   pdl_trigger();
   for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n_nodes;
        node += (int64_t)gridDim.x * blockDim.x) {
-    const int gx = (int)(node % g.nn1);
-    const int64_t rest = node / g.nn1;
-    bool bnd = on_boundary(gx, g.nn1);
-    if (g.dim == 3) bnd = bnd || on_boundary((int)(rest % g.nn1), g.nn1) || on_boundary((int)(rest / g.nn1), g.nn1);
-    else bnd = bnd || on_boundary((int)rest, g.nn1);
+    int gx, gy, gz;
+    node_xyz(node, g.nn1, gx, gy, gz);
+    bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+    if (g.dim == 3) bnd = bnd || on_boundary(gz, g.nn1);
     if (bnd)
       for (int t = 0; t < nt; ++t) y[t * g.n_nodes + node] = 0.0;
   }
@@ -448,7 +474,7 @@ int cgs_blocks() { return kCgsBlocks; }
 template <int K>
 cudaError_t launch_cgs_tma(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                            int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                           double* out, int* status, cudaStream_t s) {
+                           double* out, int* status, cudaStream_t s, const double* nrm2, float* copy32) {
   static bool attr = false;
   auto k = cgs_pass_tma_kernel<K>;
   if (!attr) {
@@ -457,19 +483,21 @@ cudaError_t launch_cgs_tma(const double* V0, int64_t stride, int nv, double* w, 
     attr = true;
   }
   { const cudaError_t e_ = launch_k(k, dim3(152 * CgsTma<K>::BPS), dim3(kCgsThreads), cgs_tma_smem<K>(), s, V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin,
-                                                                 partial, counter, out, status); if (e_ != cudaSuccess) return e_; }
+                                                                 partial, counter, out, status, nrm2, copy32); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                            double* out, cudaStream_t s, int* status) {
+                            double* out, cudaStream_t s, int* status, const double* nrm2, float* copy32) {
   if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
+  if (nrm2 && (!fin || norm || !sub)) return cudaErrorInvalidValue;
   // bulk copies need 16-byte aligned sources: w, V0 and the stride between basis vectors
   const bool aligned = ((uintptr_t)w % 16 == 0) && (nv == 0 || (((uintptr_t)V0 % 16 == 0) && stride % 2 == 0));
   if (status && aligned) {
 #define STMG_CGS_TMA(KK) \
-  return launch_cgs_tma<KK>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter, out, status, s)
+  return launch_cgs_tma<KK>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter, out, status, s, \
+                            nrm2, copy32)
     if (nv <= 4) STMG_CGS_TMA(4);
     if (nv <= 8) STMG_CGS_TMA(8);
     if (nv <= 16) STMG_CGS_TMA(16);
@@ -480,7 +508,7 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
   // one wave: blocks per SM as the register use of each width allows (4, 4, 2, 1, 1)
 #define STMG_CGS(KK, BPS) \
   return launch_k(cgs_pass_kernel<KK>, dim3(152 * (BPS)), dim3(kCgsThreads), 0, s, V0, stride, nv, w, n, c, sub, dot, \
-                  norm, h_prev, fin, partial, counter, out)
+                  norm, h_prev, fin, partial, counter, out, nrm2, copy32)
   if (nv <= 4) STMG_CGS(4, 4);
   else if (nv <= 8) STMG_CGS(8, 4);
   else if (nv <= 16) STMG_CGS(16, 2);

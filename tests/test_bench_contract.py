@@ -33,7 +33,7 @@ def test_traffic_records_match_the_current_sources_and_go_null_on_change(monkeyp
     spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    for key in ("asm_bf16", "apply_df32"):
+    for key in ("asm_bf16", "apply_df32", "apply_fp32"):
         assert bench.read_traffic(key) is not None and bench.read_traffic(key) > 1e7, key
     monkeypatch.setattr(bench, "source_sha", lambda paths: "0" * 16)
     assert bench.read_traffic("asm_bf16") is None
