@@ -149,7 +149,11 @@ cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64
 cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
                             double* out, cudaStream_t s, int* status = nullptr, const double* nrm2 = nullptr,
-                            float* copy32 = nullptr);
+                            float* copy32 = nullptr, int vfmt = 0);
+// vfmt: 0 FP64 vectors; 1 the basis and w as double-float pairs (hi, lo) in their 8 bytes per entry,
+// double-float arithmetic; 2 the same with w arriving in FP64 (converted and written back as pairs).
+// r = x * scale as double-float pairs written over x (FP64 in), and its FP32 copy (the V-cycle input).
+cudaError_t launch_scale_to_df(double* x, double scale, int64_t n, float* copy32, cudaStream_t s);
 int cgs_blocks();
 // w += sign * sum_j h[j] V_j  (h on the device, V_j = V0 + j * stride; V in FP64 or FP32)
 template <typename TV>

@@ -99,10 +99,11 @@ struct stmg_ctx {
   double* u_buf = nullptr;
   cudaGraphExec_t graph32 = nullptr, graph64 = nullptr;
   int64_t graph32_kernels = 0, graph64_kernels = 0;
-  std::vector<cudaGraphExec_t> iter_graphs;      // one FGMRES iteration per Krylov index j
-  std::vector<int64_t> iter_graph_kernels;
-  std::vector<cudaGraphExec_t> iter_graphs_low;  // the same with the relaxed (FP32) operator apply
-  std::vector<int64_t> iter_graph_kernels_low;
+  // one FGMRES iteration per Krylov index j, per variant: bit 0 the relaxed (FP32) operator apply,
+  // bit 1 the double-float Krylov basis (Gram-Schmidt on the FP32 pipe)
+  std::vector<cudaGraphExec_t> iter_graphs[4];
+  std::vector<int64_t> iter_graph_kernels[4];
+  bool gs_df = false;  // this solve keeps its Krylov basis V in double-float pairs
   bool warmed32 = false, warmed64 = false;
   int64_t launches = 0;  // kernels issued by this context (graph replays count their kernel nodes)
   std::vector<stmg_net*> nets;  // networks bound to this context; detached when it is destroyed
@@ -536,17 +537,20 @@ stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
 // hn^2 = |w|^2 - |h2|^2 (orthonormal basis), the column h1 + h2 and hn (with copy32, also the FP32
 // copy of the normalised w: the next V-cycle's input).
 stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, int nv, double* w, int64_t n,
-                                  float* copy32 = nullptr, double* hdst = nullptr) {
+                                  float* copy32 = nullptr, double* hdst = nullptr, bool df = false) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
   double* d_out = ctx->dsm + 384;
   int* st = ctx->status;
-  CK(launch_cgs_pass(V0, ld, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream, st));
+  // df: the basis is in double-float pairs; the first pass converts w (FP64, the operator's output)
+  CK(launch_cgs_pass(V0, ld, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream, st,
+                     nullptr, nullptr, df ? 2 : 0));
   // the second pass also reduces |w|^2 (into d_h2[nv]), from which the third pass knows the norm of
   // its result and normalises it (and writes the FP32 copy) as it subtracts
-  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 1, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st));
+  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 1, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st,
+                     nullptr, nullptr, df ? 1 : 0));
   CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 0, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream, st,
-                     d_h2 + nv, copy32));
+                     d_h2 + nv, copy32, df ? 1 : 0));
   ctx->launches += 3;
   CK(cudaMemcpyAsync(hdst ? hdst : ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
   return STMG_OK;
@@ -1175,7 +1179,7 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool
     // and w starts from 0 (z_j vanishes on constrained rows).  The V-cycle input (float) v_j was
     // written by the previous iteration's normalisation, except at j = 0.
     float* z32 = ctx->Z32 + (size_t)j * n;
-    if (j == 0) {
+    if (j == 0 && !ctx->gs_df) {  // with the double-float basis the restart's normalisation wrote L.f32
       CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
       ctx->launches += 1;
     }
@@ -1188,7 +1192,7 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool
     if (low) CKS(op_apply_f2d(ctx, L, z32, w));
     else CKS(op_apply_df(ctx, L, z32, w, false));
     return orthogonalise_enqueue(ctx, ctx->V, ctx->vld, j + 1, w, n, j + 1 < ctx->m ? L.f32 : nullptr,
-                                 ctx->hsm + (j & 1) * kColSlot);
+                                 ctx->hsm + (j & 1) * kColSlot, ctx->gs_df);
   }
   if (ctx->opt.vcycle_precision == STMG_FP32) {
     CK(launch_convert<double, float>(v, L.f32, n, ctx->stream));
@@ -1210,8 +1214,9 @@ stmg_status fgmres_iteration_enqueue(stmg_ctx* ctx, int j, bool in_capture, bool
 stmg_status fgmres_iteration(stmg_ctx* ctx, int j, bool low = false) {
   const bool warmed = ctx->opt.vcycle_precision == STMG_FP32 ? ctx->warmed32 : ctx->warmed64;
   if (!warmed) return fgmres_iteration_enqueue(ctx, j, false, low);  // first V-cycle runs eagerly
-  std::vector<cudaGraphExec_t>& graphs = low ? ctx->iter_graphs_low : ctx->iter_graphs;
-  std::vector<int64_t>& kernels = low ? ctx->iter_graph_kernels_low : ctx->iter_graph_kernels;
+  const int variant = (low ? 1 : 0) | (ctx->gs_df ? 2 : 0);
+  std::vector<cudaGraphExec_t>& graphs = ctx->iter_graphs[variant];
+  std::vector<int64_t>& kernels = ctx->iter_graph_kernels[variant];
   if ((int)graphs.size() < ctx->m) {
     graphs.assign(ctx->m, nullptr);
     kernels.assign(ctx->m, 0);
@@ -1270,6 +1275,9 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
   // stopping rule: ||b - S x|| <= max(rtol ||b||, atol) (the absolute part only when atol > 0)
   const double target = std::max(ctx->opt.rtol * bnorm, ctx->opt.atol);
   const bool df_residual = ctx->outer_df && target >= 1e-10 * bnorm;
+  // the Krylov basis in double-float pairs (Gram-Schmidt on the FP32 pipe, about 44 bits) under the
+  // same condition as the double-float residual; FP64 otherwise
+  ctx->gs_df = df_residual;
   std::vector<double*> V(m + 1), Z(m);
   for (int j = 0; j <= m; ++j) V[j] = ctx->V + (size_t)j * ctx->vld;
   for (int j = 0; j < m; ++j) Z[j] = ctx->Z + (size_t)j * n;
@@ -1286,7 +1294,8 @@ stmg_status solve_impl(stmg_ctx* ctx, const double* b, double* x, stmg_solve_sta
     if (beta <= target) break;
     if (its >= ctx->opt.max_it) { result = STMG_ERR_NOT_CONVERGED; break; }
     if (its > 0) s.restarts++;
-    CK(launch_axpby(0.0, V[0], 1.0 / beta, V[0], n, ctx->stream));
+    if (ctx->gs_df) CK(launch_scale_to_df(V[0], 1.0 / beta, n, L.f32, ctx->stream));
+    else CK(launch_axpby(0.0, V[0], 1.0 / beta, V[0], n, ctx->stream));
     ctx->launches += 1;
     std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), cs(m, 0.0), sn(m, 0.0);
     g[0] = beta;
@@ -1539,10 +1548,9 @@ stmg_status stmg_destroy(stmg_ctx* ctx) {
   if (!ctx) return STMG_OK;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (stmg_net* net : ctx->nets) net_detach(net);
-  for (auto g : ctx->iter_graphs)
-    if (g) cudaGraphExecDestroy(g);
-  for (auto g : ctx->iter_graphs_low)
-    if (g) cudaGraphExecDestroy(g);
+  for (auto& gv : ctx->iter_graphs)
+    for (auto g : gv)
+      if (g) cudaGraphExecDestroy(g);
   if (ctx->graph32) cudaGraphExecDestroy(ctx->graph32);
   if (ctx->graph64) cudaGraphExecDestroy(ctx->graph64);
   for (void* p : ctx->allocations) cudaFree(p);

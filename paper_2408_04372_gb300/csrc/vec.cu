@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "kernels.h"
 
 namespace stmg {
@@ -12,6 +13,17 @@ namespace {
 
 constexpr int kMaxVec = 72;
 constexpr int kCgsThreads = 256;
+
+// Nearest double-float to an FP64 value (hi = x rounded to float, lo = the rounded remainder).
+__device__ __forceinline__ df64 df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return df64(h, __double2float_rn(x - (double)h));
+}
+// Renormalised pair (Fast2Sum): hi becomes the float nearest to hi + lo.
+__device__ __forceinline__ df64 df_renorm(df64 a) {
+  const float h = __fadd_rn(a.hi, a.lo);
+  return df64(h, __fsub_rn(a.lo, __fsub_rn(h, a.hi)));
+}
 constexpr int kCgsBlocks = 152 * 4;
 
 inline int grid_blocks(int64_t total) {
@@ -32,6 +44,19 @@ __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, d
   pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
+}
+
+// x (FP64) * scale written over x as double-float pairs, and its FP32 copy (the first Krylov vector
+// of a double-float basis and the first V-cycle input, from the restart residual)
+__global__ void scale_to_df_kernel(double* __restrict__ x, double scale, int64_t n, float* __restrict__ y32) {
+  pdl_wait();
+  pdl_trigger();
+  float2* xd = reinterpret_cast<float2*>(x);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const df64 v = df_from_double(x[i] * scale);
+    xd[i] = make_float2(v.hi, v.lo);
+    if (y32) y32[i] = v.hi;
+  }
 }
 
 // x *= sc[0]; with y32, also y32 = (float) x (the next V-cycle's input, written in the same pass)
@@ -199,13 +224,18 @@ template <> struct CgsTma<32> { static constexpr int E = 128, S = 3, BPS = 1; };
 template <> struct CgsTma<64> { static constexpr int E = 64, S = 3, BPS = 1; };
 template <int K> constexpr size_t cgs_tma_smem() { return (size_t)CgsTma<K>::S * (K + 1) * CgsTma<K>::E * sizeof(double); }
 
-template <int K>
+// DFV: the basis and w hold double-float pairs (hi, lo) in their 8 bytes per entry and the pass
+// computes in double-float arithmetic on the FP32 pipe (GB300 issues FP64 at 1/64 of the FP32 rate,
+// and the FP64 pass is bound by the FP64 pipe); w64: w arrives in FP64 (the operator's output) and
+// is written back as a pair.  Dot products and norms are summed per thread in double-float and
+// reduced across threads and blocks in FP64 as in the FP64 pass.
+template <int K, bool DFV>
 __global__ void __launch_bounds__(kCgsThreads)
 cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
                     const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev,
                     int fin, double* __restrict__ partial, unsigned int* __restrict__ counter,
                     double* __restrict__ out, int* status, const double* __restrict__ nrm2,
-                    float* __restrict__ copy32) {
+                    float* __restrict__ copy32, int w64) {
   pdl_wait();
   pdl_trigger();
   constexpr int E = CgsTma<K>::E, S = CgsTma<K>::S;
@@ -249,6 +279,16 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   double acc[K + 1];
 #pragma unroll
   for (int j = 0; j <= K; ++j) acc[j] = 0.0;
+  df_acc accd[DFV ? K + 1 : 1];
+#pragma unroll
+  for (int j = 0; j < (DFV ? K + 1 : 1); ++j) accd[j] = df_acc(0.0f);
+  __shared__ df64 csd[DFV ? K : 1];
+  df64 invd(0.0f);
+  if constexpr (DFV) {
+    for (int j = tid; j < K; j += blockDim.x) csd[j] = df_from_double(cs[j]);
+    invd = df_from_double(inv);
+    __syncthreads();
+  }
   int64_t issued = 0, k = 0;
   if (!fail) {
     if (tid == 0)
@@ -270,6 +310,44 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
       const int64_t e0 = ch * E;
       const int ne = (int)(n - e0 < E ? n - e0 : E);
       const int nin = (int)(main_bytes(ch) / sizeof(double));  // elements that came by bulk copy
+      if constexpr (DFV) {
+        const float2* bufd = reinterpret_cast<const float2*>(buf);
+        const float2* V0d = reinterpret_cast<const float2*>(V0);
+        float2* wd = reinterpret_cast<float2*>(w);
+        for (int e = tid; e < ne; e += kCgsThreads) {
+          const bool in = e < nin;
+          auto vj = [&](int j) {
+            const float2 v = in ? bufd[j * E + e] : V0d[j * stride + e0 + e];
+            return df64(v.x, v.y);
+          };
+          df64 wi;
+          if (w64) {
+            wi = df_from_double(in ? buf[nv * E + e] : w[e0 + e]);
+          } else {
+            const float2 v = in ? bufd[nv * E + e] : wd[e0 + e];
+            wi = df64(v.x, v.y);
+          }
+          if (sub) {
+            df_acc sv(0.0f);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              if (j < nv) sv += csd[j] * vj(j);
+            const df64 s = sv;
+            wi = df_add(wi, df64(-s.hi, -s.lo));
+            if (nrm2) {
+              wi = df_renorm(wi * invd);
+              if (copy32) copy32[e0 + e] = wi.hi;
+            }
+          }
+          if (sub || w64) wd[e0 + e] = make_float2(wi.hi, wi.lo);
+          if (dot) {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              if (j < nv) accd[j] += vj(j) * wi;
+          }
+          if (norm) accd[K] += wi * wi;
+        }
+      } else
       for (int e = tid; e < ne; e += kCgsThreads) {
         const bool in = e < nin;
         // basis entries straight from the stage (read twice rather than kept in registers)
@@ -307,6 +385,13 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
     }
   } else {
     return;
+  }
+  if constexpr (DFV) {
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const df64 v = accd[j];
+      acc[j] = (double)v.hi + (double)v.lo;
+    }
   }
   // block partials, then the last block sums them in block order (as in cgs_pass_kernel)
 #pragma unroll
@@ -464,6 +549,11 @@ cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t
   return cudaGetLastError();
 }
 
+cudaError_t launch_scale_to_df(double* x, double scale, int64_t n, float* copy32, cudaStream_t s) {
+  { const cudaError_t e_ = launch_k(scale_to_df_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, x, scale, n, copy32); if (e_ != cudaSuccess) return e_; }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaStream_t s, float* copy32) {
   { const cudaError_t e_ = launch_k(scale_by_device_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, x, sc, n, copy32); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
@@ -471,33 +561,37 @@ cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaS
 
 int cgs_blocks() { return kCgsBlocks; }
 
-template <int K>
+template <int K, bool DFV>
 cudaError_t launch_cgs_tma(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                            int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                           double* out, int* status, cudaStream_t s, const double* nrm2, float* copy32) {
+                           double* out, int* status, cudaStream_t s, const double* nrm2, float* copy32, int w64) {
   static bool attr = false;
-  auto k = cgs_pass_tma_kernel<K>;
+  auto k = cgs_pass_tma_kernel<K, DFV>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_tma_smem<K>());
     if (e != cudaSuccess) return e;
     attr = true;
   }
   { const cudaError_t e_ = launch_k(k, dim3(152 * CgsTma<K>::BPS), dim3(kCgsThreads), cgs_tma_smem<K>(), s, V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin,
-                                                                 partial, counter, out, status, nrm2, copy32); if (e_ != cudaSuccess) return e_; }
+                                                                 partial, counter, out, status, nrm2, copy32, w64); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w, int64_t n, const double* c, int sub,
                             int dot, int norm, const double* h_prev, int fin, double* partial, unsigned int* counter,
-                            double* out, cudaStream_t s, int* status, const double* nrm2, float* copy32) {
+                            double* out, cudaStream_t s, int* status, const double* nrm2, float* copy32,
+                            int vfmt) {
   if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
   if (nrm2 && (!fin || norm || !sub)) return cudaErrorInvalidValue;
   // bulk copies need 16-byte aligned sources: w, V0 and the stride between basis vectors
   const bool aligned = ((uintptr_t)w % 16 == 0) && (nv == 0 || (((uintptr_t)V0 % 16 == 0) && stride % 2 == 0));
+  if (vfmt != 0 && !(status && aligned)) return cudaErrorInvalidValue;  // double-float: bulk-copy pass only
   if (status && aligned) {
-#define STMG_CGS_TMA(KK) \
-  return launch_cgs_tma<KK>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter, out, status, s, \
-                            nrm2, copy32)
+#define STMG_CGS_TMA(KK)                                                                                              \
+  return vfmt == 0 ? launch_cgs_tma<KK, false>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter,  \
+                                               out, status, s, nrm2, copy32, 0)                                       \
+                   : launch_cgs_tma<KK, true>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter,   \
+                                              out, status, s, nrm2, copy32, vfmt == 2)
     if (nv <= 4) STMG_CGS_TMA(4);
     if (nv <= 8) STMG_CGS_TMA(8);
     if (nv <= 16) STMG_CGS_TMA(16);
