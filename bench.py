@@ -246,7 +246,8 @@ def run_kernel_only(args):
     kind, prec = {"apply64": (stmg.KERNEL_APPLY, stmg.FP64), "apply32": (stmg.KERNEL_APPLY, stmg.FP32),
                   "applydf": (stmg.KERNEL_APPLY, stmg.DF32),
                   "asm32": (stmg.KERNEL_ASM, stmg.FP32), "asm64": (stmg.KERNEL_ASM, stmg.FP64),
-                  "vcycle32": (stmg.KERNEL_VCYCLE, stmg.FP32), "vcycle64": (stmg.KERNEL_VCYCLE, stmg.FP64)}[args.only_kernel]
+                  "vcycle32": (stmg.KERNEL_VCYCLE, stmg.FP32), "vcycle64": (stmg.KERNEL_VCYCLE, stmg.FP64),
+                  "ortho64": (stmg.KERNEL_ORTHO, stmg.FP64), "orthodf": (stmg.KERNEL_ORTHO, stmg.DF32)}[args.only_kernel]
     ms = ctx.time_kernel(kind, args.level, prec, reps=args.steps)
     print(json.dumps({"kernel": args.only_kernel, "level": args.level, "avg_launch_ms": ms, "workload": wl["name"]}))
     ctx.close()
@@ -1168,9 +1169,10 @@ def main():
                     help="local solver of the Schwarz smoother: stored inverse planes (dense) or per-cell "
                          "eigendecompositions (eig)")
     ap.add_argument("--only-kernel", default=None,
-                    choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64", "net"],
+                    choices=["apply64", "apply32", "applydf", "asm32", "asm64", "vcycle32", "vcycle64", "ortho64", "orthodf", "net"],
                     help="profiling helper: time one kernel only (fixed omega, no Arnoldi)")
-    ap.add_argument("--level", type=int, default=0, help="multigrid level of --only-kernel (0 = finest)")
+    ap.add_argument("--level", type=int, default=0,
+                    help="multigrid level of --only-kernel (0 = finest); for ortho64 and orthodf the basis size")
     ap.add_argument("--asm-weighting", type=int, default=1, choices=[0, 1],
                     help="1: each cell's Schwarz correction divided by the node's cell count (reading of the "
                          "paper's omega range and iteration tables); 0: the sum of eq. vanka0 as printed")

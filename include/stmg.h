@@ -303,8 +303,11 @@ stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count);
  * stream.  kernel: STMG_KERNEL_APPLY (the operator kernel alone, no row
  * initialisation), STMG_KERNEL_ASM (one additive Schwarz application) or
  * STMG_KERNEL_VCYCLE (one whole V-cycle from level 0; level must be 0).  Synchronous.
- * precision STMG_DF32 times the double-float level-0 apply (outer_apply = STMG_DF32). */
-enum { STMG_KERNEL_APPLY = 1, STMG_KERNEL_ASM = 2, STMG_KERNEL_VCYCLE = 3 };
+ * precision STMG_DF32 times the double-float level-0 apply (outer_apply = STMG_DF32).
+ * STMG_KERNEL_ORTHO: one FGMRES orthogonalisation (the three Gram-Schmidt passes) of a level-0
+ * vector against `level` basis vectors (1..fgmres_restart), the basis in FP64 (precision
+ * STMG_FP64) or in double-float pairs (STMG_DF32); the Krylov workspace is overwritten. */
+enum { STMG_KERNEL_APPLY = 1, STMG_KERNEL_ASM = 2, STMG_KERNEL_VCYCLE = 3, STMG_KERNEL_ORTHO = 4 };
 /* Test hook for failure detection (no counterpart in the paper).  Runs one kernel whose bounded
  * device wait cannot complete: it gives up after about one second and records the timeout in the
  * context's device status word, exactly as a bulk copy that never lands would.  Nothing faults.

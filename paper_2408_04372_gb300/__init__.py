@@ -31,7 +31,7 @@ EXPORTS = ["stmg_create", "stmg_destroy", "stmg_last_error", "stmg_sizes", "stmg
            "stmg_time_kernel", "stmg_smooth_noalloc", "stmg_net_create", "stmg_net_destroy", "stmg_net_predict",
            "stmg_net_train_step", "stmg_net_gradients", "stmg_net_weights", "stmg_select_guess",
            "stmg_solve_slab_host_learned", "stmg_selftest_device_timeout", "stmg_level_slabs", "stmg_point_values"]
-KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE = 1, 2, 3
+KERNEL_APPLY, KERNEL_ASM, KERNEL_VCYCLE, KERNEL_ORTHO = 1, 2, 3, 4
 
 
 class StmgError(RuntimeError):

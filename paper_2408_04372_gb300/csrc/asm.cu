@@ -378,6 +378,21 @@ __device__ __forceinline__ void tma_bulk_load(void* dst, const void* src, uint32
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// The same for the stored inverses, read once per sweep: marked evict-first in L2, so that the stream
+// does not push out the residual and correction vectors, which every cell's threads gather and update.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void tma_bulk_load_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                     uint64_t pol) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol) : "memory");
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -448,11 +463,12 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
   __syncthreads();
   // prologue: the first S groups of this CTA
   int64_t issued = 0;  // groups issued by this CTA (thread 0's count; all threads track it alike)
+  const uint64_t pol = l2_evict_first_policy();
   if (tid == 0)
     for (int s = 0; s < S; ++s) {
       const int64_t grp = blockIdx.x + (int64_t)s * gridDim.x;
       if (grp < ngroups)
-        tma_bulk_load(smem_raw + (size_t)s * C::STAGE_BYTES, inv + grp * CPG * CS, group_bytes(grp), &bar[s]);
+        tma_bulk_load_stream(smem_raw + (size_t)s * C::STAGE_BYTES, inv + grp * CPG * CS, group_bytes(grp), &bar[s], pol);
     }
   for (int s = 0; s < S; ++s)
     if (blockIdx.x + (int64_t)s * gridDim.x < ngroups) ++issued;
@@ -578,7 +594,7 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
     const int64_t next = grp + (int64_t)S * gridDim.x;
     if (next < ngroups) {
       if (tid == 0)
-        tma_bulk_load(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage]);
+        tma_bulk_load_stream(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage], pol);
       ++issued;
     }
     cur = nxt;  // the next group's first slab
@@ -587,6 +603,216 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
   if (s_fail) {
     for (int64_t q = k; q < issued; ++q) mbar_wait(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
   }
+}
+
+// Several slabs in one system, FP32 vectors, BF16 inverses (cells of at most 27 nodes): after a group's
+// planes land, each thread keeps its NT rows (packed BF16, NT * NBP / 2 registers) and the stage is
+// released at once, so the next group's copy starts before this group's work; the slabs then run in
+// batches of up to SB: every thread loads the batch's residuals at its node together, forms the modal
+// residuals, and after one barrier multiplies each slab's modal residual by its rows from registers.
+// Two barriers per batch instead of two per slab, and the stored rows are read from shared memory once
+// per group.
+constexpr int kMultiSB = 8;
+template <int DIM, int N, int NT>
+struct MultiCfg {
+  using C = TmaCfg<DIM, N, NT, __nv_bfloat16>;
+  static constexpr int NBP = nb_pad(C::NB);
+  static constexpr size_t SR_BYTES = (size_t)C::CPG * kMultiSB * NT * NBP * sizeof(float);
+  static constexpr size_t SMEM = C::SMEM + SR_BYTES;
+};
+
+__device__ __forceinline__ float2 bf16x2_lo_hi(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+template <int DIM, int N, int NT>
+__global__ void __launch_bounds__(TmaCfg<DIM, N, NT, __nv_bfloat16>::THREADS, 4)
+asm_multi_rows_kernel(const float* __restrict__ r, float* __restrict__ u, const __nv_bfloat16* __restrict__ inv,
+                      GridDesc g, ModeTab<float> mt, const float* __restrict__ copy_src, float* __restrict__ copy_dst,
+                      int* status, int nslab, int64_t slab_stride) {
+  pdl_wait();
+  pdl_trigger();
+  using C = TmaCfg<DIM, N, NT, __nv_bfloat16>;
+  constexpr int NB = C::NB, CPG = C::CPG, S = C::S, SB = kMultiSB;
+  constexpr int64_t CS = C::CS;
+  constexpr int NBP = nb_pad(NB), NW = NBP / 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float (*s_r)[SB][NT][NBP] = reinterpret_cast<float (*)[SB][NT][NBP]>(smem_raw + C::SMEM);
+  __shared__ __align__(8) uint64_t bar[S];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  const int64_t ngroups = (g.n_cells + CPG - 1) / CPG;
+  auto group_bytes = [&](int64_t grp) -> uint32_t {
+    const int64_t c0 = grp * CPG;
+    const int64_t nc = g.n_cells - c0 < CPG ? g.n_cells - c0 : CPG;
+    return (uint32_t)(nc * C::CELL_BYTES);
+  };
+  if (tid == 0) s_fail = *reinterpret_cast<const volatile int*>(status);
+  for (int i = tid; i < CPG * SB * NT * NBP; i += blockDim.x) (&s_r[0][0][0][0])[i] = 0.0f;
+  __syncthreads();
+  if (s_fail) return;
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[st])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  int64_t issued = 0;
+  const uint64_t pol = l2_evict_first_policy();
+  if (tid == 0)
+    for (int st = 0; st < S; ++st) {
+      const int64_t grp = blockIdx.x + (int64_t)st * gridDim.x;
+      if (grp < ngroups)
+        tma_bulk_load_stream(smem_raw + (size_t)st * C::STAGE_BYTES, inv + grp * CPG * CS, group_bytes(grp), &bar[st], pol);
+    }
+  for (int st = 0; st < S; ++st)
+    if (blockIdx.x + (int64_t)st * gridDim.x < ngroups) ++issued;
+  const int slot = tid / NB, a = tid - slot * NB;
+  int64_t k = 0;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++k) {
+    const int stage = (int)(k % S);
+    const uint32_t parity = (uint32_t)((k / S) & 1);
+    const int64_t cell = grp * CPG + slot;
+    const bool active = slot < CPG && cell < g.n_cells;
+    int64_t node = 0;
+    bool live = false;
+    if (active) {
+      int cx, cy, cz;
+      cell_xyz(cell, g, cx, cy, cz);
+      const int gx = cx * g.p + a % N, gy = cy * g.p + (a / N) % N;
+      const int gz = DIM == 3 ? cz * g.p + a / (N * N) : 0;
+      bool bnd = on_boundary(gx, g.nn1) || on_boundary(gy, g.nn1);
+      if (DIM == 3) bnd = bnd || on_boundary(gz, g.nn1);
+      node = gx + (int64_t)g.nn1 * (gy + (int64_t)g.nn1 * gz);
+      live = !bnd;
+    }
+    if (!mbar_wait(&bar[stage], parity, status)) {
+      atomicExch(status, STMG_DEVICE_TIMEOUT);
+      s_fail = 1;
+    }
+    // this thread's rows (planes 0..NT-1, row a) from the landed stage, kept packed
+    uint32_t rw[NT][NW];
+    if (active && live && !s_fail) {
+      const __nv_bfloat16* ic =
+          reinterpret_cast<const __nv_bfloat16*>(smem_raw + (size_t)stage * C::STAGE_BYTES) + slot * CS;
+#pragma unroll
+      for (int m = 0; m < NT; ++m) {
+        const uint2* src = reinterpret_cast<const uint2*>(ic + (m * NB + a) * NBP);
+#pragma unroll
+        for (int c = 0; c < NW / 2; ++c) {
+          const uint2 v = src[c];
+          rw[m][2 * c] = v.x;
+          rw[m][2 * c + 1] = v.y;
+        }
+      }
+    }
+    __syncthreads();  // every thread holds its rows: the stage is free
+    if (s_fail) break;
+    const int64_t next = grp + (int64_t)S * gridDim.x;
+    if (next < ngroups) {
+      if (tid == 0)
+        tma_bulk_load_stream(smem_raw + (size_t)stage * C::STAGE_BYTES, inv + next * CPG * CS, group_bytes(next), &bar[stage], pol);
+      ++issued;
+    }
+    for (int b0 = 0; b0 < nslab; b0 += SB) {
+      // modal residuals of the batch's slabs at this thread's node
+      if (active) {
+        float rr[SB][NT];
+#pragma unroll
+        for (int sb = 0; sb < SB; ++sb)
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const int64_t o = (int64_t)(b0 + sb) * slab_stride + t * g.n_nodes + node;
+            rr[sb][t] = (b0 + sb < nslab && live) ? r[o] : 0.0f;
+            if (copy_dst && b0 + sb < nslab) copy_dst[o] = copy_src[o];
+          }
+#pragma unroll
+        for (int sb = 0; sb < SB; ++sb)
+#pragma unroll
+          for (int m = 0; m < NT; ++m) {
+            const bool is_real = m < mt.nreal;
+            const int mode = is_real ? m : mt.nreal + (m - mt.nreal) / 2;
+            const bool im_part = !is_real && ((m - mt.nreal) & 1);
+            float v = 0.0f;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) v += (im_part ? mt.Wi[mode][t] : mt.Wr[mode][t]) * rr[sb][t];
+            s_r[slot][sb][m][a] = v;
+          }
+      }
+      __syncthreads();
+      if (active && live) {
+#pragma unroll 1
+        for (int sb = 0; sb < SB; ++sb) {
+          if (b0 + sb >= nslab) break;
+          const float* sr = &s_r[slot][sb][0][0];
+          // row m against modal residual q: the dot products each mode needs
+          auto dot = [&](int m, int q) {
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < NBP / 4; ++c) {
+              const float4 v = *reinterpret_cast<const float4*>(sr + q * NBP + 4 * c);
+              a0 = __ffma2_rn(bf16x2_lo_hi(rw[m][2 * c]), make_float2(v.x, v.y), a0);
+              a1 = __ffma2_rn(bf16x2_lo_hi(rw[m][2 * c + 1]), make_float2(v.z, v.w), a1);
+            }
+            return (a0.x + a0.y) + (a1.x + a1.y);
+          };
+          float z[NT];
+#pragma unroll
+          for (int m = 0; m < NT; ++m) {
+            if (m < mt.nreal) {
+              z[m] = dot(m, m);
+            } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+              z[m] = dot(m, m) - dot(m + 1, m + 1);
+              z[m + 1] = dot(m, m + 1) + dot(m + 1, m);
+            }
+          }
+          const int64_t so = (int64_t)(b0 + sb) * slab_stride;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            float o = 0.0f;
+#pragma unroll
+            for (int m = 0; m < NT; ++m) {
+              if (m < mt.nreal) {
+                o += mt.Vr[t][m] * z[m];
+              } else if (m + 1 < NT && ((m - mt.nreal) & 1) == 0) {
+                const int mode = mt.nreal + (m - mt.nreal) / 2;
+                o += 2.0f * (mt.Vr[t][mode] * z[m] - mt.Vi[t][mode] * z[m + 1]);
+              }
+            }
+            atomicAdd(u + so + t * g.n_nodes + node, mt.omega * o);
+          }
+        }
+      }
+      __syncthreads();  // s_r free again
+    }
+  }
+  if (s_fail) {
+    for (int64_t q = k; q < issued; ++q) mbar_wait(&bar[q % S], (uint32_t)((q / S) & 1), nullptr);
+  }
+}
+
+template <int DIM, int N, int NT>
+cudaError_t launch_multi_rows(const float* r, float* u, const void* inv, const GridDesc& g, const ModeTab<float>& mt,
+                              const float* cs, float* cd, int* status, int nslab, int64_t ss, cudaStream_t s) {
+  using C = TmaCfg<DIM, N, NT, __nv_bfloat16>;
+  using M = MultiCfg<DIM, N, NT>;
+  auto k = asm_multi_rows_kernel<DIM, N, NT>;
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::THREADS, M::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t groups = (g.n_cells + C::CPG - 1) / C::CPG;
+  const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+  { const cudaError_t e_ = launch_k(k, dim3((unsigned)grid), dim3(C::THREADS), M::SMEM, s, r, u, reinterpret_cast<const __nv_bfloat16*>(inv), g, mt, cs, cd, status, nslab, ss); if (e_ != cudaSuccess) return e_; }
+  return cudaGetLastError();
 }
 
 template <int DIM, int N>
@@ -645,6 +871,10 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
     }
     return cudaGetLastError();
     }
+  }
+  if constexpr (std::is_same<T, float>::value && std::is_same<TI, __nv_bfloat16>::value &&
+                Shape<DIM, N>::NB <= 27) {
+    if (nslab > 1) return launch_multi_rows<DIM, N, NT>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);
   }
   return nslab > 1 ? launch_tma<DIM, N, NT, T, TI, true>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s)
                    : launch_tma<DIM, N, NT, T, TI, false>(r, u, inv, g, mt, cs, cd, status, 1, ss, s);

@@ -2172,6 +2172,30 @@ stmg_status stmg_launch_count(const stmg_ctx* ctx, int64_t* count) {
 }
 
 stmg_status stmg_time_kernel(stmg_ctx* ctx, int kernel, int level, int precision, int reps, double* avg_ms) {
+  if (kernel == STMG_KERNEL_ORTHO) {
+    if (!ctx || level < 1 || level > ctx->m || reps < 1 || !avg_ms ||
+        (precision != STMG_FP64 && precision != STMG_DF32))
+      return invalid(ctx, "ortho timing: 1 <= level <= fgmres_restart basis vectors, FP64 or DF32, reps >= 1");
+    const int64_t n = ctx->levels[0].size();
+    const bool dfb = precision == STMG_DF32;
+    // a basis and a vector with nonzero entries (timing only: byte pattern 0x3f in every word)
+    CK(cudaMemsetAsync(ctx->V, 0x3f, sizeof(double) * (size_t)(level + 1) * ctx->vld, ctx->stream));
+    double* w = ctx->V + (size_t)level * ctx->vld;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CKS(orthogonalise_enqueue(ctx, ctx->V, ctx->vld, level, w, n, ctx->levels[0].f32, nullptr, dfb));
+    CK(cudaEventRecord(a, ctx->stream));
+    for (int i = 0; i < reps; ++i) CKS(orthogonalise_enqueue(ctx, ctx->V, ctx->vld, level, w, n, ctx->levels[0].f32, nullptr, dfb));
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *avg_ms = (double)ms / reps;
+    return STMG_OK;
+  }
   const bool df = precision == STMG_DF32;
   if (df && (!ctx || kernel != STMG_KERNEL_APPLY || level != 0 || !ctx->levels[0].geodf))
     return invalid(ctx, "DF32 timing exists for the level-0 apply of a context with outer_apply = DF32");

@@ -77,7 +77,7 @@ __global__ void scale_by_device_kernel(double* __restrict__ x, const double* __r
 //   dot : s_j = V_j . w, j < nv            (after the subtraction)
 //   norm: s_nv = w . w                     (after the subtraction)
 // Every block reduces a fixed contiguous slice; the last block to arrive sums the per-block
-// partials in block order, so the results do not depend on scheduling.  It then writes
+// partials in a fixed order (final_sums), so the results do not depend on scheduling.  It then writes
 //   fin 0: out[j] = s_j (j < nv) and out[nv] = s_nv when norm is set;
 //   fin 1: the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = sqrt(s_nv), out[nv+1] = 1/out[nv].
 // nrm2 (fin 1 only, norm unset): the pass also normalises.  nrm2[0] is |w|^2 before this pass's
@@ -87,12 +87,78 @@ __global__ void scale_by_device_kernel(double* __restrict__ x, const double* __r
 // one launch fewer than a separate normalisation.
 // One thread keeps the K values V_j[i] of its element in registers between the subtraction and
 // the dot products, so every basis vector is read once per pass.
+// Final fixed-order sums over the nb per-block partials of every needed slot j (j < nv with dot, slot K
+// with norm), by all THREADS threads of the last block: thread t adds blocks t, t + THREADS, ... for
+// eight slots at a time (all those loads issued together), then a fixed warp-shuffle tree and a fixed
+// sum over the warps.  The order does not depend on scheduling, so the result is bit-reproducible.
+template <int K, int THREADS>
+__device__ __forceinline__ void final_sums(const double* __restrict__ partial, int nb, int nv, int dot, int norm,
+                                           double (*red)[K + 1], double* tot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int JC = 8;
+#pragma unroll 1
+  for (int j0 = 0; j0 <= K; j0 += JC) {
+    double x[JC];
+#pragma unroll
+    for (int i = 0; i < JC; ++i) x[i] = 0.0;
+    for (int b = tid; b < nb; b += THREADS) {
+#pragma unroll
+      for (int i = 0; i < JC; ++i) {
+        const int j = j0 + i;
+        if (j <= K && ((j < K && dot && j < nv) || (j == K && norm))) x[i] += __ldcg(partial + (int64_t)j * nb + b);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      const int j = j0 + i;
+      if (j <= K && ((j < K && dot && j < nv) || (j == K && norm))) {
+        double v = x[i];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][j] = v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j <= K; j += THREADS) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double v = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) v += red[w][j];
+      tot[j] = v;
+    }
+  }
+}
+
 // sqrt(|w|^2 - |c|^2) (0 when the difference is not positive: w lies in the span of the basis)
 __device__ __forceinline__ double fused_norm(double w2, const double* cs, int nv) {
   double c2 = 0.0;
   for (int j = 0; j < nv; ++j) c2 += cs[j] * cs[j];
   const double d = w2 - c2;
   return d > 0.0 ? sqrt(d) : 0.0;
+}
+
+// The norm h = sqrt(nrm2[0] - |c|^2) of the subtracted vector and 1 / h, formed once per block by thread 0
+// (FP64 square root and division are slow on this GPU's FP64 pipe, and every thread needs the same values).
+__device__ __forceinline__ void block_fused_norm(const double* nrm2, const double* cs, int nv, double* s_hn,
+                                                 double* s_inv) {
+  if (threadIdx.x == 0) {
+    const double h = nrm2 ? fused_norm(nrm2[0], cs, nv) : 0.0;
+    *s_hn = h;
+    *s_inv = h > 0.0 ? 1.0 / h : 0.0;
+  }
+  __syncthreads();
+}
+
+// Sum of a double-float value over the warp in double-float arithmetic (FP32 pipe); lane 0 returns it in FP64.
+__device__ __forceinline__ double warp_sum_df(df_acc a) {
+  df64 v = a;
+  df_acc s(v);
+  for (int off = 16; off > 0; off >>= 1) {
+    const df64 cur = s;
+    const df64 o(__shfl_down_sync(0xffffffffu, cur.hi, off), __shfl_down_sync(0xffffffffu, cur.lo, off));
+    s += o;
+  }
+  const df64 r = s;
+  return (double)r.hi + (double)r.lo;
 }
 
 template <int K>
@@ -107,10 +173,11 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
   __shared__ double cs[K];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double s_hn, s_inv;
   for (int j = threadIdx.x; j < K; j += blockDim.x) cs[j] = (sub && j < nv) ? c[j] : 0.0;
   __syncthreads();
-  const double hn_fused = nrm2 ? fused_norm(nrm2[0], cs, nv) : 0.0;
-  const double inv = hn_fused > 0.0 ? 1.0 / hn_fused : 0.0;
+  block_fused_norm(nrm2, cs, nv, &s_hn, &s_inv);
+  const double hn_fused = s_hn, inv = s_inv;
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
   double acc[K + 1];
@@ -162,16 +229,8 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // fixed-order sums over blocks: warp w takes slots w, w + 8, ...
   __shared__ double tot[K + 1];
-  for (int j = warp; j <= K; j += kCgsThreads / 32) {
-    if ((j < K && dot && j < nv) || (j == K && norm)) {
-      double x = 0.0;
-      for (int b = lane; b < nb; b += 32) x += __ldcg(partial + (int64_t)j * nb + b);
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-      if (lane == 0) tot[j] = x;
-    }
-  }
+  final_sums<K, kCgsThreads>(partial, nb, nv, dot, norm, red, tot);
   __syncthreads();
   if (fin == 0) {
     for (int j = threadIdx.x; j < nv; j += blockDim.x)
@@ -186,6 +245,164 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
     }
   }
   if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ---- double-float pass with direct loads (basis widths up to 16) ----
+// The basis and w hold double-float pairs (w in FP64 when w64, converted and written back); each thread
+// takes two consecutive elements of every vector with one 16-byte load, all nv + 1 loads of a pair issued
+// before they are used, so that every SM keeps well over 100 KB in flight; the last element of an odd
+// n is taken by one thread.  Results, reduction order and side outputs as in the FP64 passes.
+constexpr int kCgsDfThreads = 256;
+template <int K> struct CgsDf;
+template <> struct CgsDf<4> { static constexpr int BPS = 4; };
+template <> struct CgsDf<8> { static constexpr int BPS = 3; };
+template <> struct CgsDf<16> { static constexpr int BPS = 2; };
+
+template <int K>
+__global__ void __launch_bounds__(kCgsDfThreads, CgsDf<K>::BPS)
+cgs_pass_df_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
+                   const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev,
+                   int fin, double* __restrict__ partial, unsigned int* __restrict__ counter,
+                   double* __restrict__ out, const double* __restrict__ nrm2, float* __restrict__ copy32, int w64) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double red[kCgsDfThreads / 32][K + 1];
+  __shared__ double cs[K];
+  __shared__ df64 csd[K];
+  __shared__ bool last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double s_hn, s_inv;
+  __shared__ df64 s_invd;
+  for (int j = tid; j < K; j += blockDim.x) {
+    cs[j] = (sub && j < nv) ? c[j] : 0.0;
+    csd[j] = df_from_double(cs[j]);
+  }
+  __syncthreads();
+  block_fused_norm(nrm2, cs, nv, &s_hn, &s_inv);
+  if (tid == 0) s_invd = df_from_double(s_inv);
+  __syncthreads();
+  const double hn_fused = s_hn;
+  const df64 invd = s_invd;
+  df_acc acc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) acc[j] = df_acc(0.0f);
+  // one or two elements: e = 2p (+1); the pair's entries arrive together
+  auto step = [&](int64_t e, bool pair) {
+    df64 wv[2];
+    df64 vr[K][2];
+    if (pair) {
+      if (w64) {
+        const double2 d = *reinterpret_cast<const double2*>(w + e);
+        wv[0] = df_from_double(d.x);
+        wv[1] = df_from_double(d.y);
+      } else {
+        const float4 f = *reinterpret_cast<const float4*>(w + e);
+        wv[0] = df64(f.x, f.y);
+        wv[1] = df64(f.z, f.w);
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < nv) f = __ldg(reinterpret_cast<const float4*>(V0 + j * stride + e));
+        vr[j][0] = df64(f.x, f.y);
+        vr[j][1] = df64(f.z, f.w);
+      }
+    } else {
+      if (w64) {
+        wv[0] = df_from_double(w[e]);
+      } else {
+        const float2 f = *reinterpret_cast<const float2*>(w + e);
+        wv[0] = df64(f.x, f.y);
+      }
+      wv[1] = df64(0.0f);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        float2 f = make_float2(0.f, 0.f);
+        if (j < nv) f = *reinterpret_cast<const float2*>(V0 + j * stride + e);
+        vr[j][0] = df64(f.x, f.y);
+        vr[j][1] = df64(0.0f);
+      }
+    }
+    if (sub) {
+      df_acc sv[2] = {df_acc(0.0f), df_acc(0.0f)};
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j < nv) {
+          sv[0] += csd[j] * vr[j][0];
+          sv[1] += csd[j] * vr[j][1];
+        }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const df64 sm = sv[i];
+        wv[i] = df_add(wv[i], df64(-sm.hi, -sm.lo));
+        if (nrm2) wv[i] = df_renorm(wv[i] * invd);
+      }
+      if (!pair) wv[1] = df64(0.0f);
+    }
+    if (sub || w64) {
+      if (pair) *reinterpret_cast<float4*>(w + e) = make_float4(wv[0].hi, wv[0].lo, wv[1].hi, wv[1].lo);
+      else *reinterpret_cast<float2*>(w + e) = make_float2(wv[0].hi, wv[0].lo);
+    }
+    if (sub && nrm2 && copy32) {
+      if (pair) *reinterpret_cast<float2*>(copy32 + e) = make_float2(wv[0].hi, wv[1].hi);
+      else copy32[e] = wv[0].hi;
+    }
+    if (dot) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j < nv) {
+          acc[j] += vr[j][0] * wv[0];
+          acc[j] += vr[j][1] * wv[1];
+        }
+    }
+    if (norm) {
+      acc[K] += wv[0] * wv[0];
+      acc[K] += wv[1] * wv[1];
+    }
+  };
+  const int64_t npairs = n / 2;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + tid; p < npairs; p += (int64_t)gridDim.x * blockDim.x)
+    step(2 * p, true);
+  if ((n & 1) && blockIdx.x == 0 && tid == 0) step(n - 1, false);
+  // block partials, then the last block sums them in a fixed order (final_sums)
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      const double x = warp_sum_df(acc[j]);
+      if (lane == 0) red[warp][j] = x;
+    }
+  }
+  __syncthreads();
+  const int nb = gridDim.x;
+  for (int j = tid; j <= K; j += blockDim.x) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      double x = 0.0;
+      for (int wv = 0; wv < kCgsDfThreads / 32; ++wv) x += red[wv][j];
+      partial[(int64_t)j * nb + blockIdx.x] = x;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double tot[K + 1];
+  final_sums<K, kCgsDfThreads>(partial, nb, nv, dot, norm, red, tot);
+  __syncthreads();
+  if (fin == 0) {
+    for (int j = tid; j < nv; j += blockDim.x)
+      if (dot) out[j] = tot[j];
+    if (norm && tid == 0) out[nv] = tot[K];
+  } else {
+    for (int j = tid; j < nv; j += blockDim.x) out[j] = h_prev[j] + cs[j];
+    if (tid == 0) {
+      const double hn = nrm2 ? hn_fused : sqrt(fmax(tot[K], 0.0));
+      out[nv] = hn;
+      out[nv + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    }
+  }
+  if (tid == 0) *counter = 0u;
 }
 
 // ---- the same pass fed by bulk copies (TMA) ----
@@ -216,13 +433,23 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, const i
   }
 }
 
-template <int K> struct CgsTma;
-template <> struct CgsTma<4> { static constexpr int E = 1024, S = 2, BPS = 2; };
-template <> struct CgsTma<8> { static constexpr int E = 768, S = 2, BPS = 2; };
-template <> struct CgsTma<16> { static constexpr int E = 512, S = 2, BPS = 1; };
-template <> struct CgsTma<32> { static constexpr int E = 128, S = 3, BPS = 1; };
-template <> struct CgsTma<64> { static constexpr int E = 64, S = 3, BPS = 1; };
-template <int K> constexpr size_t cgs_tma_smem() { return (size_t)CgsTma<K>::S * (K + 1) * CgsTma<K>::E * sizeof(double); }
+// Chunk elements E, stages S and CTAs per SM of the bulk-copy pass.  FP64 passes are bound by the FP64
+// pipe: few large chunks.  Double-float passes run on the FP32 pipe, where the per-element chains need
+// more warps: smaller chunks, more CTAs per SM.
+template <int K, bool DFV> struct CgsTma;
+template <> struct CgsTma<4, false> { static constexpr int E = 1024, S = 2, BPS = 2; };
+template <> struct CgsTma<8, false> { static constexpr int E = 768, S = 2, BPS = 2; };
+template <> struct CgsTma<16, false> { static constexpr int E = 512, S = 2, BPS = 1; };
+template <> struct CgsTma<32, false> { static constexpr int E = 128, S = 3, BPS = 1; };
+template <> struct CgsTma<64, false> { static constexpr int E = 64, S = 3, BPS = 1; };
+template <> struct CgsTma<4, true> { static constexpr int E = 512, S = 2, BPS = 4; };
+template <> struct CgsTma<8, true> { static constexpr int E = 512, S = 2, BPS = 3; };
+template <> struct CgsTma<16, true> { static constexpr int E = 256, S = 2, BPS = 2; };
+template <> struct CgsTma<32, true> { static constexpr int E = 128, S = 3, BPS = 1; };
+template <> struct CgsTma<64, true> { static constexpr int E = 64, S = 3, BPS = 1; };
+template <int K, bool DFV> constexpr size_t cgs_tma_smem() {
+  return (size_t)CgsTma<K, DFV>::S * (K + 1) * CgsTma<K, DFV>::E * sizeof(double);
+}
 
 // DFV: the basis and w hold double-float pairs (hi, lo) in their 8 bytes per entry and the pass
 // computes in double-float arithmetic on the FP32 pipe (GB300 issues FP64 at 1/64 of the FP32 rate,
@@ -230,7 +457,7 @@ template <int K> constexpr size_t cgs_tma_smem() { return (size_t)CgsTma<K>::S *
 // is written back as a pair.  Dot products and norms are summed per thread in double-float and
 // reduced across threads and blocks in FP64 as in the FP64 pass.
 template <int K, bool DFV>
-__global__ void __launch_bounds__(kCgsThreads)
+__global__ void __launch_bounds__(kCgsThreads, CgsTma<K, DFV>::BPS)
 cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* __restrict__ w, int64_t n,
                     const double* __restrict__ c, int sub, int dot, int norm, const double* __restrict__ h_prev,
                     int fin, double* __restrict__ partial, unsigned int* __restrict__ counter,
@@ -238,7 +465,7 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
                     float* __restrict__ copy32, int w64) {
   pdl_wait();
   pdl_trigger();
-  constexpr int E = CgsTma<K>::E, S = CgsTma<K>::S;
+  constexpr int E = CgsTma<K, DFV>::E, S = CgsTma<K, DFV>::S;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[S];
   __shared__ double red[kCgsThreads / 32][K + 1];
@@ -257,8 +484,9 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  const double hn_fused = nrm2 ? fused_norm(nrm2[0], cs, nv) : 0.0;
-  const double inv = hn_fused > 0.0 ? 1.0 / hn_fused : 0.0;
+  __shared__ double s_hn, s_inv;
+  block_fused_norm(nrm2, cs, nv, &s_hn, &s_inv);
+  const double hn_fused = s_hn, inv = s_inv;
   auto main_bytes = [&](int64_t ch) -> uint32_t {
     const int64_t ne = n - ch * E < E ? n - ch * E : E;
     return (uint32_t)((ne * (int64_t)sizeof(double)) / 16 * 16);
@@ -284,10 +512,12 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   for (int j = 0; j < (DFV ? K + 1 : 1); ++j) accd[j] = df_acc(0.0f);
   __shared__ df64 csd[DFV ? K : 1];
   df64 invd(0.0f);
+  __shared__ df64 s_invd;
   if constexpr (DFV) {
     for (int j = tid; j < K; j += blockDim.x) csd[j] = df_from_double(cs[j]);
-    invd = df_from_double(inv);
+    if (tid == 0) s_invd = df_from_double(inv);
     __syncthreads();
+    invd = s_invd;
   }
   int64_t issued = 0, k = 0;
   if (!fail) {
@@ -311,41 +541,72 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
       const int ne = (int)(n - e0 < E ? n - e0 : E);
       const int nin = (int)(main_bytes(ch) / sizeof(double));  // elements that came by bulk copy
       if constexpr (DFV) {
+        // the thread's EPT elements of the chunk together (independent double-float chains), each
+        // basis entry read from the stage once for both the subtraction and the dot products
+        constexpr int EPT = (E + kCgsThreads - 1) / kCgsThreads;
         const float2* bufd = reinterpret_cast<const float2*>(buf);
         const float2* V0d = reinterpret_cast<const float2*>(V0);
         float2* wd = reinterpret_cast<float2*>(w);
-        for (int e = tid; e < ne; e += kCgsThreads) {
-          const bool in = e < nin;
-          auto vj = [&](int j) {
-            const float2 v = in ? bufd[j * E + e] : V0d[j * stride + e0 + e];
-            return df64(v.x, v.y);
-          };
-          df64 wi;
-          if (w64) {
-            wi = df_from_double(in ? buf[nv * E + e] : w[e0 + e]);
-          } else {
-            const float2 v = in ? bufd[nv * E + e] : wd[e0 + e];
-            wi = df64(v.x, v.y);
-          }
-          if (sub) {
-            df_acc sv(0.0f);
+        bool ok[EPT], in[EPT];
+        df64 wv[EPT];
+        df64 vr[K][EPT];
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-              if (j < nv) sv += csd[j] * vj(j);
-            const df64 s = sv;
-            wi = df_add(wi, df64(-s.hi, -s.lo));
-            if (nrm2) {
-              wi = df_renorm(wi * invd);
-              if (copy32) copy32[e0 + e] = wi.hi;
+        for (int i = 0; i < EPT; ++i) {
+          const int e = tid + i * kCgsThreads;
+          ok[i] = e < ne;
+          in[i] = e < nin;
+          if (!ok[i]) {
+            wv[i] = df64(0.0f);
+          } else if (w64) {
+            wv[i] = df_from_double(in[i] ? buf[nv * E + e] : w[e0 + e]);
+          } else {
+            const float2 v = in[i] ? bufd[nv * E + e] : wd[e0 + e];
+            wv[i] = df64(v.x, v.y);
+          }
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            vr[j][i] = df64(0.0f);
+            if (j < nv && ok[i]) {
+              const float2 v = in[i] ? bufd[j * E + e] : V0d[j * stride + e0 + e];
+              vr[j][i] = df64(v.x, v.y);
             }
           }
-          if (sub || w64) wd[e0 + e] = make_float2(wi.hi, wi.lo);
-          if (dot) {
+        }
+        if (sub) {
+          df_acc sv[EPT];
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-              if (j < nv) accd[j] += vj(j) * wi;
+          for (int i = 0; i < EPT; ++i) sv[i] = df_acc(0.0f);
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (j < nv) {
+#pragma unroll
+              for (int i = 0; i < EPT; ++i) sv[i] += csd[j] * vr[j][i];
+            }
+#pragma unroll
+          for (int i = 0; i < EPT; ++i) {
+            const df64 sm = sv[i];
+            df64 wi = df_add(wv[i], df64(-sm.hi, -sm.lo));
+            if (nrm2) wi = df_renorm(wi * invd);
+            wv[i] = ok[i] ? wi : df64(0.0f);
           }
-          if (norm) accd[K] += wi * wi;
+        }
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+          const int e = tid + i * kCgsThreads;
+          if (ok[i] && (sub || w64)) wd[e0 + e] = make_float2(wv[i].hi, wv[i].lo);
+          if (ok[i] && sub && nrm2 && copy32) copy32[e0 + e] = wv[i].hi;
+        }
+        if (dot) {
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (j < nv) {
+#pragma unroll
+              for (int i = 0; i < EPT; ++i) accd[j] += vr[j][i] * wv[i];
+            }
+        }
+        if (norm) {
+#pragma unroll
+          for (int i = 0; i < EPT; ++i) accd[K] += wv[i] * wv[i];
         }
       } else
       for (int e = tid; e < ne; e += kCgsThreads) {
@@ -386,19 +647,18 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   } else {
     return;
   }
-  if constexpr (DFV) {
-#pragma unroll
-    for (int j = 0; j <= K; ++j) {
-      const df64 v = accd[j];
-      acc[j] = (double)v.hi + (double)v.lo;
-    }
-  }
-  // block partials, then the last block sums them in block order (as in cgs_pass_kernel)
+  // block partials, then the last block sums them in a fixed order (final_sums); double-float sums are
+  // reduced over the warp in double-float and converted once per warp
 #pragma unroll
   for (int j = 0; j <= K; ++j) {
     if ((j < K && dot && j < nv) || (j == K && norm)) {
-      double x = acc[j];
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      double x;
+      if constexpr (DFV) {
+        x = warp_sum_df(accd[j]);
+      } else {
+        x = acc[j];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      }
       if (lane == 0) red[warp][j] = x;
     }
   }
@@ -418,14 +678,7 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   if (!last) return;
   __threadfence();
   __shared__ double tot[K + 1];
-  for (int j = warp; j <= K; j += kCgsThreads / 32) {
-    if ((j < K && dot && j < nv) || (j == K && norm)) {
-      double x = 0.0;
-      for (int b = lane; b < nb; b += 32) x += __ldcg(partial + (int64_t)j * nb + b);
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-      if (lane == 0) tot[j] = x;
-    }
-  }
+  final_sums<K, kCgsThreads>(partial, nb, nv, dot, norm, red, tot);
   __syncthreads();
   if (fin == 0) {
     for (int j = tid; j < nv; j += blockDim.x)
@@ -568,11 +821,11 @@ cudaError_t launch_cgs_tma(const double* V0, int64_t stride, int nv, double* w, 
   static bool attr = false;
   auto k = cgs_pass_tma_kernel<K, DFV>;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_tma_smem<K>());
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cgs_tma_smem<K, DFV>());
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  { const cudaError_t e_ = launch_k(k, dim3(152 * CgsTma<K>::BPS), dim3(kCgsThreads), cgs_tma_smem<K>(), s, V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin,
+  { const cudaError_t e_ = launch_k(k, dim3(152 * CgsTma<K, DFV>::BPS), dim3(kCgsThreads), cgs_tma_smem<K, DFV>(), s, V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin,
                                                                  partial, counter, out, status, nrm2, copy32, w64); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
@@ -585,7 +838,16 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
   if (nrm2 && (!fin || norm || !sub)) return cudaErrorInvalidValue;
   // bulk copies need 16-byte aligned sources: w, V0 and the stride between basis vectors
   const bool aligned = ((uintptr_t)w % 16 == 0) && (nv == 0 || (((uintptr_t)V0 % 16 == 0) && stride % 2 == 0));
-  if (vfmt != 0 && !(status && aligned)) return cudaErrorInvalidValue;  // double-float: bulk-copy pass only
+  if (vfmt != 0 && !(status && aligned)) return cudaErrorInvalidValue;  // double-float: aligned vectors only
+  if (vfmt != 0 && nv <= 16) {
+#define STMG_CGS_DF(KK)                                                                                        \
+  return launch_k(cgs_pass_df_kernel<KK>, dim3(152 * CgsDf<KK>::BPS), dim3(kCgsDfThreads), 0, s, V0, stride, nv, w, n, \
+                  c, sub, dot, norm, h_prev, fin, partial, counter, out, nrm2, copy32, (int)(vfmt == 2))
+    if (nv <= 4) STMG_CGS_DF(4);
+    if (nv <= 8) STMG_CGS_DF(8);
+    STMG_CGS_DF(16);
+#undef STMG_CGS_DF
+  }
   if (status && aligned) {
 #define STMG_CGS_TMA(KK)                                                                                              \
   return vfmt == 0 ? launch_cgs_tma<KK, false>(V0, stride, nv, w, n, c, sub, dot, norm, h_prev, fin, partial, counter,  \

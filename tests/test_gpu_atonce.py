@@ -190,3 +190,47 @@ def test_several_slabs_need_heat_dg(env):
     assert ei.value.status == 1
     with pytest.raises(stmg.StmgError):
         stmg.Context(2, 4, 1, 1, 0.1, pde=stmg.HEAT, scheme=stmg.CGP, n_slabs=2)
+
+
+@pytest.mark.parametrize("k,nc", [(2, 12), (1, 4)])
+def test_bf16_smoother_several_slabs_in_batches(env, k, nc):
+    """FP32 vectors and BF16 inverses (the stored rows kept in registers, slabs in batches of eight): one
+    sweep from u = 0 on every level of the hierarchy (12, 6, 3 slabs; Q2 and Q1 cells) against the
+    oracle's omega B f, and two sweeps on level 0, at 2e-2 (the BF16 tolerance of the plane store; measured
+    3.6e-3).  dG(2) has one real and one complex time mode, dG(1) a complex pair only.  The V-cycle is
+    compared with the FP64-arithmetic V-cycle over the same BF16 inverses (measured 2.7e-6): against the
+    oracle's exact inverses the BF16 V-cycle of the 12-slab hierarchy differs by 0.146 in either
+    arithmetic (5.9e-3 for one slab), an effect of the storage, not of the kernel."""
+    torch, stmg = env
+    from oracle import atonce
+    dim, N, p, tau = 3, 4, 2, 1 / 32
+    V = synth.jittered_vertices(N, dim)
+    rho = synth.block_coefficient(N, dim, blocks=2)
+    H = atonce.AtOnceHierarchy(dim, N, p, k, tau, nc, V, rho_cell=rho, estimate=False, omegas=[0.5] * 16)
+    kw = dict(vertices=V, coeff=rho, n_slabs=nc, omega=H.omegas(), inverse_precision=stmg.BF16)
+    ctx = stmg.Context(dim, N, p, k, tau, vcycle_precision=stmg.FP32, **kw)
+    for li, lev in enumerate(H.levels[:-1]):
+        prob = lev.prob
+        f = _rand(prob.n, 730 + li, prob.bmask_full)
+        ref = lev.omega * (lev.B @ f)
+        for _ in range(2):  # stages and registers reused call after call
+            u32 = torch.zeros(prob.n, dtype=torch.float32, device="cuda")
+            ctx.smooth(torch.from_numpy(f).to("cuda", torch.float32), u32, sweeps=1, level=li)
+            assert rel_err(u32.cpu().numpy(), ref) < 2e-2, (k, nc, li)
+    lev = H.levels[0]
+    prob = lev.prob
+    f = _rand(prob.n, 731, prob.bmask_full)
+    u1 = lev.omega * (lev.B @ f)
+    u2 = u1 + lev.omega * (lev.B @ (f - prob.S @ u1))
+    u32 = torch.zeros(prob.n, dtype=torch.float32, device="cuda")
+    ctx.smooth(torch.from_numpy(f).to("cuda", torch.float32), u32, sweeps=2, level=0)
+    assert rel_err(u32.cpu().numpy(), u2) < 2e-2, (k, nc)
+    r = _rand(prob.n, 740, prob.bmask_full)
+    e = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    ctx.vcycle(torch.from_numpy(r).to("cuda", torch.float32), e)
+    ctx.close()
+    ctx64 = stmg.Context(dim, N, p, k, tau, vcycle_precision=stmg.FP64, **kw)
+    e64 = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ctx64.vcycle(torch.from_numpy(r).cuda(), e64)
+    ctx64.close()
+    assert rel_err(e.cpu().numpy(), e64.cpu().numpy()) < 1e-5, (k, nc)
