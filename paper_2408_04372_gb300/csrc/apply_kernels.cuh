@@ -30,21 +30,24 @@ template <int N> constexpr int cells_per_block(int dim) {
                   : (N == 2 ? 64 : N == 3 ? 42 : N == 4 ? 32 : 25);
 }
 
-// Output accumulation: the result of every cell is added to its nodes' rows.
+// Output accumulation: the result of every cell is added to its nodes' rows.  Float and double-float
+// results enter FP64 rows through exact bit-field conversions (f2d_exact, df64.cuh), a double-float one
+// as two additions (hi, then lo): no FP64 instruction in the kernel, whose FP64 pipe is slow.
 __device__ __forceinline__ void add_out(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void add_out(double* p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void add_out(double* p, float v) { atomicAdd(p, (double)v); }
-__device__ __forceinline__ void add_out(double* p, df64 v) { atomicAdd(p, df_to_double(v)); }
+__device__ __forceinline__ void add_out(double* p, float v) { atomicAdd(p, f2d_exact(v)); }
+__device__ __forceinline__ void add_out(double* p, df64 v) {
+  atomicAdd(p, f2d_exact(v.hi));
+  if (v.lo != 0.0f) atomicAdd(p, f2d_exact(v.lo));
+}
 
 // Gathered input in the arithmetic's terms: an FP64 input entering double-float arithmetic is split
-// into two floats (x = hi + lo to 48 bits, below the arithmetic's own 44); other inputs keep their type.
+// into two floats (x = hi + lo to 48 bits, below the arithmetic's own 44; bit-field split, df64.cuh);
+// other inputs keep their type.
 template <typename T, typename TI> struct gather_of { using type = TI; };
 template <> struct gather_of<df64, double> { using type = df64; };
 template <typename G, typename TI> __device__ __forceinline__ G to_gather(TI v) { return (G)v; }
-template <> __device__ __forceinline__ df64 to_gather<df64, double>(double v) {
-  const float h = __double2float_rn(v);
-  return df64(h, __double2float_rn(v - (double)h));
-}
+template <> __device__ __forceinline__ df64 to_gather<df64, double>(double v) { return df_split_fast(v); }
 
 // T: arithmetic (float, double or double-float), TI: input vector type, TO: output vector type.
 // MASS: mass part only, y (+)= sign * (TM (x) M_h) x (no derivative sweeps, TA ignored).

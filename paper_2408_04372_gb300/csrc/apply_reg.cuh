@@ -2,7 +2,10 @@
 // (Section 3.1) for n = p + 1 <= 3 nodes per direction; the general kernels are in apply_kernels.cuh.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "df64.cuh"
 #include "kernels.h"
 
 namespace stmg {
@@ -270,7 +273,10 @@ apply3d_reg_kernel(const TI* __restrict__ x, TO* __restrict__ y, const float* __
         TO* yr = y + base + nn1 * b + nn2 * k;
 #pragma unroll
         for (int a = 0; a < N; ++a)
-          if (!(bx[a] || by[b] || bz[k])) atomicAdd(yr + a, (TO)o[k][b][a]);
+          if (!(bx[a] || by[b] || bz[k])) {
+            if constexpr (std::is_same<TO, double>::value) atomicAdd(yr + a, f2d_exact(o[k][b][a]));
+            else atomicAdd(yr + a, o[k][b][a]);
+          }
       }
   }
 }

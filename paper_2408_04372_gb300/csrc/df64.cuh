@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cstdint>
 
 namespace stmg {
 
@@ -61,6 +62,48 @@ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) {
 }
 
 __device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// Conversions between FP64 and FP32 formed from the bit fields with integer and FP32 instructions:
+// on GB300 every FP64 instruction, conversions included, runs on the slow FP64 pipe (1/64 of FP32).
+// Exact float -> double for zero and normal floats (others through the FP64 conversion).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sgn = (uint64_t)(u & 0x80000000u) << 32;
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sgn);
+  if (e == 0u || e == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+// Nearest double-float to x: hi = x rounded to 24 bits (to nearest, ties to even), lo = the remainder
+// (at most 29 bits) rounded to float by one integer conversion and scaled by an exact power of two.
+// Exponents for which hi or lo would leave the normal float range, zero, and non-finite values take
+// the FP64 path.
+__device__ __forceinline__ df64 df_split_fast(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E < 949 || E > 1149) {
+    const float h = __double2float_rn(x);
+    return df64(h, __double2float_rn(x - (double)h));
+  }
+  const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);  // 53-bit significand
+  uint32_t hm = (uint32_t)(m >> 29);                           // leading 24 bits
+  const uint32_t r = (uint32_t)(m & ((1u << 29) - 1));         // trailing 29 bits
+  int32_t rem = (int32_t)r;
+  if (r > (1u << 28) || (r == (1u << 28) && (hm & 1u))) {
+    hm += 1u;
+    rem -= (int32_t)(1u << 29);
+  }
+  int eh = E;
+  if (hm == (1u << 24)) {  // rounding carried into the exponent
+    hm >>= 1;
+    eh += 1;
+  }
+  const float hi = __uint_as_float(sgn | ((uint32_t)(eh - 896) << 23) | (hm & 0x7fffffu));
+  const float scale = __uint_as_float((uint32_t)(E - 1075 + 127) << 23);  // 2^(E - 1075), normal
+  const float lo = __fmul_rn(__int2float_rn(rem), scale);
+  return df64(hi, sgn ? -lo : lo);
+}
 
 // Accumulator of a sum of double-float terms with the renormalisation deferred to the end:
 // each term costs TwoSum on the high parts (6 additions) plus 2 additions into the low part,

@@ -151,7 +151,8 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
                             double* out, cudaStream_t s, int* status = nullptr, const double* nrm2 = nullptr,
                             float* copy32 = nullptr, int vfmt = 0);
 // vfmt: 0 FP64 vectors; 1 the basis and w as double-float pairs (hi, lo) in their 8 bytes per entry,
-// double-float arithmetic; 2 the same with w arriving in FP64 (converted and written back as pairs).
+// double-float arithmetic; 2 the same with w arriving in FP64 (converted and written back as pairs);
+// 3 w in FP64, read only, double-float arithmetic (no basis: a norm; the FP64 pass when w is unaligned).
 // r = x * scale as double-float pairs written over x (FP64 in), and its FP32 copy (the V-cycle input).
 cudaError_t launch_scale_to_df(double* x, double scale, int64_t n, float* copy32, cudaStream_t s);
 int cgs_blocks();

@@ -524,10 +524,10 @@ bool node_constrained(const Level& L, int64_t node) {
   return rest == 0 || rest == nn1 - 1;
 }
 
-// out[0] = x . x (device), one launch
+// out[0] = x . x (device), one launch; double-float arithmetic when x is 16-byte aligned
 stmg_status dot_self(stmg_ctx* ctx, const double* x, int64_t n, double* out) {
   CK(launch_cgs_pass(nullptr, n, 0, const_cast<double*>(x), n, nullptr, 0, 0, 1, nullptr, 0, ctx->partial,
-                     ctx->counter, out, ctx->stream, ctx->status));
+                     ctx->counter, out, ctx->stream, ctx->status, nullptr, nullptr, 3));
   ctx->launches += 1;
   return STMG_OK;
 }

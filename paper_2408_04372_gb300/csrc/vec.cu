@@ -2,6 +2,7 @@
 // classical Gram-Schmidt passes (deterministic single-launch reductions), multi-AXPY,
 // time-only mixing of nodal blocks, the dense coarsest-level solve.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "df64.cuh"
@@ -14,11 +15,9 @@ namespace {
 constexpr int kMaxVec = 72;
 constexpr int kCgsThreads = 256;
 
-// Nearest double-float to an FP64 value (hi = x rounded to float, lo = the rounded remainder).
-__device__ __forceinline__ df64 df_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return df64(h, __double2float_rn(x - (double)h));
-}
+// Nearest double-float to an FP64 value (hi = x rounded to float, lo = the rounded remainder), formed
+// without the FP64 pipe where the exponent allows (df64.cuh).
+__device__ __forceinline__ df64 df_from_double(double x) { return df_split_fast(x); }
 // Renormalised pair (Fast2Sum): hi becomes the float nearest to hi + lo.
 __device__ __forceinline__ df64 df_renorm(df64 a) {
   const float h = __fadd_rn(a.hi, a.lo);
@@ -148,8 +147,8 @@ __device__ __forceinline__ void block_fused_norm(const double* nrm2, const doubl
   __syncthreads();
 }
 
-// Sum of a double-float value over the warp in double-float arithmetic (FP32 pipe); lane 0 returns it in FP64.
-__device__ __forceinline__ double warp_sum_df(df_acc a) {
+// Sum of a double-float value over the warp in double-float arithmetic (FP32 pipe), valid in lane 0.
+__device__ __forceinline__ df64 warp_sum_df(df_acc a) {
   df64 v = a;
   df_acc s(v);
   for (int off = 16; off > 0; off >>= 1) {
@@ -157,8 +156,49 @@ __device__ __forceinline__ double warp_sum_df(df_acc a) {
     const df64 o(__shfl_down_sync(0xffffffffu, cur.hi, off), __shfl_down_sync(0xffffffffu, cur.lo, off));
     s += o;
   }
-  const df64 r = s;
-  return (double)r.hi + (double)r.lo;
+  return s;
+}
+
+// The final sums in double-float: per-block partials as (hi, lo) pairs, sums in double-float, one
+// conversion to FP64 per slot at the end (the FP64 pipe of this GPU is slow, conversions included).
+template <int K, int THREADS>
+__device__ __forceinline__ void final_sums_df(const float2* __restrict__ partial, int nb, int nv, int dot, int norm,
+                                              float2 (*red)[K + 1], double* tot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int JC = 8;
+#pragma unroll 1
+  for (int j0 = 0; j0 <= K; j0 += JC) {
+    df_acc x[JC];
+#pragma unroll
+    for (int i = 0; i < JC; ++i) x[i] = df_acc(0.0f);
+    for (int b = tid; b < nb; b += THREADS) {
+#pragma unroll
+      for (int i = 0; i < JC; ++i) {
+        const int j = j0 + i;
+        if (j <= K && ((j < K && dot && j < nv) || (j == K && norm))) {
+          const float2 v = __ldcg(partial + (int64_t)j * nb + b);
+          x[i] += df64(v.x, v.y);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      const int j = j0 + i;
+      if (j <= K && ((j < K && dot && j < nv) || (j == K && norm))) {
+        const df64 v = warp_sum_df(x[i]);
+        if (lane == 0) red[warp][j] = make_float2(v.hi, v.lo);
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j <= K; j += THREADS) {
+    if ((j < K && dot && j < nv) || (j == K && norm)) {
+      df_acc v(0.0f);
+      for (int w = 0; w < THREADS / 32; ++w) v += df64(red[w][j].x, red[w][j].y);
+      const df64 t = v;
+      tot[j] = f2d_exact(t.hi) + f2d_exact(t.lo);
+    }
+  }
 }
 
 template <int K>
@@ -248,7 +288,8 @@ cgs_pass_kernel(const double* __restrict__ V0, int64_t stride, int nv, double* _
 }
 
 // ---- double-float pass with direct loads (basis widths up to 16) ----
-// The basis and w hold double-float pairs (w in FP64 when w64, converted and written back); each thread
+// The basis and w hold double-float pairs (w in FP64 when w64: converted and written back when w64 = 1,
+// read only when w64 = 2, e.g. for a norm); each thread
 // takes two consecutive elements of every vector with one 16-byte load, all nv + 1 loads of a pair issued
 // before they are used, so that every SM keeps well over 100 KB in flight; the last element of an odd
 // n is taken by one thread.  Results, reduction order and side outputs as in the FP64 passes.
@@ -266,7 +307,7 @@ cgs_pass_df_kernel(const double* __restrict__ V0, int64_t stride, int nv, double
                    double* __restrict__ out, const double* __restrict__ nrm2, float* __restrict__ copy32, int w64) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double red[kCgsDfThreads / 32][K + 1];
+  __shared__ float2 redd[kCgsDfThreads / 32][K + 1];
   __shared__ double cs[K];
   __shared__ df64 csd[K];
   __shared__ bool last;
@@ -339,7 +380,7 @@ cgs_pass_df_kernel(const double* __restrict__ V0, int64_t stride, int nv, double
       }
       if (!pair) wv[1] = df64(0.0f);
     }
-    if (sub || w64) {
+    if (sub || w64 == 1) {
       if (pair) *reinterpret_cast<float4*>(w + e) = make_float4(wv[0].hi, wv[0].lo, wv[1].hi, wv[1].lo);
       else *reinterpret_cast<float2*>(w + e) = make_float2(wv[0].hi, wv[0].lo);
     }
@@ -364,21 +405,24 @@ cgs_pass_df_kernel(const double* __restrict__ V0, int64_t stride, int nv, double
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + tid; p < npairs; p += (int64_t)gridDim.x * blockDim.x)
     step(2 * p, true);
   if ((n & 1) && blockIdx.x == 0 && tid == 0) step(n - 1, false);
-  // block partials, then the last block sums them in a fixed order (final_sums)
+  // block partials as double-float pairs (warp and block sums in double-float), then the last block sums
+  // them in a fixed order (final_sums_df) and converts once per slot
+  float2* partd = reinterpret_cast<float2*>(partial);
 #pragma unroll
   for (int j = 0; j <= K; ++j) {
     if ((j < K && dot && j < nv) || (j == K && norm)) {
-      const double x = warp_sum_df(acc[j]);
-      if (lane == 0) red[warp][j] = x;
+      const df64 x = warp_sum_df(acc[j]);
+      if (lane == 0) redd[warp][j] = make_float2(x.hi, x.lo);
     }
   }
   __syncthreads();
   const int nb = gridDim.x;
   for (int j = tid; j <= K; j += blockDim.x) {
     if ((j < K && dot && j < nv) || (j == K && norm)) {
-      double x = 0.0;
-      for (int wv = 0; wv < kCgsDfThreads / 32; ++wv) x += red[wv][j];
-      partial[(int64_t)j * nb + blockIdx.x] = x;
+      df_acc x(0.0f);
+      for (int wv = 0; wv < kCgsDfThreads / 32; ++wv) x += df64(redd[wv][j].x, redd[wv][j].y);
+      const df64 t = x;
+      partd[(int64_t)j * nb + blockIdx.x] = make_float2(t.hi, t.lo);
     }
   }
   __threadfence();
@@ -388,7 +432,7 @@ cgs_pass_df_kernel(const double* __restrict__ V0, int64_t stride, int nv, double
   if (!last) return;
   __threadfence();
   __shared__ double tot[K + 1];
-  final_sums<K, kCgsDfThreads>(partial, nb, nv, dot, norm, red, tot);
+  final_sums_df<K, kCgsDfThreads>(partd, nb, nv, dot, norm, redd, tot);
   __syncthreads();
   if (fin == 0) {
     for (int j = tid; j < nv; j += blockDim.x)
@@ -654,7 +698,8 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
     if ((j < K && dot && j < nv) || (j == K && norm)) {
       double x;
       if constexpr (DFV) {
-        x = warp_sum_df(accd[j]);
+        const df64 v = warp_sum_df(accd[j]);
+        x = f2d_exact(v.hi) + f2d_exact(v.lo);
       } else {
         x = acc[j];
         for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
@@ -695,18 +740,32 @@ cgs_pass_tma_kernel(const double* __restrict__ V0, int64_t stride, int nv, doubl
   if (tid == 0) *counter = 0u;
 }
 
+// w += sign * sum_j h_j V_j.  FP32 vectors (the FGMRES update from the FP32 preconditioned vectors): the
+// sum in double-float on the FP32 pipe, then one conversion and one FP64 addition per entry, so that w
+// keeps its FP64 value.
 template <typename TV>
 __global__ void multi_axpy_kernel(double* __restrict__ w, const TV* __restrict__ V0, int64_t stride,
                                   const double* __restrict__ h, int nv, double sign, int64_t n) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[kMaxVec];
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) sh[j] = h[j];
+  __shared__ df64 shd[kMaxVec];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    sh[j] = h[j];
+    if constexpr (std::is_same<TV, float>::value) shd[j] = df_from_double(sign * h[j]);
+  }
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s += sh[j] * (double)__ldg(V0 + j * stride + i);
-    w[i] += sign * s;
+    if constexpr (std::is_same<TV, float>::value) {
+      df_acc s(0.0f);
+      for (int j = 0; j < nv; ++j) s += shd[j] * __ldg(V0 + j * stride + i);
+      const df64 t = s;
+      w[i] += f2d_exact(t.hi) + f2d_exact(t.lo);
+    } else {
+      double s = 0.0;
+      for (int j = 0; j < nv; ++j) s += sh[j] * (double)__ldg(V0 + j * stride + i);
+      w[i] += sign * s;
+    }
   }
 }
 
@@ -838,11 +897,12 @@ cudaError_t launch_cgs_pass(const double* V0, int64_t stride, int nv, double* w,
   if (nrm2 && (!fin || norm || !sub)) return cudaErrorInvalidValue;
   // bulk copies need 16-byte aligned sources: w, V0 and the stride between basis vectors
   const bool aligned = ((uintptr_t)w % 16 == 0) && (nv == 0 || (((uintptr_t)V0 % 16 == 0) && stride % 2 == 0));
+  if (vfmt == 3 && !(status && aligned)) vfmt = 0;  // a norm of an FP64 vector: the FP64 pass serves as well
   if (vfmt != 0 && !(status && aligned)) return cudaErrorInvalidValue;  // double-float: aligned vectors only
   if (vfmt != 0 && nv <= 16) {
 #define STMG_CGS_DF(KK)                                                                                        \
   return launch_k(cgs_pass_df_kernel<KK>, dim3(152 * CgsDf<KK>::BPS), dim3(kCgsDfThreads), 0, s, V0, stride, nv, w, n, \
-                  c, sub, dot, norm, h_prev, fin, partial, counter, out, nrm2, copy32, (int)(vfmt == 2))
+                  c, sub, dot, norm, h_prev, fin, partial, counter, out, nrm2, copy32, vfmt == 2 ? 1 : vfmt == 3 ? 2 : 0)
     if (nv <= 4) STMG_CGS_DF(4);
     if (nv <= 8) STMG_CGS_DF(8);
     STMG_CGS_DF(16);
