@@ -612,12 +612,15 @@ asm_apply_tma_kernel(const T* __restrict__ r, T* __restrict__ u, const TI* __res
 // residuals, and after one barrier multiplies each slab's modal residual by its rows from registers.
 // Two barriers per batch instead of two per slab, and the stored rows are read from shared memory once
 // per group.
+// SB slabs per batch (8).  For one slab the early release of the stage does not pay: the rows held in
+// registers cost 4 CTAs per SM instead of 6, and the sweep measured 34.9 us against 29.6 us for
+// asm_apply_tma_kernel (bench workload, GB300).
 constexpr int kMultiSB = 8;
-template <int DIM, int N, int NT>
+template <int DIM, int N, int NT, int SB>
 struct MultiCfg {
   using C = TmaCfg<DIM, N, NT, __nv_bfloat16>;
   static constexpr int NBP = nb_pad(C::NB);
-  static constexpr size_t SR_BYTES = (size_t)C::CPG * kMultiSB * NT * NBP * sizeof(float);
+  static constexpr size_t SR_BYTES = (size_t)C::CPG * SB * NT * NBP * sizeof(float);
   static constexpr size_t SMEM = C::SMEM + SR_BYTES;
 };
 
@@ -625,7 +628,7 @@ __device__ __forceinline__ float2 bf16x2_lo_hi(uint32_t w) {
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
-template <int DIM, int N, int NT>
+template <int DIM, int N, int NT, int SB>
 __global__ void __launch_bounds__(TmaCfg<DIM, N, NT, __nv_bfloat16>::THREADS, 4)
 asm_multi_rows_kernel(const float* __restrict__ r, float* __restrict__ u, const __nv_bfloat16* __restrict__ inv,
                       GridDesc g, ModeTab<float> mt, const float* __restrict__ copy_src, float* __restrict__ copy_dst,
@@ -633,7 +636,7 @@ asm_multi_rows_kernel(const float* __restrict__ r, float* __restrict__ u, const 
   pdl_wait();
   pdl_trigger();
   using C = TmaCfg<DIM, N, NT, __nv_bfloat16>;
-  constexpr int NB = C::NB, CPG = C::CPG, S = C::S, SB = kMultiSB;
+  constexpr int NB = C::NB, CPG = C::CPG, S = C::S;
   constexpr int64_t CS = C::CS;
   constexpr int NBP = nb_pad(NB), NW = NBP / 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -792,12 +795,12 @@ asm_multi_rows_kernel(const float* __restrict__ r, float* __restrict__ u, const 
   }
 }
 
-template <int DIM, int N, int NT>
+template <int DIM, int N, int NT, int SB>
 cudaError_t launch_multi_rows(const float* r, float* u, const void* inv, const GridDesc& g, const ModeTab<float>& mt,
                               const float* cs, float* cd, int* status, int nslab, int64_t ss, cudaStream_t s) {
   using C = TmaCfg<DIM, N, NT, __nv_bfloat16>;
-  using M = MultiCfg<DIM, N, NT>;
-  auto k = asm_multi_rows_kernel<DIM, N, NT>;
+  using M = MultiCfg<DIM, N, NT, SB>;
+  auto k = asm_multi_rows_kernel<DIM, N, NT, SB>;
   static int per_sm = 0, sms = 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM);
@@ -874,7 +877,7 @@ cudaError_t apply_t(const T* r, T* u, const void* inv, const GridDesc& g, const 
   }
   if constexpr (std::is_same<T, float>::value && std::is_same<TI, __nv_bfloat16>::value &&
                 Shape<DIM, N>::NB <= 27) {
-    if (nslab > 1) return launch_multi_rows<DIM, N, NT>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);
+    if (nslab > 1) return launch_multi_rows<DIM, N, NT, kMultiSB>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s);
   }
   return nslab > 1 ? launch_tma<DIM, N, NT, T, TI, true>(r, u, inv, g, mt, cs, cd, status, nslab, ss, s)
                    : launch_tma<DIM, N, NT, T, TI, false>(r, u, inv, g, mt, cs, cd, status, 1, ss, s);

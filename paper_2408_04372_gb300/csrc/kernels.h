@@ -167,6 +167,8 @@ cudaError_t launch_point_values(const double* u, int64_t n_nodes, int ncomp, con
 // y[i][node] = sum_j C[i][j] x_j[node] over nin vectors (time-only mixing)
 cudaError_t launch_time_mix(const double* const* xs, int nin, const double* C, int nout, double* y,
                             int64_t n_nodes, int accumulate, cudaStream_t s);
+// inv: n rows of coarse_ld(n) entries (zero padding), row-major
+inline int coarse_ld(int n) { return (n + 3) / 4 * 4; }
 template <typename T>
 cudaError_t launch_coarse_solve(const T* f, T* u, const T* inv, const int64_t* map, int n, int64_t total,
                                 cudaStream_t s);

@@ -540,7 +540,6 @@ stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, i
                                   float* copy32 = nullptr, double* hdst = nullptr, bool df = false) {
   double* d_h1 = ctx->dsm;
   double* d_h2 = ctx->dsm + 128;
-  double* d_out = ctx->dsm + 384;
   int* st = ctx->status;
   // df: the basis is in double-float pairs; the first pass converts w (FP64, the operator's output)
   CK(launch_cgs_pass(V0, ld, nv, w, n, nullptr, 0, 1, 0, nullptr, 0, ctx->partial, ctx->counter, d_h1, ctx->stream, st,
@@ -549,10 +548,12 @@ stmg_status orthogonalise_enqueue(stmg_ctx* ctx, const double* V0, int64_t ld, i
   // its result and normalises it (and writes the FP32 copy) as it subtracts
   CK(launch_cgs_pass(V0, ld, nv, w, n, d_h1, 1, 1, 1, nullptr, 0, ctx->partial, ctx->counter, d_h2, ctx->stream, st,
                      nullptr, nullptr, df ? 1 : 0));
-  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 0, d_h1, 1, ctx->partial, ctx->counter, d_out, ctx->stream, st,
-                     d_h2 + nv, copy32, df ? 1 : 0));
+  // the third pass's last block writes the Arnoldi column straight into the pinned host buffer (mapped
+  // and device-addressable under unified addressing; the host reads it after the stream or the
+  // iteration's event has completed): no copy between one iteration and the next
+  CK(launch_cgs_pass(V0, ld, nv, w, n, d_h2, 1, 0, 0, d_h1, 1, ctx->partial, ctx->counter, hdst ? hdst : ctx->hsm,
+                     ctx->stream, st, d_h2 + nv, copy32, df ? 1 : 0));
   ctx->launches += 3;
-  CK(cudaMemcpyAsync(hdst ? hdst : ctx->hsm, d_out, sizeof(double) * (nv + 2), cudaMemcpyDeviceToHost, ctx->stream));
   return STMG_OK;
 }
 
@@ -873,16 +874,22 @@ stmg_status setup_coarse(stmg_ctx* ctx, Level& L) {
     for (int i = 0; i < n; ++i) S[(size_t)i * n + j] = col[map[i]];
   }
   if (!invert(n, S)) { ctx->err = "coarsest operator singular"; return STMG_ERR_INTERNAL; }
-  // row-major inverse (the coarse kernel reads one row per warp)
-  std::vector<double> cm((size_t)n * n);
-  std::vector<float> cmf((size_t)n * n);
-  for (size_t e = 0; e < (size_t)n * n; ++e) { cm[e] = S[e]; cmf[e] = (float)S[e]; }
+  // row-major inverse, rows padded with zeros to coarse_ld(n) entries (the coarse kernel reads one row
+  // per warp in 16-byte loads)
+  const int ld = coarse_ld(n);
+  std::vector<double> cm((size_t)n * ld, 0.0);
+  std::vector<float> cmf((size_t)n * ld, 0.0f);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      cm[(size_t)i * ld + j] = S[(size_t)i * n + j];
+      cmf[(size_t)i * ld + j] = (float)S[(size_t)i * n + j];
+    }
   CKS(dev_alloc(ctx, &L.cmap, n));
-  CKS(dev_alloc(ctx, &L.cinv64, (size_t)n * n));
-  CKS(dev_alloc(ctx, &L.cinv32, (size_t)n * n));
+  CKS(dev_alloc(ctx, &L.cinv64, (size_t)n * ld));
+  CKS(dev_alloc(ctx, &L.cinv32, (size_t)n * ld));
   CK(cudaMemcpy(L.cmap, map.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(L.cinv64, cm.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(L.cinv32, cmf.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cinv64, cm.data(), sizeof(double) * n * ld, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cinv32, cmf.data(), sizeof(float) * n * ld, cudaMemcpyHostToDevice));
   return STMG_OK;
 }
 

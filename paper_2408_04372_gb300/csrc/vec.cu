@@ -808,23 +808,51 @@ __global__ void time_mix_kernel(MixTab m, int nin, int nout, double* __restrict_
   }
 }
 
-// Coarsest-level solve u[map[i]] = sum_j inv[i][j] f[map[j]] with the inverse stored row-major: each
-// block gathers the n right-hand-side entries into shared memory, each warp takes one row and reduces
-// its coalesced dot product with shuffles in a fixed order (deterministic).
+// Coarsest-level solve u[map[i]] = sum_j inv[i][j] f[map[j]] with the inverse stored row-major, rows
+// of ld entries (ld a multiple of 4, zero padding, 16-byte aligned rows): each block gathers the
+// right-hand side into shared memory, each warp takes one row in 16-byte loads with four independent
+// accumulators (a few memory round trips per row instead of one per 32 entries) and reduces it with
+// shuffles in a fixed order (deterministic).
+template <typename T> struct CoarseVec;
+template <> struct CoarseVec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  static __device__ __forceinline__ float dot(const float4 a, const float4 b) {
+    return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w);
+  }
+};
+template <> struct CoarseVec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ double dot(const double2 a, const double2 b) { return a.x * b.x + a.y * b.y; }
+};
 template <typename T>
 __global__ void coarse_solve_kernel(const T* __restrict__ f, T* __restrict__ u, const T* __restrict__ inv,
-                                    const int64_t* __restrict__ map, int n) {
+                                    const int64_t* __restrict__ map, int n, int ld) {
   pdl_wait();
   pdl_trigger();
+  using CV = CoarseVec<T>;
+  using V = typename CV::V;
   extern __shared__ __align__(16) unsigned char cs_raw[];
   T* fc = reinterpret_cast<T*>(cs_raw);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) fc[j] = f[map[j]];
+  for (int j = threadIdx.x; j < ld; j += blockDim.x) fc[j] = j < n ? f[map[j]] : T(0);
   __syncthreads();
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  const int nc = ld / CV::W;
+  const V* fv = reinterpret_cast<const V*>(fc);
   for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n; i += gridDim.x * warps) {
-    const T* row = inv + (int64_t)i * n;
-    T s = 0;
-    for (int j = lane; j < n; j += 32) s += row[j] * fc[j];
+    const V* row = reinterpret_cast<const V*>(inv + (int64_t)i * ld);
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int c = lane;
+    for (; c + 96 < nc; c += 128) {
+      const V r0 = __ldg(row + c), r1 = __ldg(row + c + 32), r2 = __ldg(row + c + 64), r3 = __ldg(row + c + 96);
+      a0 += CV::dot(r0, fv[c]);
+      a1 += CV::dot(r1, fv[c + 32]);
+      a2 += CV::dot(r2, fv[c + 64]);
+      a3 += CV::dot(r3, fv[c + 96]);
+    }
+    for (; c < nc; c += 32) a0 += CV::dot(__ldg(row + c), fv[c]);
+    T s = (a0 + a1) + (a2 + a3);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) u[map[i]] = s;
   }
@@ -972,9 +1000,10 @@ template <typename T>
 cudaError_t launch_coarse_solve(const T* f, T* u, const T* inv, const int64_t* map, int n, int64_t total,
                                 cudaStream_t s) {
   (void)total;
-  const size_t smem = (size_t)n * sizeof(T);  // n <= 4096 unknowns: at most 32 KB
+  const int ld = coarse_ld(n);
+  const size_t smem = (size_t)ld * sizeof(T);  // n <= 4096 unknowns: at most 32 KB
   const int blocks = std::max(1, std::min((n + 7) / 8, 152 * 4));
-  { const cudaError_t e_ = launch_k(coarse_solve_kernel<T>, dim3(blocks), dim3(256), smem, s, f, u, inv, map, n); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_k(coarse_solve_kernel<T>, dim3(blocks), dim3(256), smem, s, f, u, inv, map, n, ld); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(const float*, float*, const float*, const int64_t*, int, int64_t,
