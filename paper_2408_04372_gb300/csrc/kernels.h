@@ -110,6 +110,8 @@ struct Transfer1D {
   const double* p_w;     // [nn1_f][width_p]
   const int* r_idx;      // [nn1_c][width_r]  (fine index, -1 padding)
   const double* r_w;     // [nn1_c][width_r]
+  const float* p_w32;    // the weights in FP32 for the FP32 V-cycle (converting per use would take the
+  const float* r_w32;    // FP64 pipe, which is slow on this GPU)
   void* tmp1;            // scratch: nt * nn1_f^2 * nn1_c doubles each
   void* tmp2;
 };

@@ -820,27 +820,33 @@ stmg_status setup_transfer(stmg_ctx* ctx, Level& F, const Level& C) {
       rlist[gc].push_back({gf, v});
     }
   auto pack = [&](const std::vector<std::vector<std::pair<int, double>>>& lists, int& R, int** d_idx,
-                  double** d_w) -> stmg_status {
+                  double** d_w, float** d_w32) -> stmg_status {
     R = 1;
     for (auto& l : lists) R = std::max<int>(R, (int)l.size());
     std::vector<int> idx(lists.size() * R, -1);
     std::vector<double> wt(lists.size() * R, 0.0);
     for (size_t i = 0; i < lists.size(); ++i)
       for (size_t c = 0; c < lists[i].size(); ++c) { idx[i * R + c] = lists[i][c].first; wt[i * R + c] = lists[i][c].second; }
+    std::vector<float> wt32(wt.begin(), wt.end());
     CKS(dev_alloc(ctx, d_idx, idx.size()));
     CKS(dev_alloc(ctx, d_w, wt.size()));
+    CKS(dev_alloc(ctx, d_w32, wt32.size()));
     CK(cudaMemcpy(*d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(*d_w, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(*d_w32, wt32.data(), sizeof(float) * wt32.size(), cudaMemcpyHostToDevice));
     return STMG_OK;
   };
   int *pi = nullptr, *ri = nullptr;
   double *pw = nullptr, *rw = nullptr;
-  CKS(pack(plist, F.tr.width_p, &pi, &pw));
-  CKS(pack(rlist, F.tr.width_r, &ri, &rw));
+  float *pw32 = nullptr, *rw32 = nullptr;
+  CKS(pack(plist, F.tr.width_p, &pi, &pw, &pw32));
+  CKS(pack(rlist, F.tr.width_r, &ri, &rw, &rw32));
   F.tr.p_idx = pi;
   F.tr.p_w = pw;
+  F.tr.p_w32 = pw32;
   F.tr.r_idx = ri;
   F.tr.r_w = rw;
+  F.tr.r_w32 = rw32;
   const size_t tmp = (size_t)F.nt * F.nc * nf * (size_t)(F.dim == 3 ? nf : 1) * nc;
   double *t1 = nullptr, *t2 = nullptr;
   CKS(dev_alloc(ctx, &t1, tmp));

@@ -42,7 +42,7 @@ struct SideJob {
 // in_dims[axis] to n_out.
 template <typename T>
 __global__ void gather_axis_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int d2, int nt,
-                                   int axis, int n_out, const int* __restrict__ idx, const double* __restrict__ w,
+                                   int axis, int n_out, const int* __restrict__ idx, const T* __restrict__ w,
                                    int R, int accumulate, SideJob<T> side) {
   pdl_wait();
   pdl_trigger();
@@ -61,7 +61,7 @@ __global__ void gather_axis_kernel(const T* __restrict__ in, T* __restrict__ out
     for (int k = 0; k < R; ++k) {
       const int j = idx[i * R + k];
       if (j < 0) break;
-      acc += (T)w[i * R + k] * in[base + (int64_t)j * sin_];
+      acc += w[i * R + k] * in[base + (int64_t)j * sin_];
     }
     if (accumulate) out[e] += acc;
     else out[e] = acc;
@@ -81,7 +81,7 @@ __host__ __device__ inline bool transfer_fused(int terms, int64_t n_out) {
 // index 0) and then issues all R^DIM input loads at once.
 template <typename T, int R, int DIM>
 __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ out, int nt, int nin, int nout,
-                                    const int* __restrict__ idx, const double* __restrict__ w, int accumulate,
+                                    const int* __restrict__ idx, const T* __restrict__ w, int accumulate,
                                     SideJob<T> side) {
   pdl_wait();
   pdl_trigger();
@@ -103,13 +103,13 @@ __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ ou
     for (int k = 0; k < R; ++k) {
       const int ix = __ldg(idx + x * R + k), iy = __ldg(idx + y * R + k);
       jx[k] = ix < 0 ? 0 : ix;
-      wx[k] = ix < 0 ? T(0) : (T)__ldg(w + x * R + k);
+      wx[k] = ix < 0 ? T(0) : __ldg(w + x * R + k);
       jy[k] = iy < 0 ? 0 : iy;
-      wy[k] = iy < 0 ? T(0) : (T)__ldg(w + y * R + k);
+      wy[k] = iy < 0 ? T(0) : __ldg(w + y * R + k);
       if (DIM == 3) {
         const int iz = __ldg(idx + z * R + k);
         jz[k] = iz < 0 ? 0 : iz;
-        wz[k] = iz < 0 ? T(0) : (T)__ldg(w + z * R + k);
+        wz[k] = iz < 0 ? T(0) : __ldg(w + z * R + k);
       } else {
         jz[k] = 0;
         wz[k] = k == 0 ? T(1) : T(0);
@@ -136,8 +136,13 @@ __global__ void gather_fused_kernel(const T* __restrict__ in, T* __restrict__ ou
   }
 }
 
+// The transfer weights in the arithmetic's own type (FP64 table or its FP32 copy).
+template <typename T> const T* weights(const double* w64, const float* w32);
+template <> const double* weights<double>(const double* w64, const float*) { return w64; }
+template <> const float* weights<float>(const double*, const float* w32) { return w32; }
+
 template <typename T>
-cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, const int* idx, const double* w, int R,
+cudaError_t separable(const T* in, T* out, int dim, int nt, int nin, int nout, const int* idx, const T* w, int R,
                       T* t1, T* t2, int accumulate, SideJob<T> side, cudaStream_t s) {
   const SideJob<T> none{};
   // passes x, y(, z): dims go from nin^dim to nout^dim
@@ -231,7 +236,8 @@ cudaError_t launch_prolong_space_add(T* uf, const T* ec, const GridDesc& gf, con
   SideJob<T> side;
   side.copy_src = copy_src;
   side.copy_dst = copy_dst;
-  return separable<T>(ec, uf, gf.dim, nt, gc.nn1, gf.nn1, t.p_idx, t.p_w, t.width_p, reinterpret_cast<T*>(t.tmp1),
+  return separable<T>(ec, uf, gf.dim, nt, gc.nn1, gf.nn1, t.p_idx, weights<T>(t.p_w, t.p_w32), t.width_p,
+                      reinterpret_cast<T*>(t.tmp1),
                       reinterpret_cast<T*>(t.tmp2), 1, side, s);
 }
 template <typename T>
@@ -239,7 +245,8 @@ cudaError_t launch_restrict_space(T* rc, const T* rf, const GridDesc& gf, const 
                                   const Transfer1D& t, T* zero_dst, cudaStream_t s) {
   SideJob<T> side;
   side.zero_dst = zero_dst;
-  return separable<T>(rf, rc, gf.dim, nt, gf.nn1, gc.nn1, t.r_idx, t.r_w, t.width_r, reinterpret_cast<T*>(t.tmp1),
+  return separable<T>(rf, rc, gf.dim, nt, gf.nn1, gc.nn1, t.r_idx, weights<T>(t.r_w, t.r_w32), t.width_r,
+                      reinterpret_cast<T*>(t.tmp1),
                       reinterpret_cast<T*>(t.tmp2), 0, side, s);
 }
 template <typename T>
