@@ -139,9 +139,6 @@ cudaError_t launch_restrict_time(T* rc, const T* rf, const GridDesc& g, const Ti
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, int64_t n, cudaStream_t s);
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
-// x *= *inv_scale_src; copy32 (may be NULL) also receives (float) x
-cudaError_t launch_scale_by_device(double* x, const double* inv_scale_src, int64_t n, cudaStream_t s,
-                                   float* copy32 = nullptr);
 // One classical Gram-Schmidt pass over V_0..V_{nv-1} (nv <= 64), single launch, bit-reproducible:
 // optionally w -= sum_j c[j] V_j, then s_j = V_j . w and/or s_nv = w . w; fin 0 writes s to out,
 // fin 1 the Arnoldi column out[j] = h_prev[j] + c[j], out[nv] = ||w||, out[nv+1] = 1/||w||.

@@ -58,19 +58,6 @@ __global__ void scale_to_df_kernel(double* __restrict__ x, double scale, int64_t
   }
 }
 
-// x *= sc[0]; with y32, also y32 = (float) x (the next V-cycle's input, written in the same pass)
-__global__ void scale_by_device_kernel(double* __restrict__ x, const double* __restrict__ sc, int64_t n,
-                                       float* __restrict__ y32) {
-  pdl_wait();
-  pdl_trigger();
-  const double s = sc[0];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = x[i] * s;
-    x[i] = v;
-    if (y32) y32[i] = (float)v;
-  }
-}
-
 // One pass of classical Gram-Schmidt against V_0..V_{nv-1} (V_j = V0 + j * stride):
 //   sub : w -= sum_j c[j] V_j             (c on the device)
 //   dot : s_j = V_j . w, j < nv            (after the subtraction)
@@ -894,8 +881,6 @@ cudaError_t launch_scale_to_df(double* x, double scale, int64_t n, float* copy32
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_by_device(double* x, const double* sc, int64_t n, cudaStream_t s, float* copy32) {
-  { const cudaError_t e_ = launch_k(scale_by_device_kernel, dim3(grid_blocks(n)), dim3(256), 0, s, x, sc, n, copy32); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
