@@ -881,9 +881,6 @@ cudaError_t launch_scale_to_df(double* x, double scale, int64_t n, float* copy32
   return cudaGetLastError();
 }
 
-  return cudaGetLastError();
-}
-
 int cgs_blocks() { return kCgsBlocks; }
 
 template <int K, bool DFV>
